@@ -1,0 +1,359 @@
+"""Benchmark: strong-bisimulation reduction of one synthetic LTS per step.
+
+A step is one whole reduction through the C ABI: bisim_plan (validation,
+sort by (source, label), mark slots, incoming-transition CSR, initial
+leaders, action-set preprocessing) and bisim_refine (the main loop and the
+canonical output) on inputs already resident in device memory. The default
+workload is the labelled LTS built by quotient expansion (seed 1: 2,000
+classes, 20,000 quotient transitions, 8 Zipf labels, 1..100 copies, 10%
+duplicates: about 101,658 states and 1,114,407 transitions).
+
+Prints one JSON line (rank 0). `--impl reference` times the CPU oracle
+(Kanellakis-Smolka, single thread) on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2105_11788_gb300 import lts_gen  # noqa: E402
+
+WORKLOADS = {
+    "qexp": ("labelled LTS by quotient expansion (seed 1, ~101.7k states, ~1.11M transitions, "
+             "|Act|=8 Zipf, single initial block)", lambda: lts_gen.quotient_expansion(seed=1)),
+    "kripke": ("Kripke structure (seed 0, n=1000, m=4000, 4 AP blocks)",
+               lambda: lts_gen.kripke_uniform(seed=0)),
+    "chain": ("deep-refinement chain (seed 2, n=50000)", lambda: lts_gen.chain(seed=2, n=50000)),
+    "powerlaw": ("power-law LTS (seed 3, n=10M, m~100M, |Act|=32, 4 AP blocks)",
+                 lambda: lts_gen.powerlaw(seed=3)),
+}
+
+L2_BYTES = 129 * 1024 * 1024
+
+
+def read_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_id: str):
+        self.device_id = device_id
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                   "-lms", "100"]
+            if self.device_id:
+                cmd += ["-i", self.device_id]
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        backend = "nccl" if args.impl != "reference" else "gloo"
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(x, world, device=None):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def dense_bytes_per_launch(st):
+    """Algorithmic bytes of one main-loop launch of the dense engine: per round
+    4n (unstable scan) + 4n (block, mark scan) + 4n (block, compare) + 8n (own
+    off pair) + 8n (leader off pair) + 2n (split flag write and read) + 8L (own
+    and leader mark slots); plus 12 B per incoming transition walked (8 B
+    record + 4 B mark store)."""
+    n, L = st.n, st.mark_length
+    return st.rounds * (30 * n + 8 * L) + 12 * st.edges_visited
+
+
+def frontier_bytes_per_launch(st):
+    """Algorithmic bytes of one main-loop launch of the frontier engine: 20 B
+    per incoming transition walked (8 B record, 4 B mark stamp, 4 B source
+    block, 4 B touched stamp) and 24 B per state whose marks were compared
+    (member id, block label, off pair, leader mark slots amortised, move and
+    relabel)."""
+    return 20 * st.edges_visited + 24 * st.states_visited
+
+
+def run_reference(args, world, rank):
+    """CPU oracle (Kanellakis-Smolka, one thread) on the same workload."""
+    import oracle
+
+    if world > 1 and rank != 0:
+        return
+    desc, make = WORKLOADS[args.workload]
+    lts = make()
+    for _ in range(args.warmup):
+        oracle.ks_lts(lts)
+    times = []
+    t_total = time.perf_counter()
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.ks_lts(lts)
+        times.append(time.perf_counter() - t0)
+    t_total = time.perf_counter() - t_total
+    ms = 1000.0 * sum(times) / len(times)
+    value = 1000.0 / ms
+    sample = f"{args.steps} full reductions of the workload (oracle_ks, single-threaded C)"
+    line = {
+        "impl": "reference", "metric": "LTS reduction throughput", "value": value,
+        "unit": "LTS/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int32", "data": "synthetic",
+        "config": {"workload": desc, "n": lts.n, "m": lts.m, "num_act": lts.num_act,
+                   "l2": "CPU run"},
+        "cpu_baseline": {"value": value, "unit": "LTS/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "LTS/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(lts, budget_s):
+    import oracle
+
+    t0 = time.perf_counter()
+    k = 0
+    while True:
+        oracle.ks_lts(lts)
+        k += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    el = time.perf_counter() - t0
+    return {"value": k / el, "unit": "LTS/s", "cores": 1, "kind": "oracle",
+            "sample": f"{k} full reductions of the same workload by oracle_ks (single-threaded C), "
+                      f"{el:.1f} s"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="qexp", choices=sorted(WORKLOADS))
+    ap.add_argument("--engine", default="auto", choices=["auto", "dense", "frontier"])
+    ap.add_argument("--cpu-budget", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import torch
+
+    from paper_2105_11788_gb300 import bisim
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    bisim.load(build_if_missing=True)
+    engine = {"auto": bisim.ENGINE_AUTO, "dense": bisim.ENGINE_DENSE,
+              "frontier": bisim.ENGINE_FRONTIER}[args.engine]
+    opts = bisim.make_opts(engine=engine)
+    desc, make = WORKLOADS[args.workload]
+    lts = make()
+    src = torch.from_numpy(lts.src).to(dev)
+    act = torch.from_numpy(lts.act).to(dev)
+    dst = torch.from_numpy(lts.dst).to(dev)
+    init = torch.from_numpy(lts.init).to(dev) if lts.init is not None else None
+    out = torch.empty(max(lts.n, 1), dtype=torch.int32, device=dev)
+    in_bytes = lts.nbytes()
+    flush = None
+    if in_bytes < 2 * L2_BYTES:
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    sp = int(stream.cuda_stream)
+
+    def step():
+        h = bisim.bisim_plan(lts.n, lts.m, lts.num_act, src.data_ptr(), act.data_ptr(),
+                             dst.data_ptr(), init.data_ptr() if init is not None else None, opts, sp)
+        try:
+            st = bisim.bisim_refine(h, out.data_ptr())
+        finally:
+            bisim.bisim_plan_destroy(h)
+        return st
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    dev_id = ""
+    try:
+        dev_id = str(torch.cuda.get_device_properties(dev).uuid)
+        if dev_id and not dev_id.startswith("GPU-"):
+            dev_id = "GPU-" + dev_id
+    except Exception:
+        dev_id = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0]
+    clocks = ClockSampler(dev_id)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    total_ms = 0.0
+    kernel_ms, kernel_bytes, stats = [], [], []
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    for _ in range(args.steps):
+        if flush is not None:
+            flush.fill_(1)  # untimed: evicts L2 between steps
+        e0.record(stream)
+        st = step()
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        stats.append(st)
+        kernel_ms.append(st.t_main_ms)
+        kernel_bytes.append(dense_bytes_per_launch(st) if st.engine == bisim.ENGINE_DENSE
+                            else frontier_bytes_per_launch(st))
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    ms_step = max_over_ranks(total_ms / args.steps, world, dev)
+    value = world * 1000.0 / ms_step
+    st = stats[-1]
+    hbm, peak_kind = read_peaks()
+    achieved = (sum(kernel_bytes) / len(kernel_bytes)) / (sum(kernel_ms) / len(kernel_ms) * 1e-3) / 1e9
+    roof = {"bound": "hbm", "kernel": "k_dense_main" if st.engine == bisim.ENGINE_DENSE
+            else "k_frontier_main", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "peak_kind": peak_kind, "traffic": None,
+            "kernel_ms": sum(kernel_ms) / len(kernel_ms),
+            "bytes_per_launch": sum(kernel_bytes) / len(kernel_bytes)}
+
+    # end to end through the host-buffer entry point
+    pin = lambda a: torch.from_numpy(a).pin_memory()  # noqa: E731
+    hs, ha, hd = pin(lts.src), pin(lts.act), pin(lts.dst)
+    hi = pin(lts.init) if lts.init is not None else None
+    ho = torch.empty(max(lts.n, 1), dtype=torch.int32).pin_memory()
+    e2e_ms = []
+    for i in range(max(3, args.steps // 2) + 1):
+        t0 = time.perf_counter()
+        bisim.bisim_reduce_host(lts.n, lts.m, lts.num_act, hs.data_ptr(), ha.data_ptr(),
+                                hd.data_ptr(), hi.data_ptr() if hi is not None else None,
+                                ho.data_ptr(), opts, sp)
+        if i:
+            e2e_ms.append(1000 * (time.perf_counter() - t0))
+    e2e_step = max_over_ranks(sum(e2e_ms) / len(e2e_ms), world, dev)
+    h2d = lts.nbytes()
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(lts, args.cpu_budget)
+    if rank == 0:
+        visits = (st.pre_rounds + st.rounds) * lts.m
+        line = {
+            "metric": "LTS reduction throughput", "value": value, "unit": "LTS/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": desc, "n": lts.n, "m": lts.m, "num_act": lts.num_act,
+                       "engine": args.engine,
+                       "l2": "flushed between steps (256 MiB write)" if flush is not None
+                             else "inputs larger than L2",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "roofline": roof,
+            "e2e": {"value": world * 1000.0 / e2e_step, "unit": "LTS/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4 * lts.n,
+                    "ms_per_step": e2e_step},
+            "cpu_baseline": cpu,
+            "gpu_launches": int(sum(s.launches for s in stats)),
+            "clocks": clk,
+            "detail": {"rounds": st.rounds, "pre_rounds": st.pre_rounds,
+                       "initial_blocks": st.initial_blocks, "num_blocks": st.num_blocks,
+                       "mark_length": st.mark_length, "t_plan_ms": st.t_plan_ms,
+                       "t_refine_ms": st.t_refine_ms, "t_pre_ms": st.t_pre_ms,
+                       "t_main_ms": st.t_main_ms, "us_per_round": 1000 * st.t_main_ms / max(st.rounds, 1),
+                       "edges_visited": st.edges_visited, "states_visited": st.states_visited,
+                       "grid_ctas": st.grid_ctas,
+                       "pram_transition_visits_per_s": visits / (ms_step * 1e-3)},
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

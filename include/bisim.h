@@ -1,0 +1,168 @@
+/*
+ * bisim.h - C ABI of the GB300 (sm_103a) strong-bisimulation library.
+ *
+ * The library computes the coarsest partition of the states of a labelled
+ * transition system (LTS) that refines an initial partition and is a
+ * bisimulation: the Bisimulation Coarsest Refinement Problem (BCRP) and, for
+ * one action label, the Relational Coarsest Partition Problem (RCPP), as
+ * stated in Section 2.2 of Martens, Groote, van den Haak, Hijma and Wijs,
+ * "A linear parallel algorithm to compute bisimulation and relational
+ * coarsest partitions" (arXiv:2105.11788). The method is the CRCW-PRAM
+ * refinement of Sections 3 and 4 (Algorithms 2, 3, 4 and 5): every round
+ * elects one splitter block, marks the (state, action) pairs that reach it,
+ * and splits every block into the states whose marks equal the block
+ * leader's and those whose marks differ, the latter led by a freshly elected
+ * leader; rounds repeat until no block is unstable.
+ *
+ * Conventions for every entry point:
+ *  - Array arguments are DEVICE pointers unless the name ends in _h (host).
+ *    The caller owns them; the library never frees them.
+ *  - Inputs are read only during the call that receives them.
+ *  - All work is ordered on the CUDA stream given to bisim_plan (NULL = the
+ *    legacy default stream). Calls synchronise that stream before returning
+ *    because they report device-side errors.
+ *  - Return value: BISIM_OK (0) or a negative BISIM_E* code. No exception
+ *    crosses the ABI and the library never traps or aborts the device; after
+ *    any error the plan (if one was returned) may still be destroyed.
+ *  - Not thread-safe per plan: one host thread at a time per plan.
+ */
+#ifndef BISIM_H
+#define BISIM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BISIM_OK 0
+#define BISIM_EINVAL (-1)   /* bad scalar argument or out-of-range array entry */
+#define BISIM_ENOMEM (-2)   /* device memory allocation failed */
+#define BISIM_ECUDA (-3)    /* a CUDA runtime call failed (see bisim_last_error) */
+#define BISIM_EROUNDS (-4)  /* round cap exceeded (Theorem 3 bound; indicates a bug) */
+#define BISIM_ETIMEOUT (-5) /* a grid-wide barrier wait exceeded its time limit */
+#define BISIM_ENOTSUP (-6)  /* requested engine/option not supported for this input */
+
+/* Refinement engines. */
+#define BISIM_ENGINE_AUTO 0
+/* Dense rounds as printed in Algorithms 3 and 5: every round scans all
+ * states and mark slots; splitter = smallest unstable label and new leader =
+ * smallest splitting state (the priority write rule of Section 2.1), so the
+ * round count and the leader labels equal the lock-step PRAM program. */
+#define BISIM_ENGINE_DENSE 1
+/* Frontier rounds: states kept grouped by block; a round touches only the
+ * splitter's members, their incoming transitions and the blocks of the
+ * marked states. Splitters come from a FIFO worklist and new leaders are
+ * elected by compare-and-swap (the arbitrary write rule). Same partition;
+ * round count may differ and may vary between runs. */
+#define BISIM_ENGINE_FRONTIER 2
+
+typedef struct bisim_opts {
+    int32_t engine;      /* BISIM_ENGINE_* (0 = auto) */
+    int32_t rcpp_alg2;   /* 1: with |Act| = 1, follow Algorithm 2 (the splitter is
+                            not set unstable again after a split); 0: Algorithm 3 */
+    int32_t raw_labels;  /* 1: bisim_refine writes leader labels instead of
+                            canonical ids (testing the election rule) */
+    int32_t threads;     /* threads per CTA for the persistent kernels (0 = 512) */
+    int32_t ctas_per_sm; /* CTAs per SM for the persistent kernels (0 = 1) */
+    int32_t test_hook;   /* testing only: 1 = CTA 0 of the refinement kernel
+                            leaves before its first barrier, so the other CTAs'
+                            barrier waits run out and BISIM_ETIMEOUT is returned */
+    int64_t round_cap;   /* 0 = 3n + |Act| + 2 (Theorem 3 plus slack) */
+    int64_t timeout_ms;  /* limit on one grid-barrier wait (0 = 2000 ms) */
+} bisim_opts;
+
+typedef struct bisim_stats {
+    int64_t n, m, num_act;
+    int64_t mark_length;    /* L: number of distinct (source, label) pairs */
+    int64_t pre_rounds;     /* action-set preprocessing rounds (labels that occur) */
+    int64_t initial_blocks; /* blocks after preprocessing (|pi_0'|) */
+    int64_t rounds;         /* main-loop iterations incl. the final empty one */
+    int64_t num_blocks;     /* blocks of the result */
+    int64_t edges_visited;  /* incoming transitions walked by mark steps */
+    int64_t states_visited; /* states whose marks were compared */
+    double t_plan_ms;       /* device time of bisim_plan (sort, CSR, preprocessing) */
+    double t_refine_ms;     /* device time of the last bisim_refine */
+    double t_pre_ms;        /* device time of the preprocessing-round kernel */
+    double t_main_ms;       /* device time of the main-loop kernel of the last refine */
+    int64_t launches;       /* kernels launched by bisim_plan + the last bisim_refine */
+    int32_t engine;         /* engine that ran */
+    int32_t grid_ctas;      /* CTAs of the persistent launch */
+} bisim_stats;
+
+typedef struct bisim_plan_s* bisim_plan_t;
+
+/*
+ * bisim_plan - validate an LTS and build everything the rounds need.
+ *
+ * Steps (all on the device): range checks of every array entry; the sort of
+ * the transitions by (source, label) with the action_switch / order /
+ * nr_marks / off arrays of Section 4.1.1 (Algorithm 4 and its scans; off is
+ * the exclusive prefix sum of nr_marks, slot(s,a) = off(s) + order); the
+ * incoming-transition index by target (CSR, each entry carrying its source
+ * and mark slot); the initial leaders of Algorithm 2, lines 1-6 (the smallest
+ * member of each initial block); and the action-set preprocessing of
+ * Algorithm 5, one round per label that occurs, in increasing label order.
+ *
+ * n          number of states, 0 <= n < 2^31
+ * m          number of transitions, 0 <= m < 2^31
+ * num_act    number of action labels, >= 1
+ * src, dst   int32 [m], values in [0, n)
+ * act        int32 [m], values in [0, num_act); NULL means every label is 0
+ * init_block int32 [n], values in [0, n) (the I_i of Section 3.2.2; states
+ *            with equal values form one initial block); NULL = one block
+ * opts       NULL = defaults
+ * stream     cudaStream_t as void*, NULL = legacy default stream
+ * out        receives the plan; the plan owns its device workspace until
+ *            bisim_plan_destroy (about 40 bytes per transition and 80 bytes
+ *            per state)
+ * Errors: BISIM_EINVAL for bad scalars or any out-of-range entry (found on
+ * the device), BISIM_ENOMEM, BISIM_ECUDA. On error *out is NULL.
+ */
+int bisim_plan(int32_t n, int64_t m, int32_t num_act, const int32_t* src, const int32_t* act,
+               const int32_t* dst, const int32_t* init_block, const bisim_opts* opts,
+               void* stream, bisim_plan_t* out);
+
+/*
+ * bisim_refine - run the refinement rounds (the while-loop of Algorithm 3,
+ * or Algorithm 2 with rcpp_alg2) from the preprocessed partition and write
+ * the result. May be called again on the same plan; every call starts from
+ * the partition left by bisim_plan.
+ *
+ * out_block  int32 [n] device: block id per state, canonical (blocks
+ *            numbered 0.. in order of their smallest state), or the leader
+ *            label of the state's block if opts.raw_labels was set.
+ * stats      NULL or receives counters and device times.
+ * Errors: BISIM_EROUNDS, BISIM_ETIMEOUT, BISIM_ECUDA, BISIM_EINVAL (NULL plan).
+ */
+int bisim_refine(bisim_plan_t plan, int32_t* out_block, bisim_stats* stats);
+
+/* Release the plan's device memory (stream-ordered). NULL is ignored. */
+void bisim_plan_destroy(bisim_plan_t plan);
+
+/*
+ * bisim_reduce_host - one whole reduction from HOST buffers: copies the
+ * arrays to the device, plans, refines, copies the canonical block ids back
+ * into out_block_h and releases everything. Same arguments and errors as
+ * bisim_plan + bisim_refine; all pointers ending in _h are host memory
+ * (pinned memory gives faster copies), act_h and init_h may be NULL.
+ */
+int bisim_reduce_host(int32_t n, int64_t m, int32_t num_act, const int32_t* src_h,
+                      const int32_t* act_h, const int32_t* dst_h, const int32_t* init_h,
+                      int32_t* out_block_h, const bisim_opts* opts, void* stream,
+                      bisim_stats* stats);
+
+/* Static description of an error code. */
+const char* bisim_strerror(int code);
+
+/* Detail of the last error raised on the calling host thread ("" if none). */
+const char* bisim_last_error(void);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int32_t bisim_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BISIM_H */

@@ -1,0 +1,260 @@
+"""Thin ctypes binding of the C ABI in include/bisim.h.
+
+The functions named like the C entry points (`bisim_plan`, `bisim_refine`,
+`bisim_plan_destroy`, `bisim_reduce_host`, ...) only marshal arguments: raw
+device or host addresses and sizes go in, error codes come out as
+`BisimError`. Every step of the computation runs in libbisim.so's CUDA
+kernels; there is no CPU fallback, and loading fails loudly when the
+library has not been built.
+
+`reduce()` and `Plan` are conveniences over torch tensors (torch is used for
+device memory and streams only).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+from . import _build
+
+BISIM_OK = 0
+BISIM_EINVAL = -1
+BISIM_ENOMEM = -2
+BISIM_ECUDA = -3
+BISIM_EROUNDS = -4
+BISIM_ETIMEOUT = -5
+BISIM_ENOTSUP = -6
+
+ENGINE_AUTO = 0
+ENGINE_DENSE = 1
+ENGINE_FRONTIER = 2
+
+
+class bisim_opts(ctypes.Structure):
+    _fields_ = [
+        ("engine", ctypes.c_int32),
+        ("rcpp_alg2", ctypes.c_int32),
+        ("raw_labels", ctypes.c_int32),
+        ("threads", ctypes.c_int32),
+        ("ctas_per_sm", ctypes.c_int32),
+        ("test_hook", ctypes.c_int32),
+        ("round_cap", ctypes.c_int64),
+        ("timeout_ms", ctypes.c_int64),
+    ]
+
+
+class bisim_stats(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int64),
+        ("m", ctypes.c_int64),
+        ("num_act", ctypes.c_int64),
+        ("mark_length", ctypes.c_int64),
+        ("pre_rounds", ctypes.c_int64),
+        ("initial_blocks", ctypes.c_int64),
+        ("rounds", ctypes.c_int64),
+        ("num_blocks", ctypes.c_int64),
+        ("edges_visited", ctypes.c_int64),
+        ("states_visited", ctypes.c_int64),
+        ("t_plan_ms", ctypes.c_double),
+        ("t_refine_ms", ctypes.c_double),
+        ("t_pre_ms", ctypes.c_double),
+        ("t_main_ms", ctypes.c_double),
+        ("launches", ctypes.c_int64),
+        ("engine", ctypes.c_int32),
+        ("grid_ctas", ctypes.c_int32),
+    ]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+EXPORTED = [
+    "bisim_plan",
+    "bisim_refine",
+    "bisim_plan_destroy",
+    "bisim_reduce_host",
+    "bisim_strerror",
+    "bisim_last_error",
+    "bisim_version",
+]
+
+
+class BisimError(RuntimeError):
+    def __init__(self, code: int, where: str, detail: str = ""):
+        self.code = code
+        super().__init__(f"{where}: {strerror(code)} ({code}){': ' + detail if detail else ''}")
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libbisim.so (raises if it is missing and build_if_missing is False)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        if not build_if_missing:
+            raise RuntimeError(f"libbisim.so not built ({_build.LIB}); run __graft_entry__.build()")
+        _build.build()
+    lib = ctypes.CDLL(_build.LIB)
+    P, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    lib.bisim_plan.argtypes = [i32, i64, i32, P, P, P, P, ctypes.POINTER(bisim_opts), P,
+                               ctypes.POINTER(P)]
+    lib.bisim_plan.restype = ctypes.c_int
+    lib.bisim_refine.argtypes = [P, P, ctypes.POINTER(bisim_stats)]
+    lib.bisim_refine.restype = ctypes.c_int
+    lib.bisim_plan_destroy.argtypes = [P]
+    lib.bisim_plan_destroy.restype = None
+    lib.bisim_reduce_host.argtypes = [i32, i64, i32, P, P, P, P, P, ctypes.POINTER(bisim_opts), P,
+                                      ctypes.POINTER(bisim_stats)]
+    lib.bisim_reduce_host.restype = ctypes.c_int
+    lib.bisim_strerror.argtypes = [ctypes.c_int]
+    lib.bisim_strerror.restype = ctypes.c_char_p
+    lib.bisim_last_error.argtypes = []
+    lib.bisim_last_error.restype = ctypes.c_char_p
+    lib.bisim_version.argtypes = []
+    lib.bisim_version.restype = i32
+    _lib = lib
+    return lib
+
+
+def strerror(code: int) -> str:
+    try:
+        return load().bisim_strerror(code).decode()
+    except Exception:  # library missing: still describe the code
+        return str(code)
+
+
+def _check(code: int, where: str):
+    if code != BISIM_OK:
+        raise BisimError(code, where, load().bisim_last_error().decode())
+
+
+def make_opts(engine: int = ENGINE_AUTO, rcpp_alg2: bool = False, raw_labels: bool = False,
+              threads: int = 0, ctas_per_sm: int = 0, round_cap: int = 0, timeout_ms: int = 0,
+              test_hook: int = 0) -> bisim_opts:
+    return bisim_opts(engine, int(rcpp_alg2), int(raw_labels), threads, ctas_per_sm, test_hook,
+                      round_cap, timeout_ms)
+
+
+# ----------------------------------------------------------- C-ABI mirrors
+
+
+def bisim_plan(n: int, m: int, num_act: int, src: int, act: Optional[int], dst: int,
+               init_block: Optional[int], opts: Optional[bisim_opts] = None,
+               stream: int = 0) -> int:
+    """Device addresses in, plan handle out (see include/bisim.h)."""
+    lib = load()
+    out = ctypes.c_void_p()
+    rc = lib.bisim_plan(n, m, num_act, src or None, act or None, dst or None, init_block or None,
+                        ctypes.byref(opts) if opts is not None else None, stream or None,
+                        ctypes.byref(out))
+    _check(rc, "bisim_plan")
+    return out.value
+
+
+def bisim_refine(plan: int, out_block: int) -> bisim_stats:
+    st = bisim_stats()
+    rc = load().bisim_refine(plan, out_block or None, ctypes.byref(st))
+    _check(rc, "bisim_refine")
+    return st
+
+
+def bisim_plan_destroy(plan: Optional[int]) -> None:
+    if plan:
+        load().bisim_plan_destroy(plan)
+
+
+def bisim_reduce_host(n: int, m: int, num_act: int, src_h: int, act_h: Optional[int], dst_h: int,
+                      init_h: Optional[int], out_h: int, opts: Optional[bisim_opts] = None,
+                      stream: int = 0) -> bisim_stats:
+    st = bisim_stats()
+    rc = load().bisim_reduce_host(n, m, num_act, src_h or None, act_h or None, dst_h or None,
+                                  init_h or None, out_h or None,
+                                  ctypes.byref(opts) if opts is not None else None, stream or None,
+                                  ctypes.byref(st))
+    _check(rc, "bisim_reduce_host")
+    return st
+
+
+def bisim_version() -> int:
+    return int(load().bisim_version())
+
+
+# --------------------------------------------------- torch conveniences
+
+
+def _stream_ptr(stream) -> int:
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+class Plan:
+    """A plan over device tensors (int32, contiguous, on the current device)."""
+
+    def __init__(self, n, num_act, src, act, dst, init=None, opts=None, stream=None):
+        import torch
+
+        for t in (src, act, dst, init):
+            if t is not None:
+                assert t.is_cuda and t.dtype == torch.int32 and t.is_contiguous()
+        self.n = int(n)
+        self.m = int(src.shape[0])
+        self.num_act = int(num_act)
+        self.opts = opts if opts is not None else make_opts()
+        self.stream = stream
+        self._keep = (src, act, dst, init)
+        self.handle = bisim_plan(self.n, self.m, self.num_act, src.data_ptr(),
+                                 act.data_ptr() if act is not None else None, dst.data_ptr(),
+                                 init.data_ptr() if init is not None else None, self.opts,
+                                 _stream_ptr(stream))
+        self._keep = None  # inputs are only read during planning
+
+    def refine(self, out=None):
+        import torch
+
+        if out is None:
+            out = torch.empty(max(self.n, 1), dtype=torch.int32, device="cuda")
+        st = bisim_refine(self.handle, out.data_ptr())
+        return out[: self.n], st
+
+    def close(self):
+        bisim_plan_destroy(self.handle)
+        self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            if self.handle:
+                self.close()
+        except Exception:
+            pass
+
+
+def reduce(lts, opts=None, device="cuda", return_stats=False):
+    """Coarsest bisimulation partition of an `lts_gen.LTS` on the GPU;
+    returns a numpy int32 array of canonical block ids."""
+    import torch
+
+    def dev(a):
+        return None if a is None else torch.from_numpy(a).to(device)
+
+    src, act, dst, init = dev(lts.src), dev(lts.act), dev(lts.dst), dev(lts.init)
+    with Plan(lts.n, lts.num_act, src, act, dst, init, opts) as p:
+        out, st = p.refine()
+        res = out.cpu().numpy()
+    return (res, st) if return_stats else res

@@ -1,0 +1,198 @@
+// C ABI entry points (include/bisim.h): argument checks, plan lifetime,
+// engine selection, device timing and error reporting.
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "plan.cuh"
+
+namespace bisim {
+
+static thread_local std::string g_last_error;
+thread_local long long g_launches = 0;
+
+void set_last_error(const std::string& s) { g_last_error = s; }
+
+}  // namespace bisim
+
+using namespace bisim;
+
+static int choose_engine(const bisim_plan_s* p) {
+    int e = p->opts.engine;
+    if (e == BISIM_ENGINE_DENSE || e == BISIM_ENGINE_FRONTIER) return e;
+    return BISIM_ENGINE_DENSE;
+}
+
+static void fill_static_stats(const bisim_plan_s* p, bisim_stats* s) {
+    s->n = p->n;
+    s->m = p->m;
+    s->num_act = p->A;
+    s->mark_length = p->L;
+    s->pre_rounds = p->pre_rounds;
+    s->initial_blocks = p->initial_blocks;
+    s->t_plan_ms = p->t_plan_ms;
+    s->t_pre_ms = p->t_pre_ms;
+}
+
+extern "C" {
+
+const char* bisim_strerror(int code) {
+    switch (code) {
+        case BISIM_OK: return "ok";
+        case BISIM_EINVAL: return "invalid argument or out-of-range array entry";
+        case BISIM_ENOMEM: return "out of device memory";
+        case BISIM_ECUDA: return "CUDA runtime error";
+        case BISIM_EROUNDS: return "round cap exceeded";
+        case BISIM_ETIMEOUT: return "grid barrier wait timed out";
+        case BISIM_ENOTSUP: return "not supported";
+        default: return "unknown error";
+    }
+}
+
+const char* bisim_last_error(void) { return g_last_error.c_str(); }
+
+int32_t bisim_version(void) { return 100; }
+
+int bisim_plan(int32_t n, int64_t m, int32_t num_act, const int32_t* src, const int32_t* act,
+               const int32_t* dst, const int32_t* init_block, const bisim_opts* opts, void* stream,
+               bisim_plan_t* out) {
+    if (!out) {
+        set_last_error("out is NULL");
+        return BISIM_EINVAL;
+    }
+    *out = nullptr;
+    if (n < 0 || m < 0 || m > 0x7fffffffll || num_act < 1 || (m > 0 && (!src || !dst))) {
+        set_last_error("bad scalar argument (need 0 <= n, 0 <= m < 2^31, num_act >= 1, src/dst)");
+        return BISIM_EINVAL;
+    }
+    if (n == 0 && m > 0) {
+        set_last_error("transitions given for an LTS without states");
+        return BISIM_EINVAL;
+    }
+    bisim_plan_s* p = new (std::nothrow) bisim_plan_s();
+    if (!p) return BISIM_ENOMEM;
+    p->n = n;
+    p->m = m;
+    p->A = num_act;
+    p->st = (cudaStream_t)stream;
+    if (opts) p->opts = *opts;
+    int dev = 0;
+    int rc = BISIM_OK;
+    do {
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaMallocHost(&p->ctrl_h, sizeof(bisim_ctrl));
+        if (e == cudaSuccess) e = cudaEventCreate(&p->ev0);
+        if (e == cudaSuccess) e = cudaEventCreate(&p->ev1);
+        if (e == cudaSuccess) e = cudaEventCreate(&p->evk0);
+        if (e == cudaSuccess) e = cudaEventCreate(&p->evk1);
+        if (e != cudaSuccess) {
+            set_last_error(std::string("device setup: ") + cudaGetErrorString(e));
+            rc = BISIM_ECUDA;
+            break;
+        }
+        e = cudaEventRecord(p->ev0, p->st);
+        if (e != cudaSuccess) {
+            set_last_error(std::string("cudaEventRecord: ") + cudaGetErrorString(e));
+            rc = BISIM_ECUDA;
+            break;
+        }
+        g_launches = 0;
+        rc = plan_build(p, src, act, dst, init_block);
+        p->plan_launches = g_launches;
+        if (rc) break;
+        float ms = 0;
+        e = cudaEventRecord(p->ev1, p->st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(p->ev1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, p->ev0, p->ev1);
+        if (e != cudaSuccess) {
+            set_last_error(std::string("plan timing: ") + cudaGetErrorString(e));
+            rc = BISIM_ECUDA;
+            break;
+        }
+        p->t_plan_ms = ms;
+    } while (0);
+    if (rc) {
+        cudaStreamSynchronize(p->st);
+        delete p;
+        return rc;
+    }
+    *out = p;
+    return BISIM_OK;
+}
+
+int bisim_refine(bisim_plan_t p, int32_t* out_block, bisim_stats* stats) {
+    if (!p || (p->n > 0 && !out_block)) {
+        set_last_error("plan or out_block is NULL");
+        return BISIM_EINVAL;
+    }
+    bisim_stats s;
+    std::memset(&s, 0, sizeof(s));
+    fill_static_stats(p, &s);
+    if (p->n == 0) {
+        if (stats) *stats = s;
+        return BISIM_OK;
+    }
+    BISIM_CUDA_TRY(cudaEventRecord(p->ev0, p->st));
+    int engine = choose_engine(p);
+    g_launches = 0;
+    int rc = engine == BISIM_ENGINE_DENSE ? refine_dense(p, &s) : refine_frontier(p, &s);
+    if (rc == BISIM_OK) rc = write_output(p, out_block, &s.num_blocks);
+    s.launches = p->plan_launches + g_launches;
+    if (rc == BISIM_OK) {
+        float ms = 0;
+        BISIM_CUDA_TRY(cudaEventRecord(p->ev1, p->st));
+        BISIM_CUDA_TRY(cudaEventSynchronize(p->ev1));
+        BISIM_CUDA_TRY(cudaEventElapsedTime(&ms, p->ev0, p->ev1));
+        s.t_refine_ms = ms;
+    }
+    p->last = s;
+    if (stats) *stats = s;
+    return rc;
+}
+
+void bisim_plan_destroy(bisim_plan_t p) {
+    if (!p) return;
+    cudaStreamSynchronize(p->st);
+    delete p;
+}
+
+int bisim_reduce_host(int32_t n, int64_t m, int32_t num_act, const int32_t* src_h,
+                      const int32_t* act_h, const int32_t* dst_h, const int32_t* init_h,
+                      int32_t* out_block_h, const bisim_opts* opts, void* stream,
+                      bisim_stats* stats) {
+    if (n < 0 || m < 0 || m > 0x7fffffffll || (m > 0 && (!src_h || !dst_h)) ||
+        (n > 0 && !out_block_h)) {
+        set_last_error("bad argument");
+        return BISIM_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    DevMem dsrc, dact, ddst, dinit, dout;
+    BISIM_TRY(dsrc.alloc(4 * (size_t)m, st));
+    BISIM_TRY(ddst.alloc(4 * (size_t)m, st));
+    BISIM_TRY(dout.alloc(4 * (size_t)n, st));
+    if (m) {
+        BISIM_CUDA_TRY(cudaMemcpyAsync(dsrc.p, src_h, 4 * (size_t)m, cudaMemcpyHostToDevice, st));
+        BISIM_CUDA_TRY(cudaMemcpyAsync(ddst.p, dst_h, 4 * (size_t)m, cudaMemcpyHostToDevice, st));
+    }
+    if (act_h) {
+        BISIM_TRY(dact.alloc(4 * (size_t)m, st));
+        if (m) BISIM_CUDA_TRY(cudaMemcpyAsync(dact.p, act_h, 4 * (size_t)m, cudaMemcpyHostToDevice, st));
+    }
+    if (init_h) {
+        BISIM_TRY(dinit.alloc(4 * (size_t)n, st));
+        if (n) BISIM_CUDA_TRY(cudaMemcpyAsync(dinit.p, init_h, 4 * (size_t)n, cudaMemcpyHostToDevice, st));
+    }
+    bisim_plan_t plan = nullptr;
+    int rc = bisim_plan(n, m, num_act, dsrc.as<int32_t>(), act_h ? dact.as<int32_t>() : nullptr,
+                        ddst.as<int32_t>(), init_h ? dinit.as<int32_t>() : nullptr, opts, stream, &plan);
+    if (rc) return rc;
+    rc = bisim_refine(plan, dout.as<int32_t>(), stats);
+    bisim_plan_destroy(plan);
+    if (rc) return rc;
+    if (n) BISIM_CUDA_TRY(cudaMemcpyAsync(out_block_h, dout.p, 4 * (size_t)n, cudaMemcpyDeviceToHost, st));
+    BISIM_CUDA_TRY(cudaStreamSynchronize(st));
+    return BISIM_OK;
+}
+
+}  // extern "C"

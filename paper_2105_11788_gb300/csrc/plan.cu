@@ -1,0 +1,489 @@
+// Plan construction (everything before the main while-loop):
+//  - range validation of the input arrays;
+//  - sort of the transitions by (source, label) and the mark-slot layout of
+//    Section 4.1.1: a new (source, label) pair starts where Algorithm 4 would
+//    see a source change or an action switch, so the running count of pair
+//    starts gives slot = off(source) + order for every transition, nr_marks
+//    is the number of pairs of a state and off their exclusive prefix sum;
+//  - the incoming-transition CSR by target, every entry carrying (source,
+//    slot), built with a second stable radix sort;
+//  - initial leaders (Algorithm 2, lines 1-6, priority rule: the smallest
+//    member of each initial block);
+//  - action-set preprocessing (Algorithm 5): for every label that occurs, in
+//    increasing order, mark the sources of that label's transitions and split
+//    every block into marked / unmarked parts, the part not containing the
+//    leader getting its smallest member as new leader.
+// Plus the canonical output step shared by both engines.
+#include <algorithm>
+
+#include "plan.cuh"
+
+using namespace bisim;
+
+namespace {
+
+constexpr int T = 256;
+
+__global__ void k_validate(const int32_t* __restrict__ src, const int32_t* __restrict__ act,
+                           const int32_t* __restrict__ dst, const int32_t* __restrict__ init,
+                           int32_t n, int64_t m, int32_t A, int* status, uint32_t* used) {
+    const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
+    int bad = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gsz) {
+        int32_t s = src[i], d = dst[i];
+        int32_t a = act ? act[i] : 0;
+        if ((unsigned)s >= (unsigned)n || (unsigned)d >= (unsigned)n || (unsigned)a >= (unsigned)A) {
+            bad = 1;
+        } else if (used[a] == 0) {
+            used[a] = 1;  // benign same-value store
+        }
+    }
+    if (init)
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gsz)
+            if ((unsigned)init[i] >= (unsigned)n) bad = 1;
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, ST_INVALID);
+}
+
+template <typename K>
+__global__ void k_make_keys(const int32_t* __restrict__ src, const int32_t* __restrict__ act,
+                            const int32_t* __restrict__ dst, int64_t m, int32_t A, K* keys,
+                            uint32_t* vals) {
+    const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gsz) {
+        keys[i] = (K)src[i] * (K)A + (K)(act ? act[i] : 0);
+        vals[i] = (uint32_t)dst[i];
+    }
+}
+
+// flag[i] = 1 where a new (source, label) pair starts in sorted order
+template <typename K>
+__global__ void k_pair_flags(const K* __restrict__ keys, int64_t m, uint32_t* flags) {
+    const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gsz)
+        flags[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1u : 0u;
+}
+
+// slot of every sorted transition, the owner and label of every slot, the
+// in-CSR key (target) and payload (source << 32 | slot), and the in-degree.
+template <typename K>
+__global__ void k_slots(const K* __restrict__ keys, const uint32_t* __restrict__ dst_sorted,
+                        const uint32_t* __restrict__ excl, int64_t m, int32_t A,
+                        int32_t* slot_src, int32_t* slot_act, uint32_t* tkey, uint64_t* tval,
+                        uint32_t* nr_cnt, uint32_t* indeg) {
+    const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gsz) {
+        const K k = keys[i];
+        const bool first = (i == 0 || k != keys[i - 1]);
+        const uint32_t slot = first ? excl[i] : excl[i] - 1u;
+        const int32_t s = (int32_t)(k / (K)A);
+        if (first) {
+            slot_src[slot] = s;
+            slot_act[slot] = (int32_t)(k % (K)A);
+            atomicAdd(&nr_cnt[s], 1u);
+        }
+        const uint32_t d = dst_sorted[i];
+        tkey[i] = d;
+        tval[i] = ((uint64_t)(uint32_t)s << 32) | slot;
+        atomicAdd(&indeg[d], 1u);
+    }
+}
+
+__global__ void k_fill_i32(int32_t* p, int64_t n, int32_t v) {
+    const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gsz) p[i] = v;
+}
+
+__global__ void k_init_min(const int32_t* __restrict__ init, int32_t n, int32_t* nl) {
+    const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gsz)
+        atomicMin(&nl[init[i]], (int32_t)i);
+}
+
+__global__ void k_init_relabel(const int32_t* __restrict__ init, int32_t n,
+                               const int32_t* __restrict__ nl, int32_t* block) {
+    const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gsz)
+        block[i] = nl[init[i]];
+}
+
+__device__ __forceinline__ unsigned long long elect_key(uint32_t stamp, int32_t s) {
+    // newer stamps compare smaller, so atomicMin keeps this round's smallest state
+    return ((unsigned long long)(0xffffffffu - stamp) << 32) | (uint32_t)s;
+}
+
+struct LabelArgs {
+    int32_t n;
+    int64_t L;
+    int32_t n_labels;
+    const int32_t* labels;
+    const int32_t* slot_src;
+    const int32_t* slot_act;
+    int32_t* block;
+    uint32_t* lmark;
+    unsigned long long* nl64;
+    uint8_t* split;
+    uint32_t stamp0;
+    GridBarrier gb;
+};
+
+// Algorithm 5: one round per label, three grid barriers per round.
+__global__ void k_label_rounds(LabelArgs a) {
+    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
+    unsigned long long tgt = 0;
+    for (int li = 0; li < a.n_labels; li++) {
+        const int32_t lab = a.labels[li];
+        const uint32_t stamp = a.stamp0 + (uint32_t)li + 1u;
+        for (int64_t k = gtid; k < a.L; k += gsz)
+            if (a.slot_act[k] == lab) a.lmark[a.slot_src[k]] = stamp;
+        if (!grid_sync(a.gb, tgt)) return;
+        for (int64_t s = gtid; s < a.n; s += gsz) {
+            const int32_t b = a.block[s];
+            const bool ms = ldcg(&a.lmark[s]) == stamp;
+            const bool mb = ldcg(&a.lmark[b]) == stamp;
+            const uint8_t sp = ms != mb;
+            a.split[s] = sp;
+            if (sp) atomicMin(&a.nl64[b], elect_key(stamp, (int32_t)s));
+        }
+        if (!grid_sync(a.gb, tgt)) return;
+        for (int64_t s = gtid; s < a.n; s += gsz)
+            if (a.split[s]) a.block[s] = (int32_t)(uint32_t)ldcg(&a.nl64[a.block[s]]);
+        if (!grid_sync(a.gb, tgt)) return;
+    }
+}
+
+__global__ void k_count_leaders(const int32_t* __restrict__ block, int32_t n,
+                                unsigned long long* count) {
+    const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
+    unsigned c = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gsz)
+        c += block[i] == (int32_t)i;
+    c = __reduce_add_sync(0xffffffffu, c);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, (unsigned long long)c);
+}
+
+// canonical output
+__global__ void k_first_min(const int32_t* __restrict__ block, int32_t n, int32_t* first) {
+    const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gsz)
+        atomicMin(&first[block[i]], (int32_t)i);
+}
+__global__ void k_is_first(const int32_t* __restrict__ block, const int32_t* __restrict__ first,
+                           int32_t n, uint32_t* flag) {
+    const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gsz)
+        flag[i] = first[block[i]] == (int32_t)i;
+}
+__global__ void k_gather_ids(const int32_t* __restrict__ block, const int32_t* __restrict__ first,
+                             const uint32_t* __restrict__ rank, int32_t n, int32_t* out) {
+    const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gsz)
+        out[i] = (int32_t)rank[first[block[i]]];
+}
+
+}  // namespace
+
+bisim_plan_s::~bisim_plan_s() {
+    if (ctrl_h) cudaFreeHost(ctrl_h);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    if (evk0) cudaEventDestroy(evk0);
+    if (evk1) cudaEventDestroy(evk1);
+}
+
+namespace bisim {
+
+int read_ctrl(bisim_plan_s* p) {
+    BISIM_CUDA_TRY(cudaMemcpyAsync(p->ctrl_h, p->ctrl.p, sizeof(bisim_ctrl), cudaMemcpyDeviceToHost,
+                                   p->st));
+    BISIM_CUDA_TRY(cudaStreamSynchronize(p->st));
+    return BISIM_OK;
+}
+
+int reserve_stamps(bisim_plan_s* p, int64_t rounds, uint32_t* base) {
+    if ((uint64_t)p->stamp + (uint64_t)rounds + 2 >= 0xffffffffull) {
+        if (p->L) BISIM_CUDA_TRY(cudaMemsetAsync(p->mark.p, 0, sizeof(uint32_t) * p->L, p->st));
+        if (p->n) {
+            BISIM_CUDA_TRY(cudaMemsetAsync(p->lmark.p, 0, sizeof(uint32_t) * p->n, p->st));
+            BISIM_CUDA_TRY(cudaMemsetAsync(p->nl64.p, 0xff, sizeof(uint64_t) * p->n, p->st));
+            if (p->frontier_ready)
+                BISIM_CUDA_TRY(cudaMemsetAsync(p->touched.p, 0, sizeof(uint32_t) * p->n, p->st));
+        }
+        p->stamp = 0;
+    }
+    *base = p->stamp;
+    return BISIM_OK;
+}
+
+int launch_persistent(const void* fn, void** args, int threads, bisim_plan_s* p, int* grid_out) {
+    int occ = 0;
+    BISIM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, 0));
+    if (occ < 1) {
+        set_last_error("persistent kernel does not fit on an SM");
+        return BISIM_ECUDA;
+    }
+    int per_sm = p->opts.ctas_per_sm > 0 ? p->opts.ctas_per_sm : 1;
+    per_sm = std::min(per_sm, occ);
+    int grid = p->sm_count * per_sm;
+    *grid_out = grid;
+    BISIM_CUDA_TRY(cudaEventRecord(p->evk0, p->st));
+    BISIM_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(threads), args, 0, p->st));
+    BISIM_LAUNCHED();
+    BISIM_CUDA_TRY(cudaEventRecord(p->evk1, p->st));
+    return BISIM_OK;
+}
+
+int persistent_ms(bisim_plan_s* p, double* ms) {
+    float f = 0;
+    BISIM_CUDA_TRY(cudaEventSynchronize(p->evk1));
+    BISIM_CUDA_TRY(cudaEventElapsedTime(&f, p->evk0, p->evk1));
+    *ms = f;
+    return BISIM_OK;
+}
+
+int plan_build(bisim_plan_s* p, const int32_t* src, const int32_t* act, const int32_t* dst,
+               const int32_t* init) {
+    const int32_t n = p->n;
+    const int64_t m = p->m;
+    const int32_t A = p->A;
+    cudaStream_t st = p->st;
+
+    BISIM_TRY(p->ctrl.alloc(sizeof(bisim_ctrl), st));
+    BISIM_CUDA_TRY(cudaMemsetAsync(p->ctrl.p, 0, sizeof(bisim_ctrl), st));
+    int* status = &p->ctrl.as<bisim_ctrl>()->status;
+
+    // a1: validation and the set of labels that occur
+    DevMem used;
+    BISIM_TRY(used.alloc(sizeof(uint32_t) * (size_t)A, st));
+    BISIM_CUDA_TRY(cudaMemsetAsync(used.p, 0, sizeof(uint32_t) * (size_t)A, st));
+    k_validate<<<grid_for(std::max<int64_t>(m, n), T), T, 0, st>>>(src, act, dst, init, n, m, A,
+                                                                   status, used.as<uint32_t>());
+    BISIM_LAUNCHED();
+    BISIM_CUDA_TRY(cudaGetLastError());
+    std::vector<uint32_t> used_h((size_t)A);
+    BISIM_CUDA_TRY(cudaMemcpyAsync(used_h.data(), used.p, sizeof(uint32_t) * (size_t)A,
+                                   cudaMemcpyDeviceToHost, st));
+    BISIM_TRY(read_ctrl(p));
+    if (p->ctrl_h->status & ST_INVALID) {
+        set_last_error("an input array entry is out of range");
+        return BISIM_EINVAL;
+    }
+    std::vector<int32_t> labels_h;
+    for (int32_t a = 0; a < A; a++)
+        if (used_h[a]) labels_h.push_back(a);
+    p->pre_rounds = (int64_t)labels_h.size();
+
+    // a2: sort by (source, label); slots, off, nr
+    const uint64_t keyspace = (uint64_t)n * (uint64_t)A;
+    const bool wide = keyspace > 0xffffffffull;
+    const int kbits = ceil_log2_u64(keyspace);
+    const size_t ksz = wide ? 8 : 4;
+    DevMem keys, keys_alt, vals, vals_alt;
+    BISIM_TRY(keys.alloc(ksz * (size_t)m, st));
+    BISIM_TRY(keys_alt.alloc(ksz * (size_t)m, st));
+    BISIM_TRY(vals.alloc(4 * (size_t)m, st));
+    BISIM_TRY(vals_alt.alloc(4 * (size_t)m, st));
+    const unsigned gm = grid_for(m, T);
+    bool alt = false;
+    if (wide) {
+        k_make_keys<uint64_t><<<gm, T, 0, st>>>(src, act, dst, m, A, keys.as<uint64_t>(),
+                                                vals.as<uint32_t>());
+        BISIM_LAUNCHED();
+        BISIM_CUDA_TRY(cudaGetLastError());
+        BISIM_TRY(radix_sort_pairs<uint64_t, uint32_t>(keys.as<uint64_t>(), vals.as<uint32_t>(),
+                                                       keys_alt.as<uint64_t>(),
+                                                       vals_alt.as<uint32_t>(), m, kbits, st, &alt));
+    } else {
+        k_make_keys<uint32_t><<<gm, T, 0, st>>>(src, act, dst, m, A, keys.as<uint32_t>(),
+                                                vals.as<uint32_t>());
+        BISIM_LAUNCHED();
+        BISIM_CUDA_TRY(cudaGetLastError());
+        BISIM_TRY(radix_sort_pairs<uint32_t, uint32_t>(keys.as<uint32_t>(), vals.as<uint32_t>(),
+                                                       keys_alt.as<uint32_t>(),
+                                                       vals_alt.as<uint32_t>(), m, kbits, st, &alt));
+    }
+    void* skeys = alt ? keys_alt.p : keys.p;
+    uint32_t* sdst = alt ? vals_alt.as<uint32_t>() : vals.as<uint32_t>();
+
+    DevMem flags, Ldev;
+    BISIM_TRY(flags.alloc(4 * (size_t)m, st));
+    BISIM_TRY(Ldev.alloc(4, st));
+    if (wide)
+        k_pair_flags<uint64_t><<<gm, T, 0, st>>>((const uint64_t*)skeys, m, flags.as<uint32_t>());
+    else
+        k_pair_flags<uint32_t><<<gm, T, 0, st>>>((const uint32_t*)skeys, m, flags.as<uint32_t>());
+    BISIM_LAUNCHED();
+    BISIM_CUDA_TRY(cudaGetLastError());
+    BISIM_TRY(scan_exclusive_u32(flags.as<uint32_t>(), flags.as<uint32_t>(), m, Ldev.as<uint32_t>(), st));
+    uint32_t L_h = 0;
+    BISIM_CUDA_TRY(cudaMemcpyAsync(&L_h, Ldev.p, 4, cudaMemcpyDeviceToHost, st));
+    BISIM_CUDA_TRY(cudaStreamSynchronize(st));
+    p->L = m ? (int64_t)L_h : 0;
+    const int64_t L = p->L;
+
+    BISIM_TRY(p->slot_src.alloc(4 * (size_t)L, st));
+    BISIM_TRY(p->slot_act.alloc(4 * (size_t)L, st));
+    BISIM_TRY(p->off.alloc(4 * ((size_t)n + 1), st));
+    BISIM_TRY(p->in_ptr.alloc(4 * ((size_t)n + 1), st));
+    BISIM_CUDA_TRY(cudaMemsetAsync(p->off.p, 0, 4 * ((size_t)n + 1), st));
+    BISIM_CUDA_TRY(cudaMemsetAsync(p->in_ptr.p, 0, 4 * ((size_t)n + 1), st));
+    DevMem tkey, tkey_alt, tval, tval_alt;
+    BISIM_TRY(tkey.alloc(4 * (size_t)m, st));
+    BISIM_TRY(tkey_alt.alloc(4 * (size_t)m, st));
+    BISIM_TRY(tval.alloc(8 * (size_t)m, st));
+    BISIM_TRY(tval_alt.alloc(8 * (size_t)m, st));
+    if (wide)
+        k_slots<uint64_t><<<gm, T, 0, st>>>((const uint64_t*)skeys, sdst, flags.as<uint32_t>(), m, A,
+                                            p->slot_src.as<int32_t>(), p->slot_act.as<int32_t>(),
+                                            tkey.as<uint32_t>(), tval.as<uint64_t>(),
+                                            p->off.as<uint32_t>(), p->in_ptr.as<uint32_t>());
+    else
+        k_slots<uint32_t><<<gm, T, 0, st>>>((const uint32_t*)skeys, sdst, flags.as<uint32_t>(), m, A,
+                                            p->slot_src.as<int32_t>(), p->slot_act.as<int32_t>(),
+                                            tkey.as<uint32_t>(), tval.as<uint64_t>(),
+                                            p->off.as<uint32_t>(), p->in_ptr.as<uint32_t>());
+    BISIM_LAUNCHED();
+    BISIM_CUDA_TRY(cudaGetLastError());
+    keys.release(); keys_alt.release(); vals.release(); vals_alt.release(); flags.release();
+    // off = exclusive sum of nr_marks (off[n] = L); in_ptr likewise over in-degrees
+    BISIM_TRY(scan_exclusive_u32(p->off.as<uint32_t>(), p->off.as<uint32_t>(), (int64_t)n + 1,
+                                 nullptr, st));
+    BISIM_TRY(scan_exclusive_u32(p->in_ptr.as<uint32_t>(), p->in_ptr.as<uint32_t>(), (int64_t)n + 1,
+                                 nullptr, st));
+
+    // a3: incoming transitions grouped by target (stable: by source, label inside)
+    bool alt2 = false;
+    BISIM_TRY(radix_sort_pairs<uint32_t, uint64_t>(tkey.as<uint32_t>(), tval.as<uint64_t>(),
+                                                   tkey_alt.as<uint32_t>(), tval_alt.as<uint64_t>(),
+                                                   m, ceil_log2_u64((uint64_t)n), st, &alt2));
+    if (alt2) {
+        std::swap(tval.p, tval_alt.p);
+    }
+    tkey.release(); tkey_alt.release(); tval_alt.release();
+    // keep the sorted payload as in_edge
+    std::swap(p->in_edge.p, tval.p);
+    std::swap(p->in_edge.bytes, tval.bytes);
+    p->in_edge.st = st;
+
+    if (!labels_h.empty()) {
+        BISIM_TRY(p->labels.alloc(4 * labels_h.size(), st));
+        BISIM_CUDA_TRY(cudaMemcpyAsync(p->labels.p, labels_h.data(), 4 * labels_h.size(),
+                                       cudaMemcpyHostToDevice, st));
+    }
+
+    // refinement state
+    BISIM_TRY(p->block.alloc(4 * (size_t)n, st));
+    BISIM_TRY(p->block0.alloc(4 * (size_t)n, st));
+    BISIM_TRY(p->mark.alloc(4 * (size_t)L, st));
+    BISIM_TRY(p->lmark.alloc(4 * (size_t)n, st));
+    BISIM_TRY(p->nl64.alloc(8 * (size_t)n, st));
+    BISIM_TRY(p->unstable.alloc(4 * (size_t)n, st));
+    BISIM_TRY(p->split.alloc((size_t)n, st));
+    if (L) BISIM_CUDA_TRY(cudaMemsetAsync(p->mark.p, 0, 4 * (size_t)L, st));
+    if (n) {
+        BISIM_CUDA_TRY(cudaMemsetAsync(p->lmark.p, 0, 4 * (size_t)n, st));
+        BISIM_CUDA_TRY(cudaMemsetAsync(p->nl64.p, 0xff, 8 * (size_t)n, st));
+    }
+    p->stamp = 0;
+
+    // a4: initial leaders
+    const unsigned gn = grid_for(n, T);
+    if (n) {
+        if (init) {
+            int32_t* nl = p->block0.as<int32_t>();  // scratch for the election
+            k_fill_i32<<<gn, T, 0, st>>>(nl, n, NONE);
+            BISIM_LAUNCHED();
+            k_init_min<<<gn, T, 0, st>>>(init, n, nl);
+            BISIM_LAUNCHED();
+            k_init_relabel<<<gn, T, 0, st>>>(init, n, nl, p->block.as<int32_t>());
+            BISIM_LAUNCHED();
+        } else {
+            BISIM_CUDA_TRY(cudaMemsetAsync(p->block.p, 0, 4 * (size_t)n, st));
+        }
+        BISIM_CUDA_TRY(cudaGetLastError());
+    }
+
+    // a5: action-set preprocessing
+    if (n && p->pre_rounds > 0) {
+        uint32_t base;
+        BISIM_TRY(reserve_stamps(p, p->pre_rounds, &base));
+        BISIM_CUDA_TRY(cudaMemsetAsync(&p->ctrl.as<bisim_ctrl>()->barrier, 0, 8, st));
+        LabelArgs a;
+        a.n = n;
+        a.L = L;
+        a.n_labels = (int32_t)p->pre_rounds;
+        a.labels = p->labels.as<int32_t>();
+        a.slot_src = p->slot_src.as<int32_t>();
+        a.slot_act = p->slot_act.as<int32_t>();
+        a.block = p->block.as<int32_t>();
+        a.lmark = p->lmark.as<uint32_t>();
+        a.nl64 = p->nl64.as<unsigned long long>();
+        a.split = p->split.as<uint8_t>();
+        a.stamp0 = base;
+        a.gb.counter = &p->ctrl.as<bisim_ctrl>()->barrier;
+        a.gb.status = status;
+        a.gb.timeout_ns = (unsigned long long)(p->opts.timeout_ms > 0 ? p->opts.timeout_ms : 2000) * 1000000ull;
+        void* args[] = {&a};
+        int grid = 0;
+        BISIM_TRY(launch_persistent((const void*)k_label_rounds, args, 512, p, &grid));
+        BISIM_TRY(persistent_ms(p, &p->t_pre_ms));
+        p->stamp = base + (uint32_t)p->pre_rounds;
+    }
+    if (n) BISIM_CUDA_TRY(cudaMemcpyAsync(p->block0.p, p->block.p, 4 * (size_t)n,
+                                          cudaMemcpyDeviceToDevice, st));
+    // |pi_0'|
+    {
+        unsigned long long* cnt = &p->ctrl.as<bisim_ctrl>()->q_tail;
+        BISIM_CUDA_TRY(cudaMemsetAsync(cnt, 0, 8, st));
+        if (n) {
+            k_count_leaders<<<gn, T, 0, st>>>(p->block0.as<int32_t>(), n, cnt);
+            BISIM_LAUNCHED();
+        }
+        BISIM_CUDA_TRY(cudaGetLastError());
+        BISIM_TRY(read_ctrl(p));
+        p->initial_blocks = (int64_t)p->ctrl_h->q_tail;
+        int code = status_to_code(p->ctrl_h->status);
+        if (code) {
+            set_last_error("preprocessing rounds failed");
+            return code;
+        }
+    }
+    return BISIM_OK;
+}
+
+int write_output(bisim_plan_s* p, int32_t* out, int64_t* num_blocks) {
+    const int32_t n = p->n;
+    cudaStream_t st = p->st;
+    if (n == 0) {
+        *num_blocks = 0;
+        return BISIM_OK;
+    }
+    const int32_t* block = p->block.as<int32_t>();
+    const unsigned gn = grid_for(n, T);
+    DevMem first, flag, tot;
+    BISIM_TRY(first.alloc(4 * (size_t)n, st));
+    BISIM_TRY(flag.alloc(4 * (size_t)n, st));
+    BISIM_TRY(tot.alloc(4, st));
+    k_fill_i32<<<gn, T, 0, st>>>(first.as<int32_t>(), n, NONE);
+    BISIM_LAUNCHED();
+    k_first_min<<<gn, T, 0, st>>>(block, n, first.as<int32_t>());
+    BISIM_LAUNCHED();
+    k_is_first<<<gn, T, 0, st>>>(block, first.as<int32_t>(), n, flag.as<uint32_t>());
+    BISIM_LAUNCHED();
+    BISIM_CUDA_TRY(cudaGetLastError());
+    BISIM_TRY(scan_exclusive_u32(flag.as<uint32_t>(), flag.as<uint32_t>(), n, tot.as<uint32_t>(), st));
+    if (p->opts.raw_labels)
+        BISIM_CUDA_TRY(cudaMemcpyAsync(out, block, 4 * (size_t)n, cudaMemcpyDeviceToDevice, st));
+    else {
+        k_gather_ids<<<gn, T, 0, st>>>(block, first.as<int32_t>(), flag.as<uint32_t>(), n, out);
+        BISIM_LAUNCHED();
+    }
+    BISIM_CUDA_TRY(cudaGetLastError());
+    uint32_t nb = 0;
+    BISIM_CUDA_TRY(cudaMemcpyAsync(&nb, tot.p, 4, cudaMemcpyDeviceToHost, st));
+    BISIM_CUDA_TRY(cudaStreamSynchronize(st));
+    *num_blocks = nb;
+    return BISIM_OK;
+}
+
+}  // namespace bisim

@@ -1,0 +1,100 @@
+// Internal plan object shared by the plan builder, the refinement engines
+// and the C ABI.
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+#include "prim.cuh"
+
+// Device control block: barrier counter, status word, splitter election
+// slots, worklist cursors and counters. Zeroed (then initialised) before
+// every persistent launch.
+struct bisim_ctrl {
+    unsigned long long barrier;  // grid barrier counter (monotonic)
+    int status;                  // ST_* bits
+    int sel[2];                  // priority splitter election, double-buffered by round parity
+    int pad0;
+    long long rounds;            // main-loop iterations incl. the final empty one
+    long long edges;             // incoming transitions walked by mark steps
+    long long states;            // states whose marks were compared
+    unsigned long long q_tail;   // FIFO worklist: total pushes so far
+    unsigned long long q_head0;  // FIFO worklist: pops before this launch
+    int n_touched[2];            // frontier: touched-block list lengths by round parity
+    int n_big[2];                // frontier: entries needing the whole grid
+    int n_mid[2];                // frontier: entries for one CTA
+    int pad1[2];
+};
+
+struct bisim_plan_s {
+    int32_t n = 0;
+    int64_t m = 0;
+    int32_t A = 1;
+    int64_t L = 0;
+    cudaStream_t st = nullptr;
+    bisim_opts opts{};
+    int sm_count = 0;
+
+    // read-only after planning
+    bisim::DevMem off;       // int32 [n+1]: first mark slot of each state; off[n] = L
+    bisim::DevMem in_ptr;    // int32 [n+1]: CSR of incoming transitions by target
+    bisim::DevMem in_edge;   // uint64 [m]: (source << 32) | mark slot of the transition
+    bisim::DevMem slot_src;  // int32 [L]: state owning each mark slot
+    bisim::DevMem slot_act;  // int32 [L]: label of each mark slot
+    bisim::DevMem labels;    // int32 [pre_rounds]: labels that occur, increasing
+    bisim::DevMem block0;    // int32 [n]: leader labels after preprocessing
+
+    // refinement state
+    bisim::DevMem block;     // int32 [n]: current leader label per state
+    bisim::DevMem mark;      // uint32 [L]: round stamp of the last mark of each slot
+    bisim::DevMem lmark;     // uint32 [n]: round stamp of the last label mark per state
+    bisim::DevMem nl64;      // uint64 [n]: new-leader election word per label
+    bisim::DevMem unstable;  // uint32 [n]: unstable flag per label
+    bisim::DevMem split;     // uint8 [n]
+    bisim::DevMem ctrl;      // bisim_ctrl
+    bisim_ctrl* ctrl_h = nullptr;  // pinned mirror
+
+    // frontier engine state (allocated on first use)
+    bool frontier_ready = false;
+    bisim::DevMem elems;     // int32 [2n]: two buffers of states grouped by block
+    bisim::DevMem which;     // uint8 [n]: buffer holding the members of each label
+    bisim::DevMem bbeg;      // int32 [n]: member range [bbeg, bend) of each label
+    bisim::DevMem bend;      // int32 [n]
+    bisim::DevMem cnt;       // uint64 [n]: per-label (kept, split) counters of a split in progress
+    bisim::DevMem done;      // int32 [n]: members processed of a split in progress
+    bisim::DevMem touched;   // uint32 [n]: round stamp of the last touch of each label
+    bisim::DevMem tlist;     // int32 [3 * n]: touched-label lists (small, CTA, grid)
+    bisim::DevMem queue;     // int32 [n]: FIFO ring of unstable labels
+
+    uint32_t stamp = 0;      // last round stamp used (marks are never cleared)
+    int64_t pre_rounds = 0;
+    int64_t initial_blocks = 0;
+    double t_plan_ms = 0;
+    double t_pre_ms = 0;
+    long long plan_launches = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;    // whole call
+    cudaEvent_t evk0 = nullptr, evk1 = nullptr;  // around the persistent kernel
+    bisim_stats last{};
+
+    ~bisim_plan_s();
+};
+
+namespace bisim {
+
+int plan_build(bisim_plan_s* p, const int32_t* src, const int32_t* act, const int32_t* dst,
+               const int32_t* init);
+int refine_dense(bisim_plan_s* p, bisim_stats* st);
+int refine_frontier(bisim_plan_s* p, bisim_stats* st);
+int write_output(bisim_plan_s* p, int32_t* out_block, int64_t* num_blocks);
+
+// Reserve `rounds` fresh stamps (resetting stamped arrays if the 32-bit
+// stamp space would wrap); returns the first stamp minus one.
+int reserve_stamps(bisim_plan_s* p, int64_t rounds, uint32_t* base);
+
+// Cooperative launch on one SM-multiple grid, bracketed by evk0 / evk1.
+int launch_persistent(const void* fn, void** args, int threads, bisim_plan_s* p, int* grid_out);
+// Device time between evk0 and evk1 of the last persistent launch.
+int persistent_ms(bisim_plan_s* p, double* ms);
+int read_ctrl(bisim_plan_s* p);
+
+}  // namespace bisim

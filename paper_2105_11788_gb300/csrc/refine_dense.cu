@@ -1,0 +1,186 @@
+// Dense refinement engine: the while-loop of Algorithm 3 (Algorithm 2 with
+// rcpp_alg2) in one persistent cooperative kernel, four grid barriers per
+// round, every concurrent write resolved by the priority rule:
+//   select   C := smallest label with unstable_C (block-reduced atomicMin)
+//   mark     for every state t with block_t = C and every incoming transition
+//            s -a-> t: mark[off(s) + order] := round stamp
+//   compare  split_s := some slot of s differs from the same slot of its
+//            leader block_s; split states atomicMin (round, s) into
+//            new_leader[block_s]
+//   relabel  split states move to new_leader[block_s]; both labels and C
+//            become unstable (C only for Algorithm 3)
+// Marks are round stamps, so no reset pass is needed; new_leader words carry
+// the round in their high half for the same reason. The loop ends in the
+// iteration that finds no unstable label, which is counted, as in Table 1.
+#include "plan.cuh"
+
+using namespace bisim;
+
+namespace {
+
+struct DenseArgs {
+    int32_t n;
+    const int32_t* __restrict__ off;
+    const int32_t* __restrict__ in_ptr;
+    const unsigned long long* __restrict__ in_edge;
+    int32_t* block;
+    uint32_t* mark;
+    unsigned long long* nl64;
+    uint32_t* unstable;
+    uint8_t* split;
+    bisim_ctrl* ctrl;
+    GridBarrier gb;
+    uint32_t stamp0;
+    int64_t round_cap;
+    int alg2;
+    int test_hook;
+};
+
+__device__ __forceinline__ unsigned long long elect_key(uint32_t stamp, int32_t s) {
+    return ((unsigned long long)(0xffffffffu - stamp) << 32) | (uint32_t)s;
+}
+
+__global__ void k_dense_init(const int32_t* __restrict__ block0, int32_t n, int32_t* block,
+                             uint32_t* unstable) {
+    const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gsz) {
+        int32_t b = block0[i];
+        block[i] = b;
+        unstable[i] = b == (int32_t)i;  // Algorithm 3, lines 1-3
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_dense_main(DenseArgs a) {
+    __shared__ int sh[32];
+    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
+    const int32_t n = a.n;
+    unsigned long long tgt = 0;
+    long long edges = 0, states = 0;
+    if (a.test_hook == 1 && blockIdx.x == 0) return;  // testing: never arrive
+    int64_t r = 0;
+    for (;;) {
+        r++;
+        const uint32_t stamp = a.stamp0 + (uint32_t)r;
+        // select: smallest unstable label
+        int loc = NONE;
+        for (int64_t i = gtid; i < n; i += gsz)
+            if (ldcg(&a.unstable[i])) {
+                loc = (int)i;
+                break;
+            }
+        const int bm = block_reduce_min(loc, sh);
+        if (threadIdx.x == 0 && bm != NONE) atomicMin(&a.ctrl->sel[r & 1], bm);
+        if (gtid == 0) a.ctrl->sel[(r + 1) & 1] = NONE;
+        if (!grid_sync(a.gb, tgt)) return;
+        const int C = ldcg(&a.ctrl->sel[r & 1]);
+        if (C < 0 || C >= n) break;  // no unstable label: C = bottom
+        if (r > a.round_cap) {
+            if (gtid == 0) atomicOr(&a.ctrl->status, ST_ROUNDS);
+            break;
+        }
+        // mark
+        if (gtid == 0) a.unstable[C] = 0;
+        for (int64_t t = gtid; t < n; t += gsz) {
+            if (ldcg(&a.block[t]) != C) continue;
+            const int32_t j1 = a.in_ptr[t + 1];
+            for (int32_t j = a.in_ptr[t]; j < j1; j++) a.mark[(uint32_t)a.in_edge[j]] = stamp;
+            edges += j1 - a.in_ptr[t];
+        }
+        if (!grid_sync(a.gb, tgt)) return;
+        // compare and elect
+        for (int64_t s = gtid; s < n; s += gsz) {
+            const int32_t b = a.block[s];
+            const int32_t o = a.off[s];
+            int32_t k = a.off[s + 1] - o;
+            const int32_t ob = a.off[b];
+            const int32_t kb = a.off[b + 1] - ob;
+            if (k != kb) {  // leader has a different label set: preprocessing broken
+                atomicOr(&a.ctrl->status, ST_INTERNAL);
+                k = min(k, kb);
+            }
+            bool sp = false;
+            for (int32_t q = 0; q < k; q++)
+                sp |= (ldcg(&a.mark[o + q]) == stamp) != (ldcg(&a.mark[ob + q]) == stamp);
+            states++;
+            a.split[s] = sp;
+            if (sp) atomicMin(&a.nl64[b], elect_key(stamp, (int32_t)s));
+        }
+        if (!grid_sync(a.gb, tgt)) return;
+        // relabel
+        for (int64_t s = gtid; s < n; s += gsz) {
+            if (!a.split[s]) continue;
+            const int32_t b = a.block[s];
+            const int32_t v = (int32_t)(uint32_t)ldcg(&a.nl64[b]);
+            a.block[s] = v;
+            a.unstable[b] = 1;
+            a.unstable[v] = 1;
+            if (!a.alg2) a.unstable[C] = 1;
+        }
+        if (!grid_sync(a.gb, tgt)) return;
+    }
+    if (edges) atomicAdd((unsigned long long*)&a.ctrl->edges, (unsigned long long)edges);
+    if (states) atomicAdd((unsigned long long*)&a.ctrl->states, (unsigned long long)states);
+    if (gtid == 0) a.ctrl->rounds = r;
+}
+
+}  // namespace
+
+namespace bisim {
+
+int refine_dense(bisim_plan_s* p, bisim_stats* stats) {
+    const int32_t n = p->n;
+    cudaStream_t st = p->st;
+    const int64_t cap = p->opts.round_cap > 0 ? p->opts.round_cap : 3ll * n + p->A + 2;
+    uint32_t base;
+    BISIM_TRY(reserve_stamps(p, cap + 1, &base));
+    bisim_ctrl* c = p->ctrl.as<bisim_ctrl>();
+    BISIM_CUDA_TRY(cudaMemsetAsync(c, 0, sizeof(bisim_ctrl), st));
+    BISIM_CUDA_TRY(cudaMemsetAsync(c->sel, 0x7f, sizeof(c->sel), st));  // 0x7f7f7f7f > any label
+    k_dense_init<<<grid_for(n, 256), 256, 0, st>>>(p->block0.as<int32_t>(), n, p->block.as<int32_t>(),
+                                                   p->unstable.as<uint32_t>());
+    BISIM_LAUNCHED();
+    BISIM_CUDA_TRY(cudaGetLastError());
+    DenseArgs a;
+    a.n = n;
+    a.off = p->off.as<int32_t>();
+    a.in_ptr = p->in_ptr.as<int32_t>();
+    a.in_edge = p->in_edge.as<unsigned long long>();
+    a.block = p->block.as<int32_t>();
+    a.mark = p->mark.as<uint32_t>();
+    a.nl64 = p->nl64.as<unsigned long long>();
+    a.unstable = p->unstable.as<uint32_t>();
+    a.split = p->split.as<uint8_t>();
+    a.ctrl = c;
+    a.gb.counter = &c->barrier;
+    a.gb.status = &c->status;
+    a.gb.timeout_ns = (unsigned long long)(p->opts.timeout_ms > 0 ? p->opts.timeout_ms : 2000) * 1000000ull;
+    a.stamp0 = base;
+    a.round_cap = cap;
+    a.alg2 = (p->opts.rcpp_alg2 && p->A == 1) ? 1 : 0;
+    a.test_hook = p->opts.test_hook;
+    void* args[] = {&a};
+    int threads = p->opts.threads > 0 ? p->opts.threads : 512;
+    int grid = 0;
+    BISIM_TRY(launch_persistent((const void*)k_dense_main, args, threads, p, &grid));
+    BISIM_TRY(read_ctrl(p));
+    if (stats) BISIM_TRY(persistent_ms(p, &stats->t_main_ms));
+    p->stamp = base + (uint32_t)std::min<long long>(p->ctrl_h->rounds + 1, cap + 1);
+    if (stats) {
+        stats->rounds = p->ctrl_h->rounds;
+        stats->edges_visited = p->ctrl_h->edges;
+        stats->states_visited = p->ctrl_h->states;
+        stats->engine = BISIM_ENGINE_DENSE;
+        stats->grid_ctas = grid;
+    }
+    int code = status_to_code(p->ctrl_h->status);
+    if (code) {
+        set_last_error(p->ctrl_h->status & ST_TIMEOUT ? "grid barrier wait timed out"
+                       : p->ctrl_h->status & ST_ROUNDS ? "round cap exceeded"
+                                                       : "internal consistency check failed");
+        return code;
+    }
+    return BISIM_OK;
+}
+
+}  // namespace bisim

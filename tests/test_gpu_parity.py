@@ -1,0 +1,218 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle,
+bit-exact on canonical block ids, plus the PRAM round counts and leader
+labels of the dense engine under the priority rule."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import defs
+from paper_2105_11788_gb300 import bisim, lts_gen
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+ENGINES = [bisim.ENGINE_DENSE, bisim.ENGINE_FRONTIER]
+ENGINE_IDS = ["dense", "frontier"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    bisim.load(build_if_missing=True)
+
+
+def run(lts, engine=bisim.ENGINE_AUTO, **kw):
+    return bisim.reduce(lts, bisim.make_opts(engine=engine, **kw), return_stats=True)
+
+
+def _golden(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return json.load(f)
+
+
+def _lts_from_golden(g, init=None):
+    return lts_gen.from_triples(g["n"], g["num_act"], g["transitions"], init)
+
+
+@pytest.mark.parametrize("engine", ENGINES, ids=ENGINE_IDS)
+def test_paper_examples(engine):
+    g1 = _golden("fig1_iteration.json")
+    lts = _lts_from_golden(g1, g1["block_before"])
+    got, st = run(lts, engine)
+    assert got.tolist() == [0, 1, 2, 3, 3]
+    g3 = _golden("fig3_preprocessing.json")
+    got, st = run(_lts_from_golden(g3), engine)
+    assert got.tolist() == [0, 1, 2]
+    assert st.mark_length == 6 and st.pre_rounds == 3
+
+
+@pytest.mark.parametrize("engine", ENGINES, ids=ENGINE_IDS)
+def test_random_small_vs_oracle(engine):
+    for seed in range(150):
+        rng = np.random.default_rng(5000 + seed)
+        n = int(rng.integers(1, 40))
+        A = int(rng.integers(1, 5))
+        m = int(rng.integers(0, 4 * n))
+        lts = lts_gen.random_small(seed, n, A, m, blocks=int(rng.integers(1, 4)))
+        want = oracle.ks_lts(lts)
+        got, st = run(lts, engine)
+        assert got.tolist() == want.tolist(), (seed, n, A, m)
+        assert st.num_blocks == defs.num_blocks(want)
+
+
+def test_dense_matches_pram_rounds_and_leaders():
+    """Priority rule on both sides: identical leader labels and iteration
+    counts (Algorithm 3, and Algorithm 2 for one label)."""
+    cases = [lts_gen.random_small(s, 30, 1 + s % 3, 70, blocks=2) for s in range(40)]
+    cases.append(lts_gen.kripke_uniform())
+    cases.append(lts_gen.chain(n=300))
+    cases.append(lts_gen.fan_out(40))
+    for lts in cases:
+        for alg2 in ([False, True] if lts.num_act == 1 else [False]):
+            labels, rounds, pre = oracle.pram_lts(lts, alg2=alg2)
+            got, st = run(lts, bisim.ENGINE_DENSE, raw_labels=True, rcpp_alg2=alg2)
+            assert got.tolist() == labels.tolist(), lts.name
+            assert st.rounds == rounds and st.pre_rounds == pre, lts.name
+
+
+@pytest.mark.parametrize("engine", ENGINES, ids=ENGINE_IDS)
+def test_kripke_1000(engine):
+    lts = lts_gen.kripke_uniform(seed=0)
+    got, st = run(lts, engine)
+    want = oracle.ks_lts(lts)
+    assert got.tolist() == want.tolist()
+    B = defs.num_blocks(want)
+    assert B + 1 <= st.rounds <= 3 * B - st.initial_blocks + 1
+
+
+@pytest.mark.parametrize("engine", ENGINES, ids=ENGINE_IDS)
+def test_quotient_expansion_full_size(engine):
+    """~100k states, ~1.1M transitions, 8 Zipf labels: equal to the oracle
+    and to the quotient's partition pulled back through the class map."""
+    lts = lts_gen.quotient_expansion(seed=1)
+    got, st = run(lts, engine)
+    want = oracle.ks_lts(lts)
+    assert got.tolist() == want.tolist()
+    assert got.tolist() == defs.pullback(lts.cls, oracle.ks_lts(lts.quotient)).tolist()
+    B = defs.num_blocks(want)
+    assert B + 1 <= st.rounds <= 3 * B - st.initial_blocks + 1
+
+
+@pytest.mark.parametrize("engine", ENGINES, ids=ENGINE_IDS)
+def test_chain_full_size(engine):
+    """Closed form: the 50,000-state chain is discrete; B+1 <= rounds <= 3n-2+1."""
+    n = 50000
+    lts = lts_gen.chain(seed=2, n=n)
+    got, st = run(lts, engine)
+    assert np.array_equal(got, np.arange(n, dtype=np.int32))
+    assert n + 1 <= st.rounds <= 3 * n - 2 + 1
+
+
+@pytest.mark.parametrize("engine", ENGINES, ids=ENGINE_IDS)
+def test_fan_out(engine):
+    for n in (3, 10, 100, 700):
+        got, _ = run(lts_gen.fan_out(n), engine)
+        assert got.tolist() == [0, 0] + list(range(1, n - 1))
+
+
+@pytest.mark.parametrize("engine", ENGINES, ids=ENGINE_IDS)
+def test_edge_cases(engine):
+    e = np.zeros(0, dtype=np.int32)
+    # no transitions: the initial partition itself
+    init = np.array([3, 3, 0, 1, 0, 3], dtype=np.int32)
+    got, st = run(lts_gen.LTS("empty", 6, 1, e, e, e, init), engine)
+    assert got.tolist() == defs.canonical(init).tolist()
+    assert st.rounds == 3 + 1
+    # one state, self loop
+    got, _ = run(lts_gen.from_triples(1, 1, [(0, 0, 0)]), engine)
+    assert got.tolist() == [0]
+    # many labels, most unused; duplicates
+    lts = lts_gen.random_small(7, 50, 3, 200)
+    lts.num_act = 1000
+    lts.act = (lts.act * 300).astype(np.int32)
+    src = np.concatenate([lts.src, lts.src]); act = np.concatenate([lts.act, lts.act])
+    dst = np.concatenate([lts.dst, lts.dst])
+    dup = lts_gen.LTS("dup", lts.n, lts.num_act, src, act, dst)
+    got, st = run(dup, engine)
+    assert got.tolist() == oracle.ks_lts(dup).tolist()
+    assert st.pre_rounds == 3
+
+
+def test_invalid_inputs_are_rejected():
+    bad = lts_gen.from_triples(3, 2, [(0, 0, 1), (2, 1, 3)])
+    with pytest.raises(bisim.BisimError) as ei:
+        run(bad)
+    assert ei.value.code == bisim.BISIM_EINVAL
+    bad = lts_gen.from_triples(3, 2, [(0, 2, 1)])
+    with pytest.raises(bisim.BisimError) as ei:
+        run(bad)
+    assert ei.value.code == bisim.BISIM_EINVAL
+    bad = lts_gen.from_triples(3, 1, [(0, 0, 1)], init=[0, 5, 0])
+    with pytest.raises(bisim.BisimError) as ei:
+        run(bad)
+    assert ei.value.code == bisim.BISIM_EINVAL
+    # still usable afterwards
+    got, _ = run(lts_gen.from_triples(3, 1, [(0, 0, 1)]))
+    assert got.tolist() == [0, 1, 2]
+
+
+@pytest.mark.parametrize("engine", ENGINES, ids=ENGINE_IDS)
+def test_round_cap_reports_error(engine):
+    lts = lts_gen.chain(n=200)
+    with pytest.raises(bisim.BisimError) as ei:
+        run(lts, engine, round_cap=5)
+    assert ei.value.code == bisim.BISIM_EROUNDS
+    got, _ = run(lts, engine)
+    assert np.array_equal(got, np.arange(200))
+
+
+@pytest.mark.parametrize("engine", ENGINES, ids=ENGINE_IDS)
+def test_barrier_wait_times_out_and_context_survives(engine):
+    """CTA 0 never arrives at its first barrier (a flag nothing sets); the
+    other CTAs give up after the time limit and the call reports it."""
+    lts = lts_gen.kripke_uniform(n=500, m=2000)
+    with pytest.raises(bisim.BisimError) as ei:
+        run(lts, engine, test_hook=1, timeout_ms=200)
+    assert ei.value.code == bisim.BISIM_ETIMEOUT
+    got, _ = run(lts, engine)
+    assert got.tolist() == oracle.ks_lts(lts).tolist()
+
+
+@pytest.mark.parametrize("engine", ENGINES, ids=ENGINE_IDS)
+def test_refine_twice_same_plan(engine):
+    import torch
+
+    lts = lts_gen.quotient_expansion(seed=9, classes=300, trans=3000, copies_hi=20)
+    d = lambda a: torch.from_numpy(a).cuda()  # noqa: E731
+    with bisim.Plan(lts.n, lts.num_act, d(lts.src), d(lts.act), d(lts.dst), None,
+                    bisim.make_opts(engine=engine)) as p:
+        a, s1 = p.refine()
+        a = a.cpu().numpy()
+        b, s2 = p.refine()
+        b = b.cpu().numpy()
+    assert np.array_equal(a, b)
+    assert a.tolist() == oracle.ks_lts(lts).tolist()
+
+
+def test_host_buffer_entry_point():
+    lts = lts_gen.quotient_expansion(seed=3, classes=200, trans=2000, copies_hi=10)
+    out = np.empty(lts.n, dtype=np.int32)
+    p = lambda a: a.ctypes.data  # noqa: E731
+    st = bisim.bisim_reduce_host(lts.n, lts.m, lts.num_act, p(lts.src), p(lts.act), p(lts.dst),
+                                 None, p(out))
+    assert out.tolist() == oracle.ks_lts(lts).tolist()
+    assert st.num_blocks == defs.num_blocks(out)
+
+
+@pytest.mark.parametrize("engine", ENGINES, ids=ENGINE_IDS)
+def test_launch_shapes(engine):
+    lts = lts_gen.quotient_expansion(seed=4, classes=400, trans=4000, copies_hi=30)
+    want = oracle.ks_lts(lts)
+    for threads, per_sm in ((128, 1), (256, 2), (1024, 1)):
+        got, _ = run(lts, engine, threads=threads, ctas_per_sm=per_sm)
+        assert got.tolist() == want.tolist(), (threads, per_sm)
