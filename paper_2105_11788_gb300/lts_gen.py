@@ -227,7 +227,7 @@ def random_small(seed: int, n: int, num_act: int, m: int, blocks: int = 1) -> LT
     act = rng.integers(0, num_act, m, dtype=np.int32)
     init = None
     if blocks > 1:
-        init = _i32(rng.integers(0, blocks, n))
+        init = _i32(rng.integers(0, min(blocks, n), n))
     return LTS(f"small_s{seed}_n{n}_a{num_act}_m{m}", n, num_act, _i32(src), _i32(act), _i32(dst), init)
 
 
