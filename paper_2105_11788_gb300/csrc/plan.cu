@@ -206,8 +206,10 @@ int reserve_stamps(bisim_plan_s* p, int64_t rounds, uint32_t* base) {
         if (p->n) {
             BISIM_CUDA_TRY(cudaMemsetAsync(p->lmark.p, 0, sizeof(uint32_t) * p->n, p->st));
             BISIM_CUDA_TRY(cudaMemsetAsync(p->nl64.p, 0xff, sizeof(uint64_t) * p->n, p->st));
-            if (p->frontier_ready)
-                BISIM_CUDA_TRY(cudaMemsetAsync(p->touched.p, 0, sizeof(uint32_t) * p->n, p->st));
+            if (p->frontier_ready) {
+                BISIM_CUDA_TRY(cudaMemsetAsync(p->smark.p, 0, sizeof(uint32_t) * p->n, p->st));
+                BISIM_CUDA_TRY(cudaMemsetAsync(p->kmark.p, 0, sizeof(uint32_t) * p->n, p->st));
+            }
         }
         p->stamp = 0;
     }
@@ -433,7 +435,7 @@ int plan_build(bisim_plan_s* p, const int32_t* src, const int32_t* act, const in
                                           cudaMemcpyDeviceToDevice, st));
     // |pi_0'|
     {
-        unsigned long long* cnt = &p->ctrl.as<bisim_ctrl>()->q_tail;
+        unsigned long long* cnt = &p->ctrl.as<bisim_ctrl>()->count;
         BISIM_CUDA_TRY(cudaMemsetAsync(cnt, 0, 8, st));
         if (n) {
             k_count_leaders<<<gn, T, 0, st>>>(p->block0.as<int32_t>(), n, cnt);
@@ -441,7 +443,7 @@ int plan_build(bisim_plan_s* p, const int32_t* src, const int32_t* act, const in
         }
         BISIM_CUDA_TRY(cudaGetLastError());
         BISIM_TRY(read_ctrl(p));
-        p->initial_blocks = (int64_t)p->ctrl_h->q_tail;
+        p->initial_blocks = (int64_t)p->ctrl_h->count;
         int code = status_to_code(p->ctrl_h->status);
         if (code) {
             set_last_error("preprocessing rounds failed");

@@ -18,13 +18,17 @@ struct bisim_ctrl {
     long long rounds;            // main-loop iterations incl. the final empty one
     long long edges;             // incoming transitions walked by mark steps
     long long states;            // states whose marks were compared
-    unsigned long long q_tail;   // FIFO worklist: total pushes so far
-    unsigned long long q_head0;  // FIFO worklist: pops before this launch
-    int n_touched[2];            // frontier: touched-block list lengths by round parity
-    int n_big[2];                // frontier: entries needing the whole grid
-    int n_mid[2];                // frontier: entries for one CTA
-    int pad1[2];
+    unsigned long long count;    // scratch counter for host queries
+    int n_touched[2];            // frontier: warp-list length by round parity
+    int n_mid[2];                // frontier: CTA-list length by round parity
+    unsigned long long bq_tail[32];  // frontier worklist: pushes per size bucket
 };
+
+// Frontier worklist: one FIFO ring of n entries per size bucket
+// floor(log2(block size)); the splitter is taken from the lowest non-empty
+// bucket, so small blocks are split on first (any unstable block is a valid
+// splitter under the arbitrary write rule).
+constexpr int BISIM_BUCKETS = 32;
 
 struct bisim_plan_s {
     int32_t n = 0;
@@ -56,14 +60,16 @@ struct bisim_plan_s {
 
     // frontier engine state (allocated on first use)
     bool frontier_ready = false;
-    bisim::DevMem elems;     // int32 [2n]: two buffers of states grouped by block
-    bisim::DevMem which;     // uint8 [n]: buffer holding the members of each label
+    bisim::DevMem elems;     // int32 [n]: states grouped by block
+    bisim::DevMem loc;       // int32 [n]: position of each state in elems
     bisim::DevMem bbeg;      // int32 [n]: member range [bbeg, bend) of each label
     bisim::DevMem bend;      // int32 [n]
-    bisim::DevMem cnt;       // uint64 [n]: per-label (kept, split) counters of a split in progress
-    bisim::DevMem done;      // int32 [n]: members processed of a split in progress
-    bisim::DevMem touched;   // uint32 [n]: round stamp of the last touch of each label
-    bisim::DevMem tlist;     // int32 [3 * n]: touched-label lists (small, CTA, grid)
+    bisim::DevMem mcnt;      // int32 [n]: marked members per label in the current round
+    bisim::DevMem mscr;      // int32 [n]: by position, marked members of each touched block
+    bisim::DevMem yscr;      // int32 [n]: by position, swap-pairing scratch
+    bisim::DevMem smark;     // uint32 [n]: round stamp of the last mark of each state
+    bisim::DevMem kmark;     // uint32 [n]: round stamp of membership in a kept part
+    bisim::DevMem tlist;     // int32 [2n]: touched-label lists (warp, CTA)
     bisim::DevMem queue;     // int32 [n]: FIFO ring of unstable labels
 
     uint32_t stamp = 0;      // last round stamp used (marks are never cleared)

@@ -1,24 +1,29 @@
 // Frontier refinement engine: the while-loop of Algorithm 3 (Algorithm 2 with
-// rcpp_alg2) where a round touches only the splitter, the transitions into it
-// and the blocks of the states that reach it.
+// rcpp_alg2) where a round touches only the splitter C, the transitions into
+// C, the states that reach C and - when a block's leader reaches C - the part
+// of that block that moves out.
 //
-// Layout: the states of every block b occupy the range [bbeg[b], bend[b]) of
-// one of two member buffers (which[b] says which). A split writes all members
-// of b to the other buffer over the same range, kept members first and split
-// members last, so concurrent splits of different blocks never collide and no
-// copy-back is needed.
+// Layout (refinable partition): the members of block b occupy
+// elems[bbeg[b] .. bend[b]) and loc[s] is the position of state s. Splits
+// rearrange a block's range in place by swapping members.
 //
 // Round r (stamp = stamp0 + r), two grid barriers:
 //   select  C := next label of the FIFO worklist; unstable_C := false
-//   mark    for every member t of C and incoming transition s -a-> t:
-//           mark[off(s) + order] := stamp, and block(s) is appended once
-//           (touched stamp) to a list by size: warp / CTA / whole grid
-//   split   every touched block compares each member's marks with its leader's;
-//           members that differ move to a new block whose leader is elected
-//           (warp and CTA teams: their smallest split state; grid teams:
-//           compare-and-swap, the arbitrary write rule); the old label, the
-//           new label and (Algorithm 3) C are pushed if they were stable.
-// A block of one state cannot split and is never listed.
+//   mark    one warp per member t of C, lanes over the transitions s -a-> t:
+//           mark[off(s) + order] := stamp. The first time s is marked in the
+//           round (smark stamp) it gets a rank r_s in its block b (atomicAdd)
+//           and is written to mscr[bend[b] - 1 - r_s], so after the step the
+//           marked members of b sit in the tail of b's range of mscr; the
+//           first one appends b to a list (warp list for blocks of at most 64
+//           states, CTA list otherwise). Blocks of one state cannot split.
+//   split   Algorithm 3's rule: s splits off iff its marks differ from the
+//           leader's. If the leader is unmarked the split part is exactly the
+//           marked members (k of them) and moves to the last k positions; if
+//           the leader is marked, the kept part is the marked members whose
+//           marks equal the leader's (kk of them) and moves to the first kk
+//           positions, the rest is relabelled. The new label is the smallest
+//           state of the split part; the old label, the new label and
+//           (Algorithm 3) C are pushed if they were stable.
 #include "plan.cuh"
 
 using namespace bisim;
@@ -34,36 +39,33 @@ struct FrontierArgs {
     const unsigned long long* __restrict__ in_edge;
     int32_t* block;
     uint32_t* mark;
-    unsigned long long* nl64;
     uint32_t* unstable;
-    int32_t* elems;  // [2n]
-    uint8_t* which;
-    int32_t* bbeg;
-    int32_t* bend;
-    unsigned long long* cnt;
-    int32_t* done;
-    uint32_t* touched;
-    int32_t* tlist;  // [3n]: warp list, CTA list, grid list
-    int32_t* queue;  // [n]
+    int32_t* elems;   // [n] members grouped by block
+    int32_t* loc;     // [n] position of each state in elems
+    int32_t* bbeg;    // [n] per label
+    int32_t* bend;    // [n] per label
+    int32_t* mcnt;    // [n] marked members per label in this round
+    int32_t* mscr;    // [n] by position: marked members in the tail of their block's range
+    int32_t* yscr;    // [n] by position: scratch for the swap pairing
+    uint32_t* smark;  // [n] per state: stamp of the round that last marked it
+    uint32_t* kmark;  // [n] per state: stamp of the round it was in a kept part
+    int32_t* tlist;   // [2n]: warp list, CTA list
+    int32_t* queue;   // [n]
     bisim_ctrl* ctrl;
     GridBarrier gb;
     uint32_t stamp0;
     int64_t round_cap;
-    int32_t cta_max;
     int alg2;
     int test_hook;
 };
 
-__device__ __forceinline__ unsigned long long elect_key(uint32_t stamp, int32_t s) {
-    return ((unsigned long long)(0xffffffffu - stamp) << 32) | (uint32_t)s;
-}
-__device__ __forceinline__ bool key_is(unsigned long long v, uint32_t stamp) {
-    return (uint32_t)(v >> 32) == 0xffffffffu - stamp;
-}
+__device__ __forceinline__ int size_bucket(int32_t sz) { return 31 - __clz(max(sz, 1)); }
 
+// append a label to the FIFO ring of its size bucket
 __device__ __forceinline__ void push(const FrontierArgs& a, int32_t label) {
-    unsigned long long pos = atomicAdd(&a.ctrl->q_tail, 1ull);
-    a.queue[pos % (unsigned long long)a.n] = label;
+    const int bk = size_bucket(ldcg(&a.bend[label]) - ldcg(&a.bbeg[label]));
+    const unsigned long long pos = atomicAdd(&a.ctrl->bq_tail[bk], 1ull);
+    a.queue[(size_t)bk * a.n + pos % (unsigned long long)a.n] = label;
 }
 
 // unstable_label := true; enqueue it if it was stable
@@ -71,211 +73,256 @@ __device__ __forceinline__ void set_unstable(const FrontierArgs& a, int32_t labe
     if (atomicExch(&a.unstable[label], 1u) == 0u) push(a, label);
 }
 
-// Does state s have a mark vector different from the leader's? k = number of
-// mark slots of the block's label set; lmask = the leader's marks (k <= 32).
-__device__ __forceinline__ bool member_splits(const FrontierArgs& a, int32_t s, int32_t lo, int32_t k,
-                                              unsigned lmask, uint32_t stamp) {
+__device__ __forceinline__ void finish_split(const FrontierArgs& a, int32_t b, int32_t leader, int32_t C) {
+    set_unstable(a, b);
+    set_unstable(a, leader);
+    if (!a.alg2) set_unstable(a, C);
+}
+
+// Does s have the same marks as the leader (lo = off[leader], k slots)?
+__device__ __forceinline__ bool same_marks(const FrontierArgs& a, int32_t s, int32_t lo, int32_t k,
+                                           unsigned lmask, uint32_t stamp) {
     const int32_t os = a.off[s];
     int32_t ks = a.off[s + 1] - os;
-    if (ks != k) {
+    if (ks != k) {  // members must share the leader's label set (preprocessing invariant)
         atomicOr(&a.ctrl->status, ST_INTERNAL);
         ks = min(ks, k);
     }
-    bool sp = false;
+    bool diff = false;
     if (k <= 32) {
         for (int32_t q = 0; q < ks; q++)
-            sp |= (ldcg(&a.mark[os + q]) == stamp) != (bool)((lmask >> q) & 1u);
+            diff |= (ldcg(&a.mark[os + q]) == stamp) != (bool)((lmask >> q) & 1u);
     } else {
         for (int32_t q = 0; q < ks; q++)
-            sp |= (ldcg(&a.mark[os + q]) == stamp) != (ldcg(&a.mark[lo + q]) == stamp);
+            diff |= (ldcg(&a.mark[os + q]) == stamp) != (ldcg(&a.mark[lo + q]) == stamp);
     }
-    return sp;
+    return !diff;
 }
 
-// One warp splits block b (size <= WARP_MAX) entirely.
+// One warp splits block b (at most 64 members) from the members themselves.
 __device__ void warp_split(const FrontierArgs& a, int32_t b, uint32_t stamp, int32_t C, long long& states) {
     const unsigned lane = threadIdx.x & 31u;
     const unsigned lt = lanemask_lt();
-    const int w = ldcg(&a.which[b]);
     const int32_t b0 = ldcg(&a.bbeg[b]), e0 = ldcg(&a.bend[b]);
     const int32_t sz = e0 - b0;
-    const int32_t* src = a.elems + (size_t)w * a.n;
-    int32_t* dst = a.elems + (size_t)(1 - w) * a.n;
+    if (lane == 0) a.mcnt[b] = 0;
     const int32_t lo = a.off[b];
     const int32_t k = a.off[b + 1] - lo;
+    const bool lead_marked = ldcg(&a.smark[b]) == stamp;
     unsigned lmask = 0;
-    if (k <= 32) lmask = __ballot_sync(0xffffffffu, (int)lane < k && ldcg(&a.mark[lo + lane]) == stamp);
-    const int32_t s0 = (int)lane < sz ? ldcg(&src[b0 + lane]) : -1;
-    const int32_t s1 = (int)lane + 32 < sz ? ldcg(&src[b0 + 32 + lane]) : -1;
-    const bool p0 = s0 >= 0 && member_splits(a, s0, lo, k, lmask, stamp);
-    const bool p1 = s1 >= 0 && member_splits(a, s1, lo, k, lmask, stamp);
+    if (lead_marked && k <= 32)
+        lmask = __ballot_sync(0xffffffffu, (int)lane < k && ldcg(&a.mark[lo + lane]) == stamp);
+    const int32_t s0 = (int)lane < sz ? ldcg(&a.elems[b0 + lane]) : -1;
+    const int32_t s1 = (int)lane + 32 < sz ? ldcg(&a.elems[b0 + 32 + lane]) : -1;
+    bool p0 = false, p1 = false;  // splits off
+    if (s0 >= 0) {
+        const bool mk = ldcg(&a.smark[s0]) == stamp;
+        p0 = lead_marked ? !(mk && same_marks(a, s0, lo, k, lmask, stamp)) : mk;
+    }
+    if (s1 >= 0) {
+        const bool mk = ldcg(&a.smark[s1]) == stamp;
+        p1 = lead_marked ? !(mk && same_marks(a, s1, lo, k, lmask, stamp)) : mk;
+    }
     const unsigned m0 = __ballot_sync(0xffffffffu, p0), m1 = __ballot_sync(0xffffffffu, p1);
     if (lane == 0) states += sz;
     if ((m0 | m1) == 0u) return;
     const unsigned v0 = __ballot_sync(0xffffffffu, s0 >= 0), v1 = __ballot_sync(0xffffffffu, s1 >= 0);
-    const int32_t nsplit = __popc(m0) + __popc(m1);
-    const int32_t nkeep = sz - nsplit;
+    const int32_t nkeep = sz - __popc(m0) - __popc(m1);
     const int32_t leader = __reduce_min_sync(0xffffffffu, min(p0 ? s0 : NONE, p1 ? s1 : NONE));
     if (s0 >= 0) {
-        const int32_t pos = p0 ? nkeep + __popc(m0 & lt) : __popc(~m0 & v0 & lt);
-        dst[b0 + pos] = s0;
+        const int32_t pos = b0 + (p0 ? nkeep + __popc(m0 & lt) : __popc(~m0 & v0 & lt));
+        a.elems[pos] = s0;
+        a.loc[s0] = pos;
         if (p0) a.block[s0] = leader;
     }
     if (s1 >= 0) {
-        const int32_t pos = p1 ? nkeep + __popc(m0) + __popc(m1 & lt)
-                               : __popc(~m0 & v0) + __popc(~m1 & v1 & lt);
-        dst[b0 + pos] = s1;
+        const int32_t pos = b0 + (p1 ? nkeep + __popc(m0) + __popc(m1 & lt)
+                                     : __popc(~m0 & v0) + __popc(~m1 & v1 & lt));
+        a.elems[pos] = s1;
+        a.loc[s1] = pos;
         if (p1) a.block[s1] = leader;
     }
     if (lane == 0) {
-        a.which[b] = (uint8_t)(1 - w);
         a.bend[b] = b0 + nkeep;
-        a.which[leader] = (uint8_t)(1 - w);
         a.bbeg[leader] = b0 + nkeep;
         a.bend[leader] = e0;
-        set_unstable(a, b);
-        set_unstable(a, leader);
-        if (!a.alg2) set_unstable(a, C);
+        finish_split(a, b, leader, C);
     }
 }
 
 struct CtaShared {
-    int wkeep[32];
-    int wsplit[32];
-    int red[32];
-    int leader;
-    int kbase;
-    int sbase;
+    int wcnt[32];
+    int wmin[32];
+    int total;
+    int mn;
     unsigned lmask;
+    int C;
+    unsigned long long head[BISIM_BUCKETS];  // this CTA's copy of the worklist heads
 };
 
-// One CTA splits members [seg_lo, seg_hi) of block b. Several CTAs may work
-// on disjoint segments of the same block: positions are reserved with one
-// 64-bit atomicAdd per chunk (kept count low, split count high), the new
-// leader is elected by compare-and-swap, and the CTA that completes the last
-// member finalises the ranges and the worklist.
-__device__ void cta_split_segment(const FrontierArgs& a, CtaShared& sh, int32_t b, int32_t seg_lo,
-                                  int32_t seg_hi, uint32_t stamp, int32_t C, long long& states) {
+// Block-wide exclusive rank of predicate p and the block total (sh.total).
+__device__ __forceinline__ int cta_rank(bool p, CtaShared& sh, int& total) {
     const unsigned lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
     const unsigned nw = blockDim.x >> 5;
-    const unsigned lt = lanemask_lt();
-    const int w = ldcg(&a.which[b]);
+    const unsigned bal = __ballot_sync(0xffffffffu, p);
+    if (lane == 0) sh.wcnt[wid] = __popc(bal);
+    __syncthreads();
+    if (wid == 0) {
+        int c = (int)lane < (int)nw ? sh.wcnt[lane] : 0;
+        int x = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, x, o);
+            if ((int)lane >= o) x += y;
+        }
+        if ((int)lane < (int)nw) sh.wcnt[lane] = x - c;
+        if (lane == 31) sh.total = x;
+    }
+    __syncthreads();
+    const int r = sh.wcnt[wid] + __popc(bal & lanemask_lt());
+    total = sh.total;
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ int cta_min(int v, CtaShared& sh) {
+    const unsigned lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
+    const unsigned nw = blockDim.x >> 5;
+    v = __reduce_min_sync(0xffffffffu, v);
+    if (lane == 0) sh.wmin[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        int c = (int)lane < (int)nw ? sh.wmin[lane] : NONE;
+        c = __reduce_min_sync(0xffffffffu, c);
+        if (lane == 0) sh.mn = c;
+    }
+    __syncthreads();
+    const int r = sh.mn;
+    __syncthreads();
+    return r;
+}
+
+// Move the set of states listed in mscr[t0 .. t0+cnt) (none of them already
+// at a position in [r0, r0+cnt), except those whose loc says so) into the
+// position range [r0, r0+cnt) by swapping with the states there that are not
+// in the set. in_set(u) tells membership of the state u currently at a
+// position of the range.
+template <typename InSet>
+__device__ void cta_gather_range(const FrontierArgs& a, CtaShared& sh, int32_t t0, int32_t cnt,
+                                 int32_t r0, InSet in_set) {
+    // outsiders of the set: X = members of the set outside [r0, r0+cnt),
+    // compacted in place at mscr[t0 ..); Y = positions inside the range held
+    // by non-members, compacted at yscr[t0 ..)
+    int nx = 0;
+    for (int32_t base = 0; base < cnt; base += blockDim.x) {
+        const int32_t i = base + threadIdx.x;
+        const int32_t s = i < cnt ? ldcg(&a.mscr[t0 + i]) : -1;
+        const bool out = s >= 0 && (ldcg(&a.loc[s]) < r0 || ldcg(&a.loc[s]) >= r0 + cnt);
+        int tot;
+        const int rk = cta_rank(out, sh, tot);
+        if (out) a.mscr[t0 + nx + rk] = s;  // stable in-place compaction (target <= source)
+        nx += tot;
+        __syncthreads();
+    }
+    int ny = 0;
+    for (int32_t base = 0; base < cnt; base += blockDim.x) {
+        const int32_t i = base + threadIdx.x;
+        const int32_t q = r0 + i;
+        const bool foreign = i < cnt && !in_set(ldcg(&a.elems[q]));
+        int tot;
+        const int rk = cta_rank(foreign, sh, tot);
+        if (foreign) a.yscr[t0 + ny + rk] = q;
+        ny += tot;
+    }
+    __syncthreads();
+    if (nx != ny) {
+        if (threadIdx.x == 0) atomicOr(&a.ctrl->status, ST_INTERNAL);
+        return;
+    }
+    for (int32_t j = threadIdx.x; j < nx; j += blockDim.x) {
+        const int32_t s = ldcg(&a.mscr[t0 + j]);
+        const int32_t q = ldcg(&a.yscr[t0 + j]);
+        const int32_t p = ldcg(&a.loc[s]);
+        const int32_t u = ldcg(&a.elems[q]);
+        a.elems[p] = u;
+        a.loc[u] = p;
+        a.elems[q] = s;
+        a.loc[s] = q;
+    }
+    __syncthreads();
+}
+
+// One CTA splits block b (more than WARP_MAX members), touching only the
+// marked members, plus the moved-out part when the leader is marked.
+__device__ void cta_split(const FrontierArgs& a, CtaShared& sh, int32_t b, uint32_t stamp, int32_t C,
+                          long long& states) {
+    const unsigned lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
     const int32_t b0 = ldcg(&a.bbeg[b]), e0 = ldcg(&a.bend[b]);
-    const int32_t* src = a.elems + (size_t)w * a.n;
-    int32_t* dst = a.elems + (size_t)(1 - w) * a.n;
+    const int32_t km = ldcg(&a.mcnt[b]);
+    const int32_t t0 = e0 - km;  // marked members are listed in mscr[t0 .. e0)
     const int32_t lo = a.off[b];
     const int32_t k = a.off[b + 1] - lo;
+    const bool lead_marked = ldcg(&a.smark[b]) == stamp;
+    __syncthreads();
+    if (threadIdx.x == 0) a.mcnt[b] = 0;
+    if (!lead_marked) {
+        // split part = the km marked members; it moves to [t0, e0)
+        int mn = NONE;
+        for (int32_t i = threadIdx.x; i < km; i += blockDim.x) mn = min(mn, ldcg(&a.mscr[t0 + i]));
+        const int32_t leader = cta_min(mn, sh);
+        for (int32_t i = threadIdx.x; i < km; i += blockDim.x) a.block[ldcg(&a.mscr[t0 + i])] = leader;
+        __syncthreads();
+        cta_gather_range(a, sh, t0, km, t0, [&](int32_t u) { return ldcg(&a.smark[u]) == stamp; });
+        if (threadIdx.x == 0) {
+            states += km;
+            a.bend[b] = t0;
+            a.bbeg[leader] = t0;
+            a.bend[leader] = e0;
+            finish_split(a, b, leader, C);
+        }
+        __syncthreads();
+        return;
+    }
+    // leader marked: kept part = marked members with the leader's marks
     if (wid == 0) {
         unsigned lm = 0;
         if (k <= 32) lm = __ballot_sync(0xffffffffu, (int)lane < k && ldcg(&a.mark[lo + lane]) == stamp);
-        if (lane == 0) {
-            sh.lmask = lm;
-            sh.leader = NONE;
-        }
+        if (lane == 0) sh.lmask = lm;
     }
     __syncthreads();
     const unsigned lmask = sh.lmask;
-    for (int32_t base = seg_lo; base < seg_hi; base += blockDim.x) {
-        const int32_t idx = base + threadIdx.x;
-        const bool valid = idx < seg_hi;
-        const int32_t s = valid ? ldcg(&src[idx]) : -1;
-        const bool p = valid && member_splits(a, s, lo, k, lmask, stamp);
-        const unsigned bs = __ballot_sync(0xffffffffu, p);
-        const unsigned bk = __ballot_sync(0xffffffffu, valid && !p);
-        if (lane == 0) {
-            sh.wsplit[wid] = __popc(bs);
-            sh.wkeep[wid] = __popc(bk);
+    int kk = 0;
+    for (int32_t base = 0; base < km; base += blockDim.x) {
+        const int32_t i = base + threadIdx.x;
+        const int32_t s = i < km ? ldcg(&a.mscr[t0 + i]) : -1;
+        const bool keep = s >= 0 && same_marks(a, s, lo, k, lmask, stamp);
+        int tot;
+        const int rk = cta_rank(keep, sh, tot);
+        if (keep) {
+            a.kmark[s] = stamp;
+            a.mscr[t0 + kk + rk] = s;  // kept members compacted in place
         }
-        int cand = __reduce_min_sync(0xffffffffu, p ? s : NONE);
-        if (lane == 0) sh.red[wid] = cand;
-        __syncthreads();
-        if (wid == 0) {
-            int ns = (int)lane < (int)nw ? sh.wsplit[lane] : 0;
-            int nk = (int)lane < (int)nw ? sh.wkeep[lane] : 0;
-            int c = (int)lane < (int)nw ? sh.red[lane] : NONE;
-            // exclusive scans over warps
-            int xs = ns, xk = nk;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                int ys = __shfl_up_sync(0xffffffffu, xs, o);
-                int yk = __shfl_up_sync(0xffffffffu, xk, o);
-                if ((int)lane >= o) {
-                    xs += ys;
-                    xk += yk;
-                }
-            }
-            const int tot_s = __shfl_sync(0xffffffffu, xs, 31);
-            const int tot_k = __shfl_sync(0xffffffffu, xk, 31);
-            c = __reduce_min_sync(0xffffffffu, c);
-            if ((int)lane < (int)nw) {
-                sh.wsplit[lane] = xs - ns;
-                sh.wkeep[lane] = xk - nk;
-            }
-            if (lane == 0) {
-                if (tot_s > 0 && sh.leader == NONE) {
-                    // elect: first writer of this round wins
-                    unsigned long long v = ldcg(&a.nl64[b]);
-                    for (int it = 0; it < 4; it++) {
-                        if (key_is(v, stamp)) {
-                            sh.leader = (int32_t)(uint32_t)v;
-                            break;
-                        }
-                        const unsigned long long want = elect_key(stamp, c);
-                        const unsigned long long old = atomicCAS(&a.nl64[b], v, want);
-                        if (old == v) {
-                            sh.leader = c;
-                            break;
-                        }
-                        v = old;
-                    }
-                    if (sh.leader == NONE) atomicOr(&a.ctrl->status, ST_INTERNAL);
-                }
-                const unsigned long long add = (unsigned long long)(uint32_t)tot_k |
-                                               ((unsigned long long)(uint32_t)tot_s << 32);
-                const unsigned long long old = atomicAdd(&a.cnt[b], add);
-                sh.kbase = b0 + (int32_t)(uint32_t)old;
-                sh.sbase = e0 - (int32_t)(uint32_t)(old >> 32) - tot_s;
-            }
-        }
-        __syncthreads();
-        if (valid) {
-            int32_t pos;
-            if (p) {
-                pos = sh.sbase + sh.wsplit[wid] + __popc(bs & lt);
-                if (sh.leader != NONE) a.block[s] = sh.leader;
-            } else {
-                pos = sh.kbase + sh.wkeep[wid] + __popc(bk & lt);
-            }
-            dst[pos] = s;
-        }
+        kk += tot;
         __syncthreads();
     }
-    __threadfence();
+    const int32_t sz = e0 - b0;
+    if (threadIdx.x == 0) states += km;
+    if (kk == sz) return;  // every member kept: no split
+    cta_gather_range(a, sh, t0, kk, b0, [&](int32_t u) { return ldcg(&a.kmark[u]) == stamp; });
+    // split part = [b0 + kk, e0)
+    int mn = NONE;
+    for (int32_t q = b0 + kk + threadIdx.x; q < e0; q += blockDim.x) mn = min(mn, ldcg(&a.elems[q]));
+    const int32_t leader = cta_min(mn, sh);
+    for (int32_t q = b0 + kk + threadIdx.x; q < e0; q += blockDim.x) a.block[ldcg(&a.elems[q])] = leader;
     __syncthreads();
     if (threadIdx.x == 0) {
-        const int32_t mine = seg_hi - seg_lo;
-        states += mine;
-        const int32_t d = atomicAdd(&a.done[b], mine) + mine;
-        if (d == e0 - b0) {
-            __threadfence();
-            const unsigned long long c = atomicExch(&a.cnt[b], 0ull);
-            const int32_t kept = (int32_t)(uint32_t)c;
-            const int32_t spl = (int32_t)(uint32_t)(c >> 32);
-            a.done[b] = 0;
-            a.which[b] = (uint8_t)(1 - w);
-            a.bend[b] = b0 + kept;
-            if (kept + spl != e0 - b0) atomicOr(&a.ctrl->status, ST_INTERNAL);
-            if (spl > 0) {
-                const int32_t leader = (int32_t)(uint32_t)ldcg(&a.nl64[b]);
-                a.which[leader] = (uint8_t)(1 - w);
-                a.bbeg[leader] = b0 + kept;
-                a.bend[leader] = e0;
-                set_unstable(a, b);
-                set_unstable(a, leader);
-                if (!a.alg2) set_unstable(a, C);
-            }
-        }
+        states += sz - kk;
+        a.bend[b] = b0 + kk;
+        a.bbeg[leader] = b0 + kk;
+        a.bend[leader] = e0;
+        finish_split(a, b, leader, C);
     }
+    __syncthreads();
 }
 
 __global__ void __launch_bounds__(1024) k_frontier_main(FrontierArgs a) {
@@ -283,55 +330,65 @@ __global__ void __launch_bounds__(1024) k_frontier_main(FrontierArgs a) {
     const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
     const int32_t n = a.n;
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = gtid >> 5, nwarps = gsz >> 5;
     unsigned long long tgt = 0;
     long long edges = 0, states = 0;
     if (a.test_hook == 1 && blockIdx.x == 0) return;  // testing: never arrive
-    unsigned long long head = a.ctrl->q_head0;
+    if (threadIdx.x < BISIM_BUCKETS) sh.head[threadIdx.x] = 0;
     int64_t r = 0;
-    const int32_t big_min = a.cta_max;
     for (;;) {
         r++;
         const uint32_t stamp = a.stamp0 + (uint32_t)r;
         const int par = (int)(r & 1);
-        const unsigned long long tail = ldcg(&a.ctrl->q_tail);
-        if (head >= tail) break;  // no unstable label: C = bottom
+        // select: every CTA pops the same label from the lowest non-empty bucket
+        if (threadIdx.x < 32) {
+            const unsigned long long h = sh.head[lane];
+            const bool ne = h < ldcg(&a.ctrl->bq_tail[lane]);
+            const unsigned bal = __ballot_sync(0xffffffffu, ne);
+            if (bal == 0u) {
+                if (lane == 0) sh.C = -1;
+            } else if (lane == __ffs(bal) - 1) {
+                sh.C = ldcg(&a.queue[(size_t)lane * n + h % (unsigned long long)n]);
+                sh.head[lane] = h + 1;
+            }
+        }
+        __syncthreads();
+        const int32_t C = sh.C;
+        __syncthreads();
+        if (C < 0) break;  // no unstable label: C = bottom
         if (r > a.round_cap) {
             if (gtid == 0) atomicOr(&a.ctrl->status, ST_ROUNDS);
             break;
         }
-        const int32_t C = ldcg(&a.queue[head % (unsigned long long)n]);
-        head++;
         if (gtid == 0) {
             a.unstable[C] = 0u;
             a.ctrl->n_touched[par ^ 1] = 0;
             a.ctrl->n_mid[par ^ 1] = 0;
-            a.ctrl->n_big[par ^ 1] = 0;
         }
-        // mark
+        // mark: one warp per member of C, lanes over its incoming transitions
         {
-            const int w = ldcg(&a.which[C]);
             const int32_t b0 = ldcg(&a.bbeg[C]), e0 = ldcg(&a.bend[C]);
-            const int32_t* mem = a.elems + (size_t)w * n;
-            for (int64_t idx = b0 + gtid; idx < e0; idx += gsz) {
-                const int32_t t = ldcg(&mem[idx]);
+            for (int64_t idx = b0 + gw; idx < e0; idx += nwarps) {
+                const int32_t t = ldcg(&a.elems[idx]);
                 const int32_t j0 = a.in_ptr[t], j1 = a.in_ptr[t + 1];
-                edges += j1 - j0;
-                for (int32_t j = j0; j < j1; j++) {
+                if (lane == 0) edges += j1 - j0;
+                for (int32_t j = j0 + lane; j < j1; j += 32) {
                     const unsigned long long e = a.in_edge[j];
-                    const uint32_t slot = (uint32_t)e;
                     const int32_t s = (int32_t)(e >> 32);
-                    a.mark[slot] = stamp;
+                    a.mark[(uint32_t)e] = stamp;
+                    if (ldcg(&a.smark[s]) == stamp) continue;
+                    if (atomicExch(&a.smark[s], stamp) == stamp) continue;
                     const int32_t b = ldcg(&a.block[s]);
-                    if (ldcg(&a.touched[b]) == stamp) continue;
-                    if (atomicExch(&a.touched[b], stamp) == stamp) continue;
-                    const int32_t sz = ldcg(&a.bend[b]) - ldcg(&a.bbeg[b]);
-                    if (sz <= 1) continue;
-                    if (sz <= WARP_MAX) {
-                        a.tlist[atomicAdd(&a.ctrl->n_touched[par], 1)] = b;
-                    } else if (sz <= big_min) {
-                        a.tlist[n + atomicAdd(&a.ctrl->n_mid[par], 1)] = b;
-                    } else {
-                        a.tlist[2 * (size_t)n + atomicAdd(&a.ctrl->n_big[par], 1)] = b;
+                    const int32_t bb = ldcg(&a.bbeg[b]), be = ldcg(&a.bend[b]);
+                    if (be - bb <= 1) continue;
+                    const int32_t rk = atomicAdd(&a.mcnt[b], 1);
+                    a.mscr[be - 1 - rk] = s;
+                    if (rk == 0) {
+                        if (be - bb <= WARP_MAX)
+                            a.tlist[atomicAdd(&a.ctrl->n_touched[par], 1)] = b;
+                        else
+                            a.tlist[n + atomicAdd(&a.ctrl->n_mid[par], 1)] = b;
                     }
                 }
             }
@@ -341,23 +398,9 @@ __global__ void __launch_bounds__(1024) k_frontier_main(FrontierArgs a) {
         {
             const int32_t ns = ldcg(&a.ctrl->n_touched[par]);
             const int32_t nm = ldcg(&a.ctrl->n_mid[par]);
-            const int32_t nb = ldcg(&a.ctrl->n_big[par]);
-            const int64_t gw = gtid >> 5, nwarps = gsz >> 5;
             for (int64_t i = gw; i < ns; i += nwarps) warp_split(a, ldcg(&a.tlist[i]), stamp, C, states);
-            for (int32_t i = blockIdx.x; i < nm; i += gridDim.x) {
-                const int32_t b = ldcg(&a.tlist[n + i]);
-                const int32_t b0 = ldcg(&a.bbeg[b]), e0 = ldcg(&a.bend[b]);
-                cta_split_segment(a, sh, b, b0, e0, stamp, C, states);
-            }
-            for (int32_t i = 0; i < nb; i++) {
-                const int32_t b = ldcg(&a.tlist[2 * (size_t)n + i]);
-                const int32_t b0 = ldcg(&a.bbeg[b]), e0 = ldcg(&a.bend[b]);
-                const int32_t sz = e0 - b0;
-                const int32_t chunk = (sz + (int32_t)gridDim.x - 1) / (int32_t)gridDim.x;
-                const int32_t lo = b0 + (int32_t)blockIdx.x * chunk;
-                const int32_t hi = min(e0, lo + chunk);
-                if (lo < hi) cta_split_segment(a, sh, b, lo, hi, stamp, C, states);
-            }
+            for (int32_t i = blockIdx.x; i < nm; i += gridDim.x)
+                cta_split(a, sh, ldcg(&a.tlist[n + i]), stamp, C, states);
         }
         if (!grid_sync(a.gb, tgt)) return;
     }
@@ -382,40 +425,48 @@ __global__ void k_front_init(const int32_t* __restrict__ block0, int32_t n, int3
     }
 }
 
-// ranges of each label in the label-sorted member array; all members start
-// in buffer 0
-__global__ void k_front_ranges(const uint32_t* __restrict__ skeys, int32_t n, int32_t* bbeg,
-                               int32_t* bend) {
+// ranges of each label in the label-sorted member array, and loc
+__global__ void k_front_ranges(const uint32_t* __restrict__ skeys, const int32_t* __restrict__ elems,
+                               int32_t n, int32_t* bbeg, int32_t* bend, int32_t* loc) {
     const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gsz) {
         const uint32_t b = skeys[i];
         if (i == 0 || skeys[i - 1] != b) bbeg[b] = (int32_t)i;
         if (i == n - 1 || skeys[i + 1] != b) bend[b] = (int32_t)i + 1;
+        loc[elems[i]] = (int32_t)i;
     }
 }
 
-// initial worklist: every label in increasing order
-__global__ void k_front_queue(const uint32_t* __restrict__ flags, const uint32_t* __restrict__ pos,
-                              int32_t n, int32_t* queue) {
+// initial worklist: every label, in the bucket of its block size
+__global__ void k_front_queue(const uint32_t* __restrict__ flags, const int32_t* __restrict__ bbeg,
+                              const int32_t* __restrict__ bend, int32_t n, bisim_ctrl* ctrl,
+                              int32_t* queue) {
     const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gsz)
-        if (flags[i]) queue[pos[i]] = (int32_t)i;
+        if (flags[i]) {
+            const int bk = size_bucket(bend[i] - bbeg[i]);
+            const unsigned long long pos = atomicAdd(&ctrl->bq_tail[bk], 1ull);
+            queue[(size_t)bk * n + pos] = (int32_t)i;
+        }
 }
 
 int ensure_frontier(bisim_plan_s* p) {
     if (p->frontier_ready) return BISIM_OK;
     const size_t n = (size_t)p->n;
     cudaStream_t st = p->st;
-    BISIM_TRY(p->elems.alloc(8 * n, st));
-    BISIM_TRY(p->which.alloc(n, st));
+    BISIM_TRY(p->elems.alloc(4 * n, st));
+    BISIM_TRY(p->loc.alloc(4 * n, st));
     BISIM_TRY(p->bbeg.alloc(4 * n, st));
     BISIM_TRY(p->bend.alloc(4 * n, st));
-    BISIM_TRY(p->cnt.alloc(8 * n, st));
-    BISIM_TRY(p->done.alloc(4 * n, st));
-    BISIM_TRY(p->touched.alloc(4 * n, st));
-    BISIM_TRY(p->tlist.alloc(12 * n, st));
-    BISIM_TRY(p->queue.alloc(4 * n, st));
-    BISIM_CUDA_TRY(cudaMemsetAsync(p->touched.p, 0, 4 * n, st));
+    BISIM_TRY(p->mcnt.alloc(4 * n, st));
+    BISIM_TRY(p->mscr.alloc(4 * n, st));
+    BISIM_TRY(p->yscr.alloc(4 * n, st));
+    BISIM_TRY(p->smark.alloc(4 * n, st));
+    BISIM_TRY(p->kmark.alloc(4 * n, st));
+    BISIM_TRY(p->tlist.alloc(8 * n, st));
+    BISIM_TRY(p->queue.alloc(4 * n * BISIM_BUCKETS, st));
+    BISIM_CUDA_TRY(cudaMemsetAsync(p->smark.p, 0, 4 * n, st));
+    BISIM_CUDA_TRY(cudaMemsetAsync(p->kmark.p, 0, 4 * n, st));
     p->frontier_ready = true;
     return BISIM_OK;
 }
@@ -433,9 +484,7 @@ int refine_frontier(bisim_plan_s* p, bisim_stats* stats) {
     BISIM_TRY(reserve_stamps(p, cap + 1, &base));
     bisim_ctrl* c = p->ctrl.as<bisim_ctrl>();
     BISIM_CUDA_TRY(cudaMemsetAsync(c, 0, sizeof(bisim_ctrl), st));
-    BISIM_CUDA_TRY(cudaMemsetAsync(p->which.p, 0, (size_t)n, st));
-    BISIM_CUDA_TRY(cudaMemsetAsync(p->cnt.p, 0, 8 * (size_t)n, st));
-    BISIM_CUDA_TRY(cudaMemsetAsync(p->done.p, 0, 4 * (size_t)n, st));
+    BISIM_CUDA_TRY(cudaMemsetAsync(p->mcnt.p, 0, 4 * (size_t)n, st));
     {
         DevMem keys, vals, keys2, flags;
         BISIM_TRY(keys.alloc(4 * (size_t)n, st));
@@ -448,23 +497,21 @@ int refine_frontier(bisim_plan_s* p, bisim_stats* stats) {
                                          vals.as<uint32_t>(), flags.as<uint32_t>());
         BISIM_LAUNCHED();
         BISIM_CUDA_TRY(cudaGetLastError());
-        // members grouped by label: sort (label, state); the sorted states are
-        // buffer 0 of the member array
-        uint32_t* e0 = p->elems.as<uint32_t>();
+        // members grouped by label: sort (label, state)
+        uint32_t* el = p->elems.as<uint32_t>();
         bool alt = false;
         BISIM_TRY(radix_sort_pairs<uint32_t, uint32_t>(keys.as<uint32_t>(), vals.as<uint32_t>(),
-                                                       keys2.as<uint32_t>(), e0, n,
+                                                       keys2.as<uint32_t>(), el, n,
                                                        ceil_log2_u64((uint64_t)n), st, &alt));
         uint32_t* skeys = alt ? keys2.as<uint32_t>() : keys.as<uint32_t>();
-        if (!alt) BISIM_CUDA_TRY(cudaMemcpyAsync(e0, vals.p, 4 * (size_t)n, cudaMemcpyDeviceToDevice, st));
-        k_front_ranges<<<gn, 256, 0, st>>>(skeys, n, p->bbeg.as<int32_t>(), p->bend.as<int32_t>());
+        if (!alt) BISIM_CUDA_TRY(cudaMemcpyAsync(el, vals.p, 4 * (size_t)n, cudaMemcpyDeviceToDevice, st));
+        k_front_ranges<<<gn, 256, 0, st>>>(skeys, p->elems.as<int32_t>(), n, p->bbeg.as<int32_t>(),
+                                           p->bend.as<int32_t>(), p->loc.as<int32_t>());
         BISIM_LAUNCHED();
         BISIM_CUDA_TRY(cudaGetLastError());
-        // worklist: all labels, increasing
-        BISIM_TRY(scan_exclusive_u32(flags.as<uint32_t>(), keys.as<uint32_t>(), n,
-                                     (uint32_t*)&c->q_tail, st));
-        k_front_queue<<<gn, 256, 0, st>>>(flags.as<uint32_t>(), keys.as<uint32_t>(), n,
-                                          p->queue.as<int32_t>());
+        // worklist: all labels
+        k_front_queue<<<gn, 256, 0, st>>>(flags.as<uint32_t>(), p->bbeg.as<int32_t>(),
+                                          p->bend.as<int32_t>(), n, c, p->queue.as<int32_t>());
         BISIM_LAUNCHED();
         BISIM_CUDA_TRY(cudaGetLastError());
     }
@@ -475,15 +522,16 @@ int refine_frontier(bisim_plan_s* p, bisim_stats* stats) {
     a.in_edge = p->in_edge.as<unsigned long long>();
     a.block = p->block.as<int32_t>();
     a.mark = p->mark.as<uint32_t>();
-    a.nl64 = p->nl64.as<unsigned long long>();
     a.unstable = p->unstable.as<uint32_t>();
     a.elems = p->elems.as<int32_t>();
-    a.which = p->which.as<uint8_t>();
+    a.loc = p->loc.as<int32_t>();
     a.bbeg = p->bbeg.as<int32_t>();
     a.bend = p->bend.as<int32_t>();
-    a.cnt = p->cnt.as<unsigned long long>();
-    a.done = p->done.as<int32_t>();
-    a.touched = p->touched.as<uint32_t>();
+    a.mcnt = p->mcnt.as<int32_t>();
+    a.mscr = p->mscr.as<int32_t>();
+    a.yscr = p->yscr.as<int32_t>();
+    a.smark = p->smark.as<uint32_t>();
+    a.kmark = p->kmark.as<uint32_t>();
     a.tlist = p->tlist.as<int32_t>();
     a.queue = p->queue.as<int32_t>();
     a.ctrl = c;
@@ -495,7 +543,6 @@ int refine_frontier(bisim_plan_s* p, bisim_stats* stats) {
     a.alg2 = (p->opts.rcpp_alg2 && p->A == 1) ? 1 : 0;
     a.test_hook = p->opts.test_hook;
     const int threads = p->opts.threads > 0 ? p->opts.threads : 512;
-    a.cta_max = 16 * threads;
     void* args[] = {&a};
     int grid = 0;
     BISIM_TRY(launch_persistent((const void*)k_frontier_main, args, threads, p, &grid));
