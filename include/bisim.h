@@ -152,6 +152,44 @@ int bisim_reduce_host(int32_t n, int64_t m, int32_t num_act, const int32_t* src_
                       int32_t* out_block_h, const bisim_opts* opts, void* stream,
                       bisim_stats* stats);
 
+/* Largest n accepted by bisim_canonical_ids_noalloc. */
+#define BISIM_NOALLOC_MAX_N (1 << 20)
+
+/*
+ * bisim_canonical_ids_noalloc - renumber block labels canonically without
+ * allocating any memory. The paper has no counterpart: this is a service for
+ * callers that cannot allocate device memory, e.g. because a framework's
+ * caching allocator owns the whole device budget, or because a cudaMalloc /
+ * cudaFree in a latency-critical loop would synchronise the device.
+ *
+ * Same result as the output step of bisim_refine: given any labelling of
+ * states (labels[i] in [0, n), equal labels = same block), out_ids[i] is the
+ * block's rank when blocks are ordered by their smallest state.
+ *
+ * labels       int32 [n] device, values in [0, n) (caller-owned, read only)
+ * n            0 <= n <= BISIM_NOALLOC_MAX_N (1,048,576); larger n returns
+ *              BISIM_EINVAL without touching anything
+ * out_ids      int32 [n] device (caller-owned), written
+ * num_blocks_h NULL or host int32 receiving the number of blocks
+ * stream       cudaStream_t as void*, NULL = legacy default stream; the call
+ *              synchronises it before returning
+ *
+ * Scratch: a fixed file-scope device array of about 8 MB (two int32 arrays of
+ * BISIM_NOALLOC_MAX_N plus counters), held on every GPU that loads the
+ * library until the process exits. The call makes no cudaMalloc, cudaFree or
+ * other allocating call. The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture. Every call on a device shares the
+ * one array and resets the parts that must start at zero; calls that overlap
+ * on the GPU (other streams, other host threads) race on it and must be
+ * serialised by the caller.
+ * Errors (return code only; bisim_last_error is not updated): BISIM_EINVAL
+ * (n out of range, NULL pointer, or a label outside [0, n)), BISIM_ETIMEOUT,
+ * BISIM_ECUDA, BISIM_ENOTSUP (device ordinal >= 64).
+ */
+int bisim_canonical_ids_noalloc(const int32_t* labels, int32_t n, int32_t* out_ids,
+                                int32_t* num_blocks_h, void* stream);
+
 /* Static description of an error code. */
 const char* bisim_strerror(int code);
 

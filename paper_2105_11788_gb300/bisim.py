@@ -258,3 +258,22 @@ def reduce(lts, opts=None, device="cuda", return_stats=False):
         out, st = p.refine()
         res = out.cpu().numpy()
     return (res, st) if return_stats else res
+
+
+def bisim_canonical_ids_noalloc(labels: int, n: int, out_ids: int, stream: int = 0) -> int:
+    """Allocation-free canonical renumbering (device addresses in); returns
+    the number of blocks. For callers that cannot allocate device memory: its
+    scratch is a fixed array of the library, so n is limited to
+    BISIM_NOALLOC_MAX_N and overlapping calls must be serialised."""
+    f = load().bisim_canonical_ids_noalloc
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32),
+                  ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    nb = ctypes.c_int32(0)
+    rc = f(labels or None, n, out_ids or None, ctypes.byref(nb), stream or None)
+    if rc != BISIM_OK:
+        raise BisimError(rc, "bisim_canonical_ids_noalloc")
+    return int(nb.value)
+
+
+BISIM_NOALLOC_MAX_N = 1 << 20
