@@ -217,6 +217,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="qexp", choices=sorted(WORKLOADS))
     ap.add_argument("--engine", default="auto", choices=["auto", "dense", "frontier"])
+    ap.add_argument("--threads", type=int, default=0, help="threads per CTA (0 = library default)")
+    ap.add_argument("--max-ctas", type=int, default=0, help="cap on persistent-kernel CTAs")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -234,7 +236,7 @@ def main():
     bisim.load(build_if_missing=True)
     engine = {"auto": bisim.ENGINE_AUTO, "dense": bisim.ENGINE_DENSE,
               "frontier": bisim.ENGINE_FRONTIER}[args.engine]
-    opts = bisim.make_opts(engine=engine)
+    opts = bisim.make_opts(engine=engine, threads=args.threads, max_ctas=args.max_ctas)
     desc, make = WORKLOADS[args.workload]
     lts = make()
     src = torch.from_numpy(lts.src).to(dev)
@@ -328,7 +330,7 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic",
             "config": {"workload": desc, "n": lts.n, "m": lts.m, "num_act": lts.num_act,
-                       "engine": args.engine,
+                       "engine": args.engine, "threads": args.threads, "max_ctas": args.max_ctas,
                        "l2": "flushed between steps (256 MiB write)" if flush is not None
                              else "inputs larger than L2",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},

@@ -70,6 +70,9 @@ typedef struct bisim_opts {
                             barrier waits run out and BISIM_ETIMEOUT is returned */
     int64_t round_cap;   /* 0 = 3n + |Act| + 2 (Theorem 3 plus slack) */
     int64_t timeout_ms;  /* limit on one grid-barrier wait (0 = 2000 ms) */
+    int32_t max_ctas;    /* cap on the CTAs of the persistent launches (0 = no cap;
+                            fewer CTAs make the grid barrier cheaper) */
+    int32_t reserved;
 } bisim_opts;
 
 typedef struct bisim_stats {
@@ -151,6 +154,18 @@ int bisim_reduce_host(int32_t n, int64_t m, int32_t num_act, const int32_t* src_
                       const int32_t* act_h, const int32_t* dst_h, const int32_t* init_h,
                       int32_t* out_block_h, const bisim_opts* opts, void* stream,
                       bisim_stats* stats);
+
+/*
+ * bisim_barrier_cost - diagnostic: time `iters` back-to-back grid-wide
+ * barriers (the synchronisation the persistent kernels use between the steps
+ * of a round; §5 of the paper needs four such points per iteration, the
+ * frontier engine two) in one cooperative launch of `ctas` CTAs of `threads`
+ * threads, and return the average device time per barrier in nanoseconds.
+ * Errors: BISIM_EINVAL (bad argument or more CTAs than can be co-resident),
+ * BISIM_ECUDA, BISIM_ETIMEOUT.
+ */
+int bisim_barrier_cost(int32_t ctas, int32_t threads, int32_t iters, void* stream,
+                       double* ns_per_barrier);
 
 /* Largest n accepted by bisim_canonical_ids_noalloc. */
 #define BISIM_NOALLOC_MAX_N (1 << 20)

@@ -41,6 +41,8 @@ class bisim_opts(ctypes.Structure):
         ("test_hook", ctypes.c_int32),
         ("round_cap", ctypes.c_int64),
         ("timeout_ms", ctypes.c_int64),
+        ("max_ctas", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 
@@ -138,9 +140,9 @@ def _check(code: int, where: str):
 
 def make_opts(engine: int = ENGINE_AUTO, rcpp_alg2: bool = False, raw_labels: bool = False,
               threads: int = 0, ctas_per_sm: int = 0, round_cap: int = 0, timeout_ms: int = 0,
-              test_hook: int = 0) -> bisim_opts:
+              test_hook: int = 0, max_ctas: int = 0) -> bisim_opts:
     return bisim_opts(engine, int(rcpp_alg2), int(raw_labels), threads, ctas_per_sm, test_hook,
-                      round_cap, timeout_ms)
+                      round_cap, timeout_ms, max_ctas, 0)
 
 
 # ----------------------------------------------------------- C-ABI mirrors
@@ -185,6 +187,17 @@ def bisim_reduce_host(n: int, m: int, num_act: int, src_h: int, act_h: Optional[
 
 def bisim_version() -> int:
     return int(load().bisim_version())
+
+
+def bisim_barrier_cost(ctas: int, threads: int, iters: int, stream: int = 0) -> float:
+    """Average device time of one grid-wide barrier, in nanoseconds."""
+    f = load().bisim_barrier_cost
+    f.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                  ctypes.POINTER(ctypes.c_double)]
+    f.restype = ctypes.c_int
+    ns = ctypes.c_double(0)
+    _check(f(ctas, threads, iters, stream or None, ctypes.byref(ns)), "bisim_barrier_cost")
+    return float(ns.value)
 
 
 # --------------------------------------------------- torch conveniences

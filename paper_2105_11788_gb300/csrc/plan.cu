@@ -227,6 +227,7 @@ int launch_persistent(const void* fn, void** args, int threads, bisim_plan_s* p,
     int per_sm = p->opts.ctas_per_sm > 0 ? p->opts.ctas_per_sm : 1;
     per_sm = std::min(per_sm, occ);
     int grid = p->sm_count * per_sm;
+    if (p->opts.max_ctas > 0) grid = std::min(grid, p->opts.max_ctas);
     *grid_out = grid;
     BISIM_CUDA_TRY(cudaEventRecord(p->evk0, p->st));
     BISIM_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(threads), args, 0, p->st));

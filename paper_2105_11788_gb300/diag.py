@@ -1,0 +1,64 @@
+"""Diagnostics on the GPU: grid-barrier cost and launch-shape sweeps.
+
+    python -m paper_2105_11788_gb300.diag barrier        # ns per grid barrier
+    python -m paper_2105_11788_gb300.diag shapes         # main-loop time per launch shape
+
+Each prints JSON lines.
+"""
+from __future__ import annotations
+
+import json
+import sys
+
+from . import bisim, lts_gen
+
+WORKLOADS = {
+    "kripke": lambda: lts_gen.kripke_uniform(seed=0),
+    "qexp": lambda: lts_gen.quotient_expansion(seed=1),
+    "chain": lambda: lts_gen.chain(seed=2, n=50000),
+}
+
+
+def barrier(iters: int = 20000, repeats: int = 3):
+    res = {}
+    for threads in (256, 512, 1024):
+        for ctas in (1, 8, 16, 38, 76, 152, 304):
+            try:
+                res[f"{ctas}x{threads}"] = min(bisim.bisim_barrier_cost(ctas, threads, iters)
+                                               for _ in range(repeats))
+            except bisim.BisimError as e:
+                res[f"{ctas}x{threads}"] = str(e)
+    print(json.dumps({"barrier_ns": res}), flush=True)
+
+
+def shapes(workloads=("kripke", "qexp", "chain"), repeats: int = 3):
+    for wl in workloads:
+        lts = WORKLOADS[wl]()
+        for eng in (bisim.ENGINE_FRONTIER, bisim.ENGINE_DENSE):
+            for threads, mc in ((512, 0), (512, 76), (512, 38), (512, 16), (256, 152), (1024, 152)):
+                best, st = None, None
+                for _ in range(repeats):
+                    _, st = bisim.reduce(lts, bisim.make_opts(engine=eng, threads=threads, max_ctas=mc),
+                                         return_stats=True)
+                    best = st.t_main_ms if best is None else min(best, st.t_main_ms)
+                print(json.dumps({"workload": wl, "engine": eng, "threads": threads, "max_ctas": mc,
+                                  "main_ms": best, "rounds": st.rounds,
+                                  "us_per_round": 1000 * best / max(st.rounds, 1)}), flush=True)
+
+
+def main(argv):
+    import torch
+
+    torch.cuda.init()
+    bisim.load(build_if_missing=True)
+    what = argv[1] if len(argv) > 1 else "barrier"
+    if what == "barrier":
+        barrier()
+    elif what == "shapes":
+        shapes(tuple(argv[2:]) or ("kripke", "qexp", "chain"))
+    else:
+        raise SystemExit(f"unknown diagnostic {what}")
+
+
+if __name__ == "__main__":
+    main(sys.argv)

@@ -44,13 +44,13 @@ def test_struct_layouts_match_header(tmp_path):
         '#include <stdio.h>\n#include <stddef.h>\n#include "bisim.h"\n'
         "int main(void){printf(\"%zu %zu %zu %zu %zu %zu\\n\", sizeof(bisim_opts),"
         " sizeof(bisim_stats), offsetof(bisim_opts, round_cap), offsetof(bisim_stats, t_plan_ms),"
-        " offsetof(bisim_stats, engine), offsetof(bisim_opts, test_hook)); return 0;}\n")
+        " offsetof(bisim_stats, engine), offsetof(bisim_opts, max_ctas)); return 0;}\n")
     exe = tmp_path / "sz"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
     got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
     want = [ctypes.sizeof(bisim.bisim_opts), ctypes.sizeof(bisim.bisim_stats),
             bisim.bisim_opts.round_cap.offset, bisim.bisim_stats.t_plan_ms.offset,
-            bisim.bisim_stats.engine.offset, bisim.bisim_opts.test_hook.offset]
+            bisim.bisim_stats.engine.offset, bisim.bisim_opts.max_ctas.offset]
     assert got == want
 
 
