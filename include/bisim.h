@@ -155,6 +155,52 @@ int bisim_reduce_host(int32_t n, int64_t m, int32_t num_act, const int32_t* src_
                       int32_t* out_block_h, const bisim_opts* opts, void* stream,
                       bisim_stats* stats);
 
+/* Per-LTS results of bisim_batch_refine. */
+typedef struct bisim_batch_inst {
+    int64_t rounds;     /* main-loop iterations of this LTS, incl. the final empty one */
+    int64_t num_blocks; /* blocks of its result */
+} bisim_batch_inst;
+
+/*
+ * bisim_batch_plan - plan k LTSs at once (not in the paper: a throughput
+ * mode). The LTSs are packed into one union whose state ranges are disjoint;
+ * the union's initial partition separates the LTSs, so its coarsest stable
+ * refinement is the union of theirs, and one sort, one CSR and one set of
+ * preprocessing rounds (Algorithm 5, one per label occurring anywhere) serve
+ * the batch.
+ *
+ * k            number of LTSs, >= 1
+ * state_off_h  host int64 [k+1]: LTS i has states [state_off_h[i], state_off_h[i+1])
+ *              of the concatenated state arrays; state_off_h[0] = 0, total < 2^31
+ * trans_off_h  host int64 [k+1]: LTS i has transitions [trans_off_h[i], trans_off_h[i+1])
+ * num_act_h    host int32 [k]: label count of each LTS (>= 1)
+ * src, dst     device int32 [total m]: LOCAL state numbers in [0, n_i)
+ * act          device int32 [total m]: local labels in [0, num_act_h[i]), or NULL (all 0)
+ * init_block   device int32 [total n]: local initial labels in [0, n_i), or NULL
+ * Same ownership, stream and error rules as bisim_plan.
+ */
+int bisim_batch_plan(int32_t k, const int64_t* state_off_h, const int64_t* trans_off_h,
+                     const int32_t* num_act_h, const int32_t* src, const int32_t* act,
+                     const int32_t* dst, const int32_t* init_block, const bisim_opts* opts,
+                     void* stream, bisim_plan_t* out);
+
+/*
+ * bisim_batch_refine - refine every LTS of a batch plan in one launch: each
+ * CTA takes one LTS at a time (largest first) and runs the frontier rounds
+ * for it with CTA-local barriers and a CTA-local worklist, so different LTSs
+ * proceed concurrently on different SMs. The launch is not cooperative and
+ * can overlap other work on the device.
+ *
+ * out_block  device int32 [total n]: canonical ids local to each LTS (blocks
+ *            of LTS i numbered 0.. by their smallest state), or union leader
+ *            labels with opts.raw_labels
+ * stats      NULL or aggregate counters (rounds = sum over the LTSs)
+ * inst_h     NULL or host array of k per-LTS results
+ * Errors as bisim_refine; BISIM_EINVAL if the plan is not a batch plan.
+ */
+int bisim_batch_refine(bisim_plan_t plan, int32_t* out_block, bisim_stats* stats,
+                       bisim_batch_inst* inst_h);
+
 /*
  * bisim_barrier_cost - diagnostic: time `iters` back-to-back grid-wide
  * barriers (the synchronisation the persistent kernels use between the steps

@@ -290,3 +290,83 @@ def bisim_canonical_ids_noalloc(labels: int, n: int, out_ids: int, stream: int =
 
 
 BISIM_NOALLOC_MAX_N = 1 << 20
+
+
+class bisim_batch_inst(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_int64), ("num_blocks", ctypes.c_int64)]
+
+
+def bisim_batch_plan(k: int, state_off_h, trans_off_h, num_act_h, src: int, act: Optional[int], dst: int,
+                     init_block: Optional[int], opts: Optional[bisim_opts] = None, stream: int = 0) -> int:
+    """Batch plan (host offset arrays as numpy int64/int32, device addresses
+    for the concatenated local arrays); returns the plan handle."""
+    import numpy as np
+
+    f = load().bisim_batch_plan
+    P = ctypes.c_void_p
+    f.argtypes = [ctypes.c_int32, P, P, P, P, P, P, P, ctypes.POINTER(bisim_opts), P, ctypes.POINTER(P)]
+    f.restype = ctypes.c_int
+    so = np.ascontiguousarray(state_off_h, dtype=np.int64)
+    to = np.ascontiguousarray(trans_off_h, dtype=np.int64)
+    na = np.ascontiguousarray(num_act_h, dtype=np.int32)
+    out = ctypes.c_void_p()
+    rc = f(k, so.ctypes.data, to.ctypes.data, na.ctypes.data, src or None, act or None, dst or None,
+           init_block or None, ctypes.byref(opts) if opts is not None else None, stream or None,
+           ctypes.byref(out))
+    _check(rc, "bisim_batch_plan")
+    return out.value
+
+
+def bisim_batch_refine(plan: int, out_block: int, k: int):
+    """Returns (aggregate bisim_stats, array of k bisim_batch_inst)."""
+    f = load().bisim_batch_refine
+    f.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(bisim_stats),
+                  ctypes.POINTER(bisim_batch_inst)]
+    f.restype = ctypes.c_int
+    st = bisim_stats()
+    inst = (bisim_batch_inst * k)()
+    _check(f(plan, out_block or None, ctypes.byref(st), inst), "bisim_batch_refine")
+    return st, inst
+
+
+def pack_batch(ltss):
+    """Concatenate LTSs (local ids) into the arrays bisim_batch_plan takes."""
+    import numpy as np
+
+    so = np.zeros(len(ltss) + 1, dtype=np.int64)
+    to = np.zeros(len(ltss) + 1, dtype=np.int64)
+    for i, l in enumerate(ltss):
+        so[i + 1] = so[i] + l.n
+        to[i + 1] = to[i] + l.m
+    na = np.array([l.num_act for l in ltss], dtype=np.int32)
+    cat = lambda xs: np.ascontiguousarray(np.concatenate(xs) if xs else np.zeros(0), dtype=np.int32)  # noqa
+    src = cat([l.src for l in ltss])
+    act = cat([l.act for l in ltss])
+    dst = cat([l.dst for l in ltss])
+    init = None
+    if any(l.init is not None for l in ltss):
+        init = cat([l.init if l.init is not None else np.zeros(l.n, np.int32) for l in ltss])
+    return so, to, na, src, act, dst, init
+
+
+def reduce_batch(ltss, opts=None, device="cuda", stream=None, return_stats=False):
+    """Coarsest bisimulation partitions of many LTSs in one batched plan and
+    one refinement launch; returns a list of numpy arrays (canonical ids)."""
+    import torch
+
+    so, to, na, src, act, dst, init = pack_batch(ltss)
+    d = lambda a: None if a is None else torch.from_numpy(a).to(device)  # noqa: E731
+    tsrc, tact, tdst, tinit = d(src), d(act), d(dst), d(init)
+    N = int(so[-1])
+    out = torch.empty(max(N, 1), dtype=torch.int32, device=device)
+    sp = _stream_ptr(stream)
+    h = bisim_batch_plan(len(ltss), so, to, na, tsrc.data_ptr() if tsrc.numel() else 0,
+                         tact.data_ptr() if tact.numel() else 0, tdst.data_ptr() if tdst.numel() else 0,
+                         tinit.data_ptr() if tinit is not None else None, opts, sp)
+    try:
+        st, inst = bisim_batch_refine(h, out.data_ptr(), len(ltss))
+    finally:
+        bisim_plan_destroy(h)
+    res = out[:N].cpu().numpy()
+    parts = [res[so[i]:so[i + 1]] for i in range(len(ltss))]
+    return (parts, st, inst) if return_stats else parts

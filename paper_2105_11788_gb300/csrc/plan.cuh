@@ -22,6 +22,8 @@ struct bisim_ctrl {
     int n_touched[2];            // frontier: warp-list length by round parity
     int n_mid[2];                // frontier: CTA-list length by round parity
     unsigned long long bq_tail[32];  // frontier worklist: pushes per size bucket
+    int next_inst;                   // batch engine: next LTS to take
+    int pad2;
 };
 
 // Frontier worklist: one FIFO ring of n entries per size bucket
@@ -72,6 +74,15 @@ struct bisim_plan_s {
     bisim::DevMem tlist;     // int32 [2n]: touched-label lists (warp, CTA)
     bisim::DevMem queue;     // int32 [n]: FIFO ring of unstable labels
 
+    // batch plans: k LTSs over disjoint state ranges of one union LTS
+    int32_t batch_k = 0;
+    std::vector<int64_t> state_off_h;   // [k+1]
+    std::vector<int32_t> batch_act_h;   // [k] label count of each LTS
+    bisim::DevMem state_off;            // int64 [k+1]
+    bisim::DevMem batch_act;            // int32 [k]
+    bisim::DevMem batch_order;          // int32 [k]: LTS indices, largest first
+    bisim::DevMem inst_rounds;          // int64 [k]
+
     uint32_t stamp = 0;      // last round stamp used (marks are never cleared)
     int64_t pre_rounds = 0;
     int64_t initial_blocks = 0;
@@ -91,6 +102,8 @@ int plan_build(bisim_plan_s* p, const int32_t* src, const int32_t* act, const in
                const int32_t* init);
 int refine_dense(bisim_plan_s* p, bisim_stats* st);
 int refine_frontier(bisim_plan_s* p, bisim_stats* st);
+// CTA-per-LTS frontier rounds over a batch plan; rounds[i] = iterations of LTS i
+int refine_frontier_batch(bisim_plan_s* p, bisim_stats* st, std::vector<long long>& rounds);
 int write_output(bisim_plan_s* p, int32_t* out_block, int64_t* num_blocks);
 
 // Reserve `rounds` fresh stamps (resetting stamped arrays if the 32-bit

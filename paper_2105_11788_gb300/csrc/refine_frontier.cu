@@ -61,22 +61,35 @@ struct FrontierArgs {
 
 __device__ __forceinline__ int size_bucket(int32_t sz) { return 31 - __clz(max(sz, 1)); }
 
+// The splitter worklist of one LTS: BISIM_BUCKETS FIFO rings of `cap`
+// entries, bucket k at queue[k * stride + base ...]. `tail` holds the pushes
+// per bucket; it lives in global memory for the grid engine (every CTA pops)
+// and in shared memory for the CTA-per-instance engine.
+struct Worklist {
+    unsigned long long* tail;
+    int32_t* queue;
+    size_t stride;
+    int32_t base;
+    int32_t cap;
+};
+
 // append a label to the FIFO ring of its size bucket
-__device__ __forceinline__ void push(const FrontierArgs& a, int32_t label) {
+__device__ __forceinline__ void push(const FrontierArgs& a, const Worklist& wl, int32_t label) {
     const int bk = size_bucket(ldcg(&a.bend[label]) - ldcg(&a.bbeg[label]));
-    const unsigned long long pos = atomicAdd(&a.ctrl->bq_tail[bk], 1ull);
-    a.queue[(size_t)bk * a.n + pos % (unsigned long long)a.n] = label;
+    const unsigned long long pos = atomicAdd(&wl.tail[bk], 1ull);
+    wl.queue[(size_t)bk * wl.stride + wl.base + pos % (unsigned long long)wl.cap] = label;
 }
 
 // unstable_label := true; enqueue it if it was stable
-__device__ __forceinline__ void set_unstable(const FrontierArgs& a, int32_t label) {
-    if (atomicExch(&a.unstable[label], 1u) == 0u) push(a, label);
+__device__ __forceinline__ void set_unstable(const FrontierArgs& a, const Worklist& wl, int32_t label) {
+    if (atomicExch(&a.unstable[label], 1u) == 0u) push(a, wl, label);
 }
 
-__device__ __forceinline__ void finish_split(const FrontierArgs& a, int32_t b, int32_t leader, int32_t C) {
-    set_unstable(a, b);
-    set_unstable(a, leader);
-    if (!a.alg2) set_unstable(a, C);
+__device__ __forceinline__ void finish_split(const FrontierArgs& a, const Worklist& wl, int32_t b,
+                                             int32_t leader, int32_t C) {
+    set_unstable(a, wl, b);
+    set_unstable(a, wl, leader);
+    if (!a.alg2) set_unstable(a, wl, C);
 }
 
 // Does s have the same marks as the leader (lo = off[leader], k slots)?
@@ -100,7 +113,8 @@ __device__ __forceinline__ bool same_marks(const FrontierArgs& a, int32_t s, int
 }
 
 // One warp splits block b (at most 64 members) from the members themselves.
-__device__ void warp_split(const FrontierArgs& a, int32_t b, uint32_t stamp, int32_t C, long long& states) {
+__device__ void warp_split(const FrontierArgs& a, const Worklist& wl, int32_t b, uint32_t stamp, int32_t C,
+                           long long& states) {
     const unsigned lane = threadIdx.x & 31u;
     const unsigned lt = lanemask_lt();
     const int32_t b0 = ldcg(&a.bbeg[b]), e0 = ldcg(&a.bend[b]);
@@ -146,7 +160,7 @@ __device__ void warp_split(const FrontierArgs& a, int32_t b, uint32_t stamp, int
         a.bend[b] = b0 + nkeep;
         a.bbeg[leader] = b0 + nkeep;
         a.bend[leader] = e0;
-        finish_split(a, b, leader, C);
+        finish_split(a, wl, b, leader, C);
     }
 }
 
@@ -254,8 +268,8 @@ __device__ void cta_gather_range(const FrontierArgs& a, CtaShared& sh, int32_t t
 
 // One CTA splits block b (more than WARP_MAX members), touching only the
 // marked members, plus the moved-out part when the leader is marked.
-__device__ void cta_split(const FrontierArgs& a, CtaShared& sh, int32_t b, uint32_t stamp, int32_t C,
-                          long long& states) {
+__device__ void cta_split(const FrontierArgs& a, const Worklist& wl, CtaShared& sh, int32_t b, uint32_t stamp,
+                          int32_t C, long long& states) {
     const unsigned lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
     const int32_t b0 = ldcg(&a.bbeg[b]), e0 = ldcg(&a.bend[b]);
     const int32_t km = ldcg(&a.mcnt[b]);
@@ -278,7 +292,7 @@ __device__ void cta_split(const FrontierArgs& a, CtaShared& sh, int32_t b, uint3
             a.bend[b] = t0;
             a.bbeg[leader] = t0;
             a.bend[leader] = e0;
-            finish_split(a, b, leader, C);
+            finish_split(a, wl, b, leader, C);
         }
         __syncthreads();
         return;
@@ -320,9 +334,67 @@ __device__ void cta_split(const FrontierArgs& a, CtaShared& sh, int32_t b, uint3
         a.bend[b] = b0 + kk;
         a.bbeg[leader] = b0 + kk;
         a.bend[leader] = e0;
-        finish_split(a, b, leader, C);
+        finish_split(a, wl, b, leader, C);
     }
     __syncthreads();
+}
+
+// Mark step of one round (Algorithm 3, mark lines) for splitter C, done by the
+// warps gw, gw + nwarps, ... (the whole grid or one CTA): one warp per member
+// of C, lanes over its incoming transitions. The first mark of a source s in
+// the round ranks it among the marked members of its block; the first marked
+// member of a block appends the block to the warp list or the CTA list.
+__device__ __forceinline__ void mark_step(const FrontierArgs& a, int32_t C, uint32_t stamp, int64_t gw,
+                                          int64_t nwarps, int* n_small, int* n_mid, int32_t* small_list,
+                                          int32_t* mid_list, long long& edges) {
+    const int lane = threadIdx.x & 31;
+    const int32_t b0 = ldcg(&a.bbeg[C]), e0 = ldcg(&a.bend[C]);
+    for (int64_t idx = b0 + gw; idx < e0; idx += nwarps) {
+        const int32_t t = ldcg(&a.elems[idx]);
+        const int32_t j0 = a.in_ptr[t], j1 = a.in_ptr[t + 1];
+        if (lane == 0) edges += j1 - j0;
+        for (int32_t j = j0 + lane; j < j1; j += 32) {
+            const unsigned long long e = a.in_edge[j];
+            const int32_t s = (int32_t)(e >> 32);
+            a.mark[(uint32_t)e] = stamp;
+            if (ldcg(&a.smark[s]) == stamp) continue;
+            if (atomicExch(&a.smark[s], stamp) == stamp) continue;
+            const int32_t b = ldcg(&a.block[s]);
+            const int32_t bb = ldcg(&a.bbeg[b]), be = ldcg(&a.bend[b]);
+            if (be - bb <= 1) continue;
+            const int32_t rk = atomicAdd(&a.mcnt[b], 1);
+            a.mscr[be - 1 - rk] = s;
+            if (rk == 0) {
+                if (be - bb <= WARP_MAX)
+                    small_list[atomicAdd(n_small, 1)] = b;
+                else
+                    mid_list[atomicAdd(n_mid, 1)] = b;
+            }
+        }
+    }
+}
+
+// Pop the next splitter (lowest non-empty size bucket) with warp 0 of the CTA;
+// returns it to every thread, or -1 when the worklist is empty.
+__device__ __forceinline__ int32_t select_splitter(const Worklist& wl, unsigned long long* head, CtaShared& sh) {
+    const unsigned lane = threadIdx.x & 31u;
+    if (threadIdx.x < 32) {
+        const unsigned long long h = head[lane];
+        // the tails are global (grid engine) or shared (batch engine): a
+        // volatile generic load serves both without using a stale L1 line
+        const bool ne = h < *(volatile const unsigned long long*)&wl.tail[lane];
+        const unsigned bal = __ballot_sync(0xffffffffu, ne);
+        if (bal == 0u) {
+            if (lane == 0) sh.C = -1;
+        } else if ((int)lane == __ffs(bal) - 1) {
+            sh.C = ldcg(&wl.queue[(size_t)lane * wl.stride + wl.base + h % (unsigned long long)wl.cap]);
+            head[lane] = h + 1;
+        }
+    }
+    __syncthreads();
+    const int32_t C = sh.C;
+    __syncthreads();
+    return C;
 }
 
 __global__ void __launch_bounds__(1024) k_frontier_main(FrontierArgs a) {
@@ -330,32 +402,19 @@ __global__ void __launch_bounds__(1024) k_frontier_main(FrontierArgs a) {
     const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
     const int32_t n = a.n;
-    const int lane = threadIdx.x & 31;
     const int64_t gw = gtid >> 5, nwarps = gsz >> 5;
     unsigned long long tgt = 0;
     long long edges = 0, states = 0;
     if (a.test_hook == 1 && blockIdx.x == 0) return;  // testing: never arrive
     if (threadIdx.x < BISIM_BUCKETS) sh.head[threadIdx.x] = 0;
+    const Worklist wl{a.ctrl->bq_tail, a.queue, (size_t)n, 0, n};
     int64_t r = 0;
     for (;;) {
         r++;
         const uint32_t stamp = a.stamp0 + (uint32_t)r;
         const int par = (int)(r & 1);
-        // select: every CTA pops the same label from the lowest non-empty bucket
-        if (threadIdx.x < 32) {
-            const unsigned long long h = sh.head[lane];
-            const bool ne = h < ldcg(&a.ctrl->bq_tail[lane]);
-            const unsigned bal = __ballot_sync(0xffffffffu, ne);
-            if (bal == 0u) {
-                if (lane == 0) sh.C = -1;
-            } else if (lane == __ffs(bal) - 1) {
-                sh.C = ldcg(&a.queue[(size_t)lane * n + h % (unsigned long long)n]);
-                sh.head[lane] = h + 1;
-            }
-        }
-        __syncthreads();
-        const int32_t C = sh.C;
-        __syncthreads();
+        // every CTA pops the same label
+        const int32_t C = select_splitter(wl, sh.head, sh);
         if (C < 0) break;  // no unstable label: C = bottom
         if (r > a.round_cap) {
             if (gtid == 0) atomicOr(&a.ctrl->status, ST_ROUNDS);
@@ -366,47 +425,93 @@ __global__ void __launch_bounds__(1024) k_frontier_main(FrontierArgs a) {
             a.ctrl->n_touched[par ^ 1] = 0;
             a.ctrl->n_mid[par ^ 1] = 0;
         }
-        // mark: one warp per member of C, lanes over its incoming transitions
-        {
-            const int32_t b0 = ldcg(&a.bbeg[C]), e0 = ldcg(&a.bend[C]);
-            for (int64_t idx = b0 + gw; idx < e0; idx += nwarps) {
-                const int32_t t = ldcg(&a.elems[idx]);
-                const int32_t j0 = a.in_ptr[t], j1 = a.in_ptr[t + 1];
-                if (lane == 0) edges += j1 - j0;
-                for (int32_t j = j0 + lane; j < j1; j += 32) {
-                    const unsigned long long e = a.in_edge[j];
-                    const int32_t s = (int32_t)(e >> 32);
-                    a.mark[(uint32_t)e] = stamp;
-                    if (ldcg(&a.smark[s]) == stamp) continue;
-                    if (atomicExch(&a.smark[s], stamp) == stamp) continue;
-                    const int32_t b = ldcg(&a.block[s]);
-                    const int32_t bb = ldcg(&a.bbeg[b]), be = ldcg(&a.bend[b]);
-                    if (be - bb <= 1) continue;
-                    const int32_t rk = atomicAdd(&a.mcnt[b], 1);
-                    a.mscr[be - 1 - rk] = s;
-                    if (rk == 0) {
-                        if (be - bb <= WARP_MAX)
-                            a.tlist[atomicAdd(&a.ctrl->n_touched[par], 1)] = b;
-                        else
-                            a.tlist[n + atomicAdd(&a.ctrl->n_mid[par], 1)] = b;
-                    }
-                }
-            }
-        }
+        mark_step(a, C, stamp, gw, nwarps, &a.ctrl->n_touched[par], &a.ctrl->n_mid[par], a.tlist,
+                  a.tlist + n, edges);
         if (!grid_sync(a.gb, tgt)) return;
-        // split
         {
             const int32_t ns = ldcg(&a.ctrl->n_touched[par]);
             const int32_t nm = ldcg(&a.ctrl->n_mid[par]);
-            for (int64_t i = gw; i < ns; i += nwarps) warp_split(a, ldcg(&a.tlist[i]), stamp, C, states);
+            for (int64_t i = gw; i < ns; i += nwarps) warp_split(a, wl, ldcg(&a.tlist[i]), stamp, C, states);
             for (int32_t i = blockIdx.x; i < nm; i += gridDim.x)
-                cta_split(a, sh, ldcg(&a.tlist[n + i]), stamp, C, states);
+                cta_split(a, wl, sh, ldcg(&a.tlist[n + i]), stamp, C, states);
         }
         if (!grid_sync(a.gb, tgt)) return;
     }
     if (edges) atomicAdd((unsigned long long*)&a.ctrl->edges, (unsigned long long)edges);
     if (states) atomicAdd((unsigned long long*)&a.ctrl->states, (unsigned long long)states);
     if (gtid == 0) a.ctrl->rounds = r;
+}
+
+// Many LTSs in one launch, one CTA per LTS at a time: the same rounds, with
+// __syncthreads in place of the grid barrier and the worklist cursors in
+// shared memory. LTS i owns states, labels and member positions
+// [state_off[i], state_off[i+1]) of the batch arrays; CTAs take LTSs from a
+// counter in `order` (largest first). Nothing waits on another CTA, so the
+// launch is an ordinary one and may overlap other work.
+struct BatchArgs {
+    int32_t k;
+    const int64_t* __restrict__ state_off;  // [k+1]
+    const int32_t* __restrict__ order;      // [k] LTS indices, largest first
+    const int32_t* __restrict__ num_act;    // [k]
+    int* next;                              // LTS counter
+    long long* inst_rounds;                 // [k] out
+    int32_t* block0;
+};
+
+__global__ void __launch_bounds__(1024) k_frontier_batch(FrontierArgs a, BatchArgs bt) {
+    __shared__ CtaShared sh;
+    __shared__ unsigned long long s_tail[BISIM_BUCKETS];
+    __shared__ int s_ns, s_nm, s_inst;
+    const int64_t gw = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    long long edges = 0, states = 0;
+    for (;;) {
+        if (threadIdx.x == 0) s_inst = atomicAdd(bt.next, 1);
+        __syncthreads();
+        const int inst = s_inst;
+        __syncthreads();
+        if (inst >= bt.k) break;
+        const int32_t li = bt.order[inst];
+        const int32_t s0 = (int32_t)bt.state_off[li];
+        const int32_t ni = (int32_t)(bt.state_off[li + 1] - s0);
+        if (threadIdx.x < BISIM_BUCKETS) {
+            s_tail[threadIdx.x] = 0;
+            sh.head[threadIdx.x] = 0;
+        }
+        __syncthreads();
+        const Worklist wl{s_tail, a.queue, (size_t)a.n, s0, max(ni, 1)};
+        // Algorithm 3, lines 1-3: every label of this LTS is unstable
+        for (int32_t l = s0 + threadIdx.x; l < s0 + ni; l += blockDim.x)
+            if (bt.block0[l] == l) push(a, wl, l);
+        __syncthreads();
+        const int64_t cap = 3ll * ni + bt.num_act[li] + 2;
+        int64_t r = 0;
+        for (;;) {
+            r++;
+            const uint32_t stamp = a.stamp0 + (uint32_t)r;
+            const int32_t C = select_splitter(wl, sh.head, sh);
+            if (C < 0) break;
+            if (r > cap) {
+                if (threadIdx.x == 0) atomicOr(&a.ctrl->status, ST_ROUNDS);
+                break;
+            }
+            if (threadIdx.x == 0) {
+                a.unstable[C] = 0u;
+                s_ns = 0;
+                s_nm = 0;
+            }
+            __syncthreads();
+            mark_step(a, C, stamp, gw, nwarps, &s_ns, &s_nm, a.tlist + s0, a.tlist + a.n + s0, edges);
+            __syncthreads();
+            const int ns = s_ns, nm = s_nm;
+            for (int i = (int)gw; i < ns; i += (int)nwarps) warp_split(a, wl, ldcg(&a.tlist[s0 + i]), stamp, C, states);
+            for (int i = 0; i < nm; i++) cta_split(a, wl, sh, ldcg(&a.tlist[a.n + s0 + i]), stamp, C, states);
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) bt.inst_rounds[li] = r;
+        __syncthreads();
+    }
+    if (edges) atomicAdd((unsigned long long*)&a.ctrl->edges, (unsigned long long)edges);
+    if (states) atomicAdd((unsigned long long*)&a.ctrl->states, (unsigned long long)states);
 }
 
 // ---------------------------------------------------------------- set-up
@@ -471,52 +576,50 @@ int ensure_frontier(bisim_plan_s* p) {
     return BISIM_OK;
 }
 
-}  // namespace
-
-namespace bisim {
-
-int refine_frontier(bisim_plan_s* p, bisim_stats* stats) {
+// Grouped member array, ranges, loc, labels and unstable flags from block0;
+// with fill_queue, also the global worklist (grid engine).
+int frontier_setup(bisim_plan_s* p, bool fill_queue) {
     const int32_t n = p->n;
     cudaStream_t st = p->st;
     BISIM_TRY(ensure_frontier(p));
-    const int64_t cap = p->opts.round_cap > 0 ? p->opts.round_cap : 3ll * n + p->A + 2;
-    uint32_t base;
-    BISIM_TRY(reserve_stamps(p, cap + 1, &base));
     bisim_ctrl* c = p->ctrl.as<bisim_ctrl>();
     BISIM_CUDA_TRY(cudaMemsetAsync(c, 0, sizeof(bisim_ctrl), st));
     BISIM_CUDA_TRY(cudaMemsetAsync(p->mcnt.p, 0, 4 * (size_t)n, st));
-    {
-        DevMem keys, vals, keys2, flags;
-        BISIM_TRY(keys.alloc(4 * (size_t)n, st));
-        BISIM_TRY(vals.alloc(4 * (size_t)n, st));
-        BISIM_TRY(keys2.alloc(4 * (size_t)n, st));
-        BISIM_TRY(flags.alloc(4 * (size_t)n, st));
-        const unsigned gn = grid_for(n, 256);
-        k_front_init<<<gn, 256, 0, st>>>(p->block0.as<int32_t>(), n, p->block.as<int32_t>(),
-                                         p->unstable.as<uint32_t>(), keys.as<uint32_t>(),
-                                         vals.as<uint32_t>(), flags.as<uint32_t>());
-        BISIM_LAUNCHED();
-        BISIM_CUDA_TRY(cudaGetLastError());
-        // members grouped by label: sort (label, state)
-        uint32_t* el = p->elems.as<uint32_t>();
-        bool alt = false;
-        BISIM_TRY(radix_sort_pairs<uint32_t, uint32_t>(keys.as<uint32_t>(), vals.as<uint32_t>(),
-                                                       keys2.as<uint32_t>(), el, n,
-                                                       ceil_log2_u64((uint64_t)n), st, &alt));
-        uint32_t* skeys = alt ? keys2.as<uint32_t>() : keys.as<uint32_t>();
-        if (!alt) BISIM_CUDA_TRY(cudaMemcpyAsync(el, vals.p, 4 * (size_t)n, cudaMemcpyDeviceToDevice, st));
-        k_front_ranges<<<gn, 256, 0, st>>>(skeys, p->elems.as<int32_t>(), n, p->bbeg.as<int32_t>(),
-                                           p->bend.as<int32_t>(), p->loc.as<int32_t>());
-        BISIM_LAUNCHED();
-        BISIM_CUDA_TRY(cudaGetLastError());
-        // worklist: all labels
-        k_front_queue<<<gn, 256, 0, st>>>(flags.as<uint32_t>(), p->bbeg.as<int32_t>(),
-                                          p->bend.as<int32_t>(), n, c, p->queue.as<int32_t>());
+    DevMem keys, vals, keys2, flags;
+    BISIM_TRY(keys.alloc(4 * (size_t)n, st));
+    BISIM_TRY(vals.alloc(4 * (size_t)n, st));
+    BISIM_TRY(keys2.alloc(4 * (size_t)n, st));
+    BISIM_TRY(flags.alloc(4 * (size_t)n, st));
+    const unsigned gn = grid_for(n, 256);
+    k_front_init<<<gn, 256, 0, st>>>(p->block0.as<int32_t>(), n, p->block.as<int32_t>(),
+                                     p->unstable.as<uint32_t>(), keys.as<uint32_t>(), vals.as<uint32_t>(),
+                                     flags.as<uint32_t>());
+    BISIM_LAUNCHED();
+    BISIM_CUDA_TRY(cudaGetLastError());
+    // members grouped by label: sort (label, state)
+    uint32_t* el = p->elems.as<uint32_t>();
+    bool alt = false;
+    BISIM_TRY(radix_sort_pairs<uint32_t, uint32_t>(keys.as<uint32_t>(), vals.as<uint32_t>(), keys2.as<uint32_t>(),
+                                                   el, n, ceil_log2_u64((uint64_t)n), st, &alt));
+    uint32_t* skeys = alt ? keys2.as<uint32_t>() : keys.as<uint32_t>();
+    if (!alt) BISIM_CUDA_TRY(cudaMemcpyAsync(el, vals.p, 4 * (size_t)n, cudaMemcpyDeviceToDevice, st));
+    k_front_ranges<<<gn, 256, 0, st>>>(skeys, p->elems.as<int32_t>(), n, p->bbeg.as<int32_t>(),
+                                       p->bend.as<int32_t>(), p->loc.as<int32_t>());
+    BISIM_LAUNCHED();
+    BISIM_CUDA_TRY(cudaGetLastError());
+    if (fill_queue) {
+        k_front_queue<<<gn, 256, 0, st>>>(flags.as<uint32_t>(), p->bbeg.as<int32_t>(), p->bend.as<int32_t>(), n,
+                                          c, p->queue.as<int32_t>());
         BISIM_LAUNCHED();
         BISIM_CUDA_TRY(cudaGetLastError());
     }
+    return BISIM_OK;
+}
+
+FrontierArgs make_args(bisim_plan_s* p, uint32_t base, int64_t cap) {
     FrontierArgs a;
-    a.n = n;
+    bisim_ctrl* c = p->ctrl.as<bisim_ctrl>();
+    a.n = p->n;
     a.off = p->off.as<int32_t>();
     a.in_ptr = p->in_ptr.as<int32_t>();
     a.in_edge = p->in_edge.as<unsigned long long>();
@@ -542,6 +645,29 @@ int refine_frontier(bisim_plan_s* p, bisim_stats* stats) {
     a.round_cap = cap;
     a.alg2 = (p->opts.rcpp_alg2 && p->A == 1) ? 1 : 0;
     a.test_hook = p->opts.test_hook;
+    return a;
+}
+
+int report(bisim_plan_s* p) {
+    int code = status_to_code(p->ctrl_h->status);
+    if (code)
+        set_last_error(p->ctrl_h->status & ST_TIMEOUT ? "grid barrier wait timed out"
+                       : p->ctrl_h->status & ST_ROUNDS ? "round cap exceeded"
+                                                       : "internal consistency check failed");
+    return code;
+}
+
+}  // namespace
+
+namespace bisim {
+
+int refine_frontier(bisim_plan_s* p, bisim_stats* stats) {
+    const int32_t n = p->n;
+    const int64_t cap = p->opts.round_cap > 0 ? p->opts.round_cap : 3ll * n + p->A + 2;
+    uint32_t base;
+    BISIM_TRY(reserve_stamps(p, cap + 1, &base));
+    BISIM_TRY(frontier_setup(p, true));
+    FrontierArgs a = make_args(p, base, cap);
     const int threads = p->opts.threads > 0 ? p->opts.threads : 512;
     void* args[] = {&a};
     int grid = 0;
@@ -556,14 +682,56 @@ int refine_frontier(bisim_plan_s* p, bisim_stats* stats) {
         stats->engine = BISIM_ENGINE_FRONTIER;
         stats->grid_ctas = grid;
     }
-    int code = status_to_code(p->ctrl_h->status);
-    if (code) {
-        set_last_error(p->ctrl_h->status & ST_TIMEOUT ? "grid barrier wait timed out"
-                       : p->ctrl_h->status & ST_ROUNDS ? "round cap exceeded"
-                                                       : "internal consistency check failed");
-        return code;
+    return report(p);
+}
+
+int refine_frontier_batch(bisim_plan_s* p, bisim_stats* stats, std::vector<long long>& rounds) {
+    const int32_t k = p->batch_k;
+    cudaStream_t st = p->st;
+    int64_t cap = 0;
+    for (int32_t i = 0; i < k; i++)
+        cap = std::max<int64_t>(cap, 3ll * (p->state_off_h[i + 1] - p->state_off_h[i]) + p->batch_act_h[i] + 2);
+    uint32_t base;
+    BISIM_TRY(reserve_stamps(p, cap + 1, &base));
+    BISIM_TRY(frontier_setup(p, false));
+    FrontierArgs a = make_args(p, base, cap);
+    BatchArgs bt;
+    bt.k = k;
+    bt.state_off = p->state_off.as<int64_t>();
+    bt.order = p->batch_order.as<int32_t>();
+    bt.num_act = p->batch_act.as<int32_t>();
+    bt.next = &p->ctrl.as<bisim_ctrl>()->next_inst;
+    bt.inst_rounds = p->inst_rounds.as<long long>();
+    bt.block0 = p->block0.as<int32_t>();
+    const int threads = p->opts.threads > 0 ? p->opts.threads : 256;
+    int occ = 0;
+    BISIM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_frontier_batch, threads, 0));
+    int per_sm = p->opts.ctas_per_sm > 0 ? std::min(p->opts.ctas_per_sm, occ) : occ;
+    int grid = std::max(1, std::min(k, p->sm_count * std::max(per_sm, 1)));
+    if (p->opts.max_ctas > 0) grid = std::min(grid, p->opts.max_ctas);
+    BISIM_CUDA_TRY(cudaEventRecord(p->evk0, st));
+    k_frontier_batch<<<grid, threads, 0, st>>>(a, bt);
+    BISIM_LAUNCHED();
+    BISIM_CUDA_TRY(cudaGetLastError());
+    BISIM_CUDA_TRY(cudaEventRecord(p->evk1, st));
+    rounds.assign((size_t)k, 0);
+    if (k) BISIM_CUDA_TRY(cudaMemcpyAsync(rounds.data(), p->inst_rounds.p, 8 * (size_t)k, cudaMemcpyDeviceToHost, st));
+    BISIM_TRY(read_ctrl(p));
+    long long rmax = 0, rsum = 0;
+    for (long long r : rounds) {
+        rmax = std::max(rmax, r);
+        rsum += r;
     }
-    return BISIM_OK;
+    p->stamp = base + (uint32_t)std::min<long long>(rmax + 1, cap + 1);
+    if (stats) {
+        BISIM_TRY(persistent_ms(p, &stats->t_main_ms));
+        stats->rounds = rsum;
+        stats->edges_visited = p->ctrl_h->edges;
+        stats->states_visited = p->ctrl_h->states;
+        stats->engine = BISIM_ENGINE_FRONTIER;
+        stats->grid_ctas = grid;
+    }
+    return report(p);
 }
 
 }  // namespace bisim
