@@ -193,6 +193,142 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+STREAM_DESC = ("batched stream (seed 4): LTSs with n log-uniform in [100, 200000], m = 5n, |Act| in "
+               "[1, 32], quotient expansion with n/20 classes")
+
+
+def run_stream(args, world, rank, local):
+    """Stream workload: one step = batch plan + batch refine of all LTSs
+    (inputs resident); plus the one-at-a-time rate on a sample, the serving
+    loop at 0.5x / 1x / 2x that rate, and the oracle on a sample."""
+    import torch
+
+    from paper_2105_11788_gb300 import bisim, serve
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    bisim.load(build_if_missing=True)
+    t_gen = time.perf_counter()
+    ltss, _ = lts_gen.batch_stream(seed=4, k=args.stream_k)
+    t_gen = time.perf_counter() - t_gen
+    k = len(ltss)
+    so, to, na, src, act, dst, init = bisim.pack_batch(ltss)
+    N, M = int(so[-1]), int(to[-1])
+    opts = bisim.make_opts(threads=args.threads, max_ctas=args.max_ctas)
+    d = lambda a: torch.from_numpy(a).to(dev)  # noqa: E731
+    tsrc, tact, tdst = d(src), d(act), d(dst)
+    out = torch.empty(N, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    sp = int(stream.cuda_stream)
+
+    def step():
+        h = bisim.bisim_batch_plan(k, so, to, na, tsrc.data_ptr(), tact.data_ptr(), tdst.data_ptr(), None,
+                                   opts, sp)
+        try:
+            return bisim.bisim_batch_refine(h, out.data_ptr(), k)
+        finally:
+            bisim.bisim_plan_destroy(h)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0])
+    clocks.start()
+    barrier(world)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    total_ms, kern_ms, stats = 0.0, [], []
+    for _ in range(args.steps):
+        e0.record(stream)
+        st, inst = step()
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        kern_ms.append(st.t_main_ms)
+        stats.append(st)
+    barrier(world)
+    clk = clocks.stop()
+    ms_step = max_over_ranks(total_ms / args.steps, world, dev)
+    value = world * k * 1000.0 / ms_step
+    st = stats[-1]
+    # end to end from pinned host buffers (copies inside the timed region)
+    pin = lambda a: torch.from_numpy(a).pin_memory()  # noqa: E731
+    hsrc, hact, hdst = pin(src), pin(act), pin(dst)
+    hout = torch.empty(N, dtype=torch.int32).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tsrc.copy_(hsrc, non_blocking=True)
+    tact.copy_(hact, non_blocking=True)
+    tdst.copy_(hdst, non_blocking=True)
+    step()
+    hout.copy_(out, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_ms = 1000 * (time.perf_counter() - t0)
+    # one at a time on a sample
+    rng = np.random.default_rng(0)
+    sample = rng.choice(k, size=min(args.plain_sample, k), replace=False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in sample:
+        bisim.reduce(ltss[i], device=dev)
+    plain_s = time.perf_counter() - t0
+    plain_rate = len(sample) / plain_s
+    # serving loop at 0.5x, 1x and 2x the one-at-a-time rate
+    serving = {}
+    if args.serve_requests > 0:
+        sub = [ltss[i] for i in rng.choice(k, size=min(args.serve_requests, k), replace=False)]
+        for mult in (0.5, 1.0, 2.0):
+            reqs = serve.poisson_requests(sub, rate_per_s=mult * plain_rate, seed=int(mult * 10))
+            srv = serve.BatchServer(serve.gpu_executor(device=str(dev)), mem_budget=64 << 30, workers=3,
+                                    max_batch=256)
+            res = srv.serve(reqs)
+            serving[f"{mult}x"] = dict(serve.latency_summary(res), rate_per_s=mult * plain_rate)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+
+        t0 = time.perf_counter()
+        cnt = 0
+        for i in rng.permutation(k):
+            oracle.ks_lts(ltss[i])
+            cnt += 1
+            if time.perf_counter() - t0 > args.cpu_budget:
+                break
+        el = time.perf_counter() - t0
+        cpu = {"value": cnt / el, "unit": "LTS/s", "cores": 1, "kind": "oracle",
+               "sample": f"{cnt} LTSs of the stream in random order reduced by oracle_ks "
+                         f"(single-threaded C), {el:.1f} s"}
+    hbm, peak_kind = read_peaks()
+    bytes_launch = frontier_bytes_per_launch(st)
+    km = sum(kern_ms) / len(kern_ms)
+    achieved = bytes_launch / (km * 1e-3) / 1e9
+    if rank == 0:
+        line = {
+            "metric": "batched LTS reduction throughput", "value": value, "unit": "LTS/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": STREAM_DESC, "k": k, "n_total": N, "m_total": M,
+                       "l2": "inputs larger than L2",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "roofline": {"bound": "hbm", "kernel": "k_frontier_batch", "achieved": achieved, "peak": hbm,
+                         "unit": "GB/s", "frac": achieved / hbm, "peak_kind": peak_kind, "traffic": None,
+                         "kernel_ms": km, "bytes_per_launch": bytes_launch},
+            "e2e": {"value": world * k * 1000.0 / e2e_ms, "unit": "LTS/s",
+                    "h2d_bytes_per_step": int(src.nbytes + act.nbytes + dst.nbytes),
+                    "d2h_bytes_per_step": int(4 * N), "ms_per_step": e2e_ms},
+            "cpu_baseline": cpu,
+            "gpu_launches": int(sum(s.launches for s in stats)),
+            "clocks": clk,
+            "detail": {"plain_one_at_a_time_lts_per_s": plain_rate, "plain_sample": int(len(sample)),
+                       "batched_over_plain": value / plain_rate, "serving": serving,
+                       "t_plan_ms": st.t_plan_ms, "t_refine_ms": st.t_refine_ms, "t_main_ms": st.t_main_ms,
+                       "rounds_total": st.rounds, "edges_visited": st.edges_visited,
+                       "states_visited": st.states_visited, "grid_ctas": st.grid_ctas,
+                       "generation_s": t_gen},
+        }
+        print(json.dumps(line), flush=True)
+
+
 def cpu_baseline(lts, budget_s):
     import oracle
 
@@ -215,7 +351,12 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="qexp", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="qexp", choices=sorted(WORKLOADS) + ["stream"])
+    ap.add_argument("--stream-k", type=int, default=4096, help="LTSs in the stream workload")
+    ap.add_argument("--plain-sample", type=int, default=128,
+                    help="stream: LTSs reduced one at a time to estimate the plain rate")
+    ap.add_argument("--serve-requests", type=int, default=256,
+                    help="stream: requests per arrival rate in the serving run")
     ap.add_argument("--engine", default="auto", choices=["auto", "dense", "frontier"])
     ap.add_argument("--threads", type=int, default=0, help="threads per CTA (0 = library default)")
     ap.add_argument("--max-ctas", type=int, default=0, help="cap on persistent-kernel CTAs")
@@ -225,6 +366,9 @@ def main():
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if args.workload == "stream":
+        run_stream(args, world, rank, local)
         return
 
     import torch

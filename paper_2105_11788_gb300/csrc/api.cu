@@ -20,7 +20,7 @@ using namespace bisim;
 static int choose_engine(const bisim_plan_s* p) {
     int e = p->opts.engine;
     if (e == BISIM_ENGINE_DENSE || e == BISIM_ENGINE_FRONTIER) return e;
-    return BISIM_ENGINE_DENSE;
+    return BISIM_ENGINE_FRONTIER;
 }
 
 static void fill_static_stats(const bisim_plan_s* p, bisim_stats* s) {
