@@ -72,7 +72,10 @@ typedef struct bisim_opts {
     int64_t timeout_ms;  /* limit on one grid-barrier wait (0 = 2000 ms) */
     int32_t max_ctas;    /* cap on the CTAs of the persistent launches (0 = no cap;
                             fewer CTAs make the grid barrier cheaper) */
-    int32_t reserved;
+    int32_t light_edges; /* frontier engine: a round whose splitter has at most 32
+                            members and at most this many incoming transitions runs
+                            on one CTA without grid barriers (0 = 256; negative =
+                            every round on the whole grid) */
 } bisim_opts;
 
 typedef struct bisim_stats {

@@ -6,7 +6,7 @@
 //    starts gives slot = off(source) + order for every transition, nr_marks
 //    is the number of pairs of a state and off their exclusive prefix sum;
 //  - the incoming-transition CSR by target, every entry carrying (source,
-//    slot), built with a second stable radix sort;
+//    slot), built with a counting sort;
 //  - initial leaders (Algorithm 2, lines 1-6, priority rule: the smallest
 //    member of each initial block);
 //  - action-set preprocessing (Algorithm 5): for every label that occurs, in
@@ -88,6 +88,23 @@ __global__ void k_slots(const K* __restrict__ keys, const uint32_t* __restrict__
     }
 }
 
+__global__ void k_csr_scatter(const uint32_t* __restrict__ tkey, const uint64_t* __restrict__ tval, int64_t m,
+                              uint32_t* cursor, uint64_t* in_edge) {
+    const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gsz)
+        in_edge[atomicAdd(&cursor[tkey[i]], 1u)] = tval[i];
+}
+
+// label set of every state as a bitmask of mask_words 32-bit words
+__global__ void k_label_masks(const int32_t* __restrict__ slot_src, const int32_t* __restrict__ slot_act,
+                              int64_t L, int mask_words, uint32_t* amask) {
+    const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < L; k += gsz) {
+        const int32_t a = slot_act[k];
+        atomicOr(&amask[(size_t)slot_src[k] * mask_words + (a >> 5)], 1u << (a & 31));
+    }
+}
+
 __global__ void k_fill_i32(int32_t* p, int64_t n, int32_t v) {
     const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gsz) p[i] = v;
@@ -122,11 +139,16 @@ struct LabelArgs {
     uint32_t* lmark;
     unsigned long long* nl64;
     uint8_t* split;
+    const uint32_t* amask;  // label sets as bitmasks (NULL: mark by scanning the slots)
+    int mask_words;
     uint32_t stamp0;
     GridBarrier gb;
 };
 
-// Algorithm 5: one round per label, three grid barriers per round.
+// Algorithm 5: one round per label that occurs. The mark of state s in the
+// round of label a is "s has an a-transition": read from the state's label
+// bitmask when there is one (two grid barriers per round), else written by
+// one thread per mark slot (three).
 __global__ void k_label_rounds(LabelArgs a) {
     const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
@@ -134,13 +156,23 @@ __global__ void k_label_rounds(LabelArgs a) {
     for (int li = 0; li < a.n_labels; li++) {
         const int32_t lab = a.labels[li];
         const uint32_t stamp = a.stamp0 + (uint32_t)li + 1u;
-        for (int64_t k = gtid; k < a.L; k += gsz)
-            if (a.slot_act[k] == lab) a.lmark[a.slot_src[k]] = stamp;
-        if (!grid_sync(a.gb, tgt)) return;
+        if (!a.amask) {
+            for (int64_t k = gtid; k < a.L; k += gsz)
+                if (a.slot_act[k] == lab) a.lmark[a.slot_src[k]] = stamp;
+            if (!grid_sync(a.gb, tgt)) return;
+        }
+        const int w = lab >> 5;
+        const uint32_t bit = 1u << (lab & 31);
         for (int64_t s = gtid; s < a.n; s += gsz) {
             const int32_t b = a.block[s];
-            const bool ms = ldcg(&a.lmark[s]) == stamp;
-            const bool mb = ldcg(&a.lmark[b]) == stamp;
+            bool ms, mb;
+            if (a.amask) {
+                ms = (a.amask[(size_t)s * a.mask_words + w] & bit) != 0u;
+                mb = (a.amask[(size_t)b * a.mask_words + w] & bit) != 0u;
+            } else {
+                ms = ldcg(&a.lmark[s]) == stamp;
+                mb = ldcg(&a.lmark[b]) == stamp;
+            }
             const uint8_t sp = ms != mb;
             a.split[s] = sp;
             if (sp) atomicMin(&a.nl64[b], elect_key(stamp, (int32_t)s));
@@ -330,11 +362,9 @@ int plan_build(bisim_plan_s* p, const int32_t* src, const int32_t* act, const in
     BISIM_TRY(p->in_ptr.alloc(4 * ((size_t)n + 1), st));
     BISIM_CUDA_TRY(cudaMemsetAsync(p->off.p, 0, 4 * ((size_t)n + 1), st));
     BISIM_CUDA_TRY(cudaMemsetAsync(p->in_ptr.p, 0, 4 * ((size_t)n + 1), st));
-    DevMem tkey, tkey_alt, tval, tval_alt;
+    DevMem tkey, tval;
     BISIM_TRY(tkey.alloc(4 * (size_t)m, st));
-    BISIM_TRY(tkey_alt.alloc(4 * (size_t)m, st));
     BISIM_TRY(tval.alloc(8 * (size_t)m, st));
-    BISIM_TRY(tval_alt.alloc(8 * (size_t)m, st));
     if (wide)
         k_slots<uint64_t><<<gm, T, 0, st>>>((const uint64_t*)skeys, sdst, flags.as<uint32_t>(), m, A,
                                             p->slot_src.as<int32_t>(), p->slot_act.as<int32_t>(),
@@ -354,19 +384,21 @@ int plan_build(bisim_plan_s* p, const int32_t* src, const int32_t* act, const in
     BISIM_TRY(scan_exclusive_u32(p->in_ptr.as<uint32_t>(), p->in_ptr.as<uint32_t>(), (int64_t)n + 1,
                                  nullptr, st));
 
-    // a3: incoming transitions grouped by target (stable: by source, label inside)
-    bool alt2 = false;
-    BISIM_TRY(radix_sort_pairs<uint32_t, uint64_t>(tkey.as<uint32_t>(), tval.as<uint64_t>(),
-                                                   tkey_alt.as<uint32_t>(), tval_alt.as<uint64_t>(),
-                                                   m, ceil_log2_u64((uint64_t)n), st, &alt2));
-    if (alt2) {
-        std::swap(tval.p, tval_alt.p);
+    // a3: incoming transitions grouped by target (counting sort; the order
+    // inside one target's list is whatever the atomics give: marking is
+    // idempotent, so it never matters)
+    {
+        DevMem cursor;
+        BISIM_TRY(cursor.alloc(4 * ((size_t)n + 1), st));
+        BISIM_CUDA_TRY(cudaMemcpyAsync(cursor.p, p->in_ptr.p, 4 * ((size_t)n + 1), cudaMemcpyDeviceToDevice, st));
+        BISIM_TRY(p->in_edge.alloc(8 * (size_t)m, st));
+        k_csr_scatter<<<gm, T, 0, st>>>(tkey.as<uint32_t>(), tval.as<uint64_t>(), m, cursor.as<uint32_t>(),
+                                        p->in_edge.as<uint64_t>());
+        BISIM_LAUNCHED();
+        BISIM_CUDA_TRY(cudaGetLastError());
     }
-    tkey.release(); tkey_alt.release(); tval_alt.release();
-    // keep the sorted payload as in_edge
-    std::swap(p->in_edge.p, tval.p);
-    std::swap(p->in_edge.bytes, tval.bytes);
-    p->in_edge.st = st;
+    tkey.release();
+    tval.release();
 
     if (!labels_h.empty()) {
         BISIM_TRY(p->labels.alloc(4 * labels_h.size(), st));
@@ -423,6 +455,18 @@ int plan_build(bisim_plan_s* p, const int32_t* src, const int32_t* act, const in
         a.nl64 = p->nl64.as<unsigned long long>();
         a.split = p->split.as<uint8_t>();
         a.stamp0 = base;
+        DevMem amask;
+        a.amask = nullptr;
+        a.mask_words = (A + 31) / 32;
+        if (a.mask_words <= 4) {  // up to 128 labels: 16 B or less per state
+            BISIM_TRY(amask.alloc(4 * (size_t)a.mask_words * n, st));
+            BISIM_CUDA_TRY(cudaMemsetAsync(amask.p, 0, 4 * (size_t)a.mask_words * n, st));
+            k_label_masks<<<grid_for(L, T), T, 0, st>>>(a.slot_src, a.slot_act, L, a.mask_words,
+                                                        amask.as<uint32_t>());
+            BISIM_LAUNCHED();
+            BISIM_CUDA_TRY(cudaGetLastError());
+            a.amask = amask.as<uint32_t>();
+        }
         a.gb.counter = &p->ctrl.as<bisim_ctrl>()->barrier;
         a.gb.status = status;
         a.gb.timeout_ns = (unsigned long long)(p->opts.timeout_ms > 0 ? p->opts.timeout_ms : 2000) * 1000000ull;

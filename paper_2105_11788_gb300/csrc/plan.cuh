@@ -24,6 +24,11 @@ struct bisim_ctrl {
     unsigned long long bq_tail[32];  // frontier worklist: pushes per size bucket
     int next_inst;                   // batch engine: next LTS to take
     int pad2;
+    // hybrid engine: CTA 0 publishes heavy rounds to the parked CTAs
+    unsigned long long cmd_seq;      // number of commands published
+    unsigned long long heartbeat;    // rounds CTA 0 has finished (progress for the parked CTAs' limit)
+    int cmd_C;                       // splitter of the published heavy round, -1 = stop
+    unsigned cmd_stamp;              // its round stamp
 };
 
 // Frontier worklist: one FIFO ring of n entries per size bucket

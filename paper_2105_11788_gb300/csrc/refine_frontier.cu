@@ -85,11 +85,13 @@ __device__ __forceinline__ void set_unstable(const FrontierArgs& a, const Workli
     if (atomicExch(&a.unstable[label], 1u) == 0u) push(a, wl, label);
 }
 
-__device__ __forceinline__ void finish_split(const FrontierArgs& a, const Worklist& wl, int32_t b,
-                                             int32_t leader, int32_t C) {
-    set_unstable(a, wl, b);
-    set_unstable(a, wl, leader);
-    if (!a.alg2) set_unstable(a, wl, C);
+// finish_split by a whole warp: the (up to) three labels are pushed by three
+// lanes at once. The caller's stores of the new ranges precede a __syncwarp.
+__device__ __forceinline__ void finish_split_warp(const FrontierArgs& a, const Worklist& wl, int32_t b,
+                                                  int32_t leader, int32_t C) {
+    const unsigned lane = threadIdx.x & 31u;
+    const int32_t lab = lane == 0 ? b : lane == 1 ? leader : (lane == 2 && !a.alg2) ? C : -1;
+    if (lab >= 0) set_unstable(a, wl, lab);
 }
 
 // Does s have the same marks as the leader (lo = off[leader], k slots)?
@@ -160,8 +162,9 @@ __device__ void warp_split(const FrontierArgs& a, const Worklist& wl, int32_t b,
         a.bend[b] = b0 + nkeep;
         a.bbeg[leader] = b0 + nkeep;
         a.bend[leader] = e0;
-        finish_split(a, wl, b, leader, C);
     }
+    __syncwarp();
+    finish_split_warp(a, wl, b, leader, C);
 }
 
 struct CtaShared {
@@ -287,12 +290,15 @@ __device__ void cta_split(const FrontierArgs& a, const Worklist& wl, CtaShared& 
         for (int32_t i = threadIdx.x; i < km; i += blockDim.x) a.block[ldcg(&a.mscr[t0 + i])] = leader;
         __syncthreads();
         cta_gather_range(a, sh, t0, km, t0, [&](int32_t u) { return ldcg(&a.smark[u]) == stamp; });
-        if (threadIdx.x == 0) {
-            states += km;
-            a.bend[b] = t0;
-            a.bbeg[leader] = t0;
-            a.bend[leader] = e0;
-            finish_split(a, wl, b, leader, C);
+        if (threadIdx.x < 32) {
+            if (threadIdx.x == 0) {
+                states += km;
+                a.bend[b] = t0;
+                a.bbeg[leader] = t0;
+                a.bend[leader] = e0;
+            }
+            __syncwarp();
+            finish_split_warp(a, wl, b, leader, C);
         }
         __syncthreads();
         return;
@@ -329,14 +335,147 @@ __device__ void cta_split(const FrontierArgs& a, const Worklist& wl, CtaShared& 
     const int32_t leader = cta_min(mn, sh);
     for (int32_t q = b0 + kk + threadIdx.x; q < e0; q += blockDim.x) a.block[ldcg(&a.elems[q])] = leader;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        states += sz - kk;
+    if (threadIdx.x < 32) {
+        if (threadIdx.x == 0) {
+            states += sz - kk;
+            a.bend[b] = b0 + kk;
+            a.bbeg[leader] = b0 + kk;
+            a.bend[leader] = e0;
+        }
+        __syncwarp();
+        finish_split_warp(a, wl, b, leader, C);
+    }
+    __syncthreads();
+}
+
+// Warp version of the gather: lanes l < cnt hold the members s_l of a set
+// (cnt <= 32) that must end up at positions [r0, r0 + cnt). Members outside
+// the range swap with the non-members inside it, paired by rank.
+template <typename InSet>
+__device__ __forceinline__ void warp_gather(const FrontierArgs& a, int32_t s, int32_t cnt, int32_t r0,
+                                            InSet in_set) {
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned lt = lanemask_lt();
+    const bool mine = (int)lane < cnt;
+    const int32_t p = mine ? ldcg(&a.loc[s]) : -1;
+    const bool x = mine && (p < r0 || p >= r0 + cnt);
+    const int32_t q = r0 + (int32_t)lane;
+    const bool y = mine && !in_set(ldcg(&a.elems[q]));
+    const unsigned xm = __ballot_sync(0xffffffffu, x), ym = __ballot_sync(0xffffffffu, y);
+    if (__popc(xm) != __popc(ym)) {
+        if (lane == 0) atomicOr(&a.ctrl->status, ST_INTERNAL);
+        return;
+    }
+    int src = (int)lane;
+    if (x) {
+        unsigned mm = ym;
+        for (int j = __popc(xm & lt); j > 0; j--) mm &= mm - 1u;  // drop the j lowest set bits
+        src = __ffs(mm) - 1;
+    }
+    const int32_t qq = __shfl_sync(0xffffffffu, q, src);
+    if (x) {
+        const int32_t u = ldcg(&a.elems[qq]);
+        a.elems[p] = u;
+        a.loc[u] = p;
+        a.elems[qq] = s;
+        a.loc[s] = qq;
+    }
+    __syncwarp();
+}
+
+// One warp splits block b (more than WARP_MAX members) that has at most 32
+// marked members this round.
+__device__ void warp_split_sparse(const FrontierArgs& a, const Worklist& wl, int32_t b, int32_t km,
+                                  uint32_t stamp, int32_t C, long long& states) {
+    const unsigned lane = threadIdx.x & 31u;
+    const int32_t b0 = ldcg(&a.bbeg[b]), e0 = ldcg(&a.bend[b]);
+    const int32_t t0 = e0 - km;  // marked members listed in mscr[t0 .. e0)
+    const int32_t lo = a.off[b];
+    const int32_t k = a.off[b + 1] - lo;
+    const bool lead_marked = ldcg(&a.smark[b]) == stamp;
+    const int32_t s = (int)lane < km ? ldcg(&a.mscr[t0 + lane]) : -1;
+    __syncwarp();
+    if (lane == 0) a.mcnt[b] = 0;
+    if (!lead_marked) {
+        // split part = the marked members; they move to [t0, e0)
+        const int32_t leader = __reduce_min_sync(0xffffffffu, s >= 0 ? s : NONE);
+        if (s >= 0) a.block[s] = leader;
+        warp_gather(a, s, km, t0, [&](int32_t u) { return ldcg(&a.smark[u]) == stamp; });
+        if (lane == 0) {
+            states += km;
+            a.bend[b] = t0;
+            a.bbeg[leader] = t0;
+            a.bend[leader] = e0;
+        }
+        __syncwarp();
+        finish_split_warp(a, wl, b, leader, C);
+        return;
+    }
+    // leader marked: kept part = marked members with the leader's marks
+    unsigned lmask = 0;
+    if (k <= 32) lmask = __ballot_sync(0xffffffffu, (int)lane < k && ldcg(&a.mark[lo + lane]) == stamp);
+    const bool keep = s >= 0 && same_marks(a, s, lo, k, lmask, stamp);
+    const unsigned km_mask = __ballot_sync(0xffffffffu, keep);
+    const int32_t kk = __popc(km_mask);
+    // compact the kept members into lanes 0..kk-1
+    int src = (int)lane;
+    {
+        unsigned mm = km_mask;
+        for (int j = (int)lane; j > 0 && mm; j--) mm &= mm - 1u;
+        src = mm ? __ffs(mm) - 1 : 0;
+    }
+    const int32_t ks = __shfl_sync(0xffffffffu, s, src);
+    if ((int)lane < kk) a.kmark[ks] = stamp;
+    __syncwarp();
+    warp_gather(a, (int)lane < kk ? ks : -1, kk, b0, [&](int32_t u) { return ldcg(&a.kmark[u]) == stamp; });
+    // split part = [b0 + kk, e0): every other member
+    int mn = NONE;
+    for (int32_t q = b0 + kk + (int32_t)lane; q < e0; q += 32) mn = min(mn, ldcg(&a.elems[q]));
+    const int32_t leader = __reduce_min_sync(0xffffffffu, mn);
+    for (int32_t q = b0 + kk + (int32_t)lane; q < e0; q += 32) a.block[ldcg(&a.elems[q])] = leader;
+    __syncwarp();
+    if (lane == 0) {
+        states += e0 - b0;
         a.bend[b] = b0 + kk;
         a.bbeg[leader] = b0 + kk;
         a.bend[leader] = e0;
-        finish_split(a, wl, b, leader, C);
     }
-    __syncthreads();
+    __syncwarp();
+    finish_split_warp(a, wl, b, leader, C);
+}
+
+// Split step of a round for the touched blocks listed by the mark step:
+// blocks of at most WARP_MAX states one per warp; larger blocks one per warp
+// when at most 32 members are marked, otherwise one per CTA. CTA `cta` of
+// `ncta` takes its share; `defer` is a CTA-local list of at least
+// blockDim/32 entries.
+__device__ void split_step(const FrontierArgs& a, const Worklist& wl, CtaShared& sh, int* defer, int* ndefer,
+                           uint32_t stamp, int32_t C, int ns, const int32_t* small_list, int nm,
+                           const int32_t* mid_list, int64_t gw, int64_t nwarps, int cta, int ncta,
+                           long long& states) {
+    const int wid = (int)(threadIdx.x >> 5);
+    const int nw = (int)(blockDim.x >> 5);
+    for (int64_t i = gw; i < ns; i += nwarps) warp_split(a, wl, ldcg(&small_list[i]), stamp, C, states);
+    // entry i goes to CTA i % ncta, so the first ncta entries land on
+    // different CTAs; inside a CTA its entries go to different warps
+    for (int base = 0; base < nm; base += ncta * nw) {
+        if (threadIdx.x == 0) *ndefer = 0;
+        __syncthreads();
+        const int i = base + wid * ncta + cta;
+        if (i < nm) {
+            const int32_t b = ldcg(&mid_list[i]);
+            const int32_t km = ldcg(&a.mcnt[b]);
+            if (km <= 32) {
+                warp_split_sparse(a, wl, b, km, stamp, C, states);
+            } else if ((threadIdx.x & 31) == 0) {
+                defer[atomicAdd(ndefer, 1)] = b;
+            }
+        }
+        __syncthreads();
+        const int nd = *ndefer;
+        for (int j = 0; j < nd; j++) cta_split(a, wl, sh, defer[j], stamp, C, states);
+        __syncthreads();
+    }
 }
 
 // Mark step of one round (Algorithm 3, mark lines) for splitter C, done by the
@@ -357,9 +496,8 @@ __device__ __forceinline__ void mark_step(const FrontierArgs& a, int32_t C, uint
             const unsigned long long e = a.in_edge[j];
             const int32_t s = (int32_t)(e >> 32);
             a.mark[(uint32_t)e] = stamp;
-            if (ldcg(&a.smark[s]) == stamp) continue;
+            const int32_t b = ldcg(&a.block[s]);  // issued before the atomic: both depend on s only
             if (atomicExch(&a.smark[s], stamp) == stamp) continue;
-            const int32_t b = ldcg(&a.block[s]);
             const int32_t bb = ldcg(&a.bbeg[b]), be = ldcg(&a.bend[b]);
             if (be - bb <= 1) continue;
             const int32_t rk = atomicAdd(&a.mcnt[b], 1);
@@ -399,6 +537,8 @@ __device__ __forceinline__ int32_t select_splitter(const Worklist& wl, unsigned 
 
 __global__ void __launch_bounds__(1024) k_frontier_main(FrontierArgs a) {
     __shared__ CtaShared sh;
+    __shared__ int s_defer[32];
+    __shared__ int s_ndefer;
     const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
     const int32_t n = a.n;
@@ -428,18 +568,155 @@ __global__ void __launch_bounds__(1024) k_frontier_main(FrontierArgs a) {
         mark_step(a, C, stamp, gw, nwarps, &a.ctrl->n_touched[par], &a.ctrl->n_mid[par], a.tlist,
                   a.tlist + n, edges);
         if (!grid_sync(a.gb, tgt)) return;
-        {
-            const int32_t ns = ldcg(&a.ctrl->n_touched[par]);
-            const int32_t nm = ldcg(&a.ctrl->n_mid[par]);
-            for (int64_t i = gw; i < ns; i += nwarps) warp_split(a, wl, ldcg(&a.tlist[i]), stamp, C, states);
-            for (int32_t i = blockIdx.x; i < nm; i += gridDim.x)
-                cta_split(a, wl, sh, ldcg(&a.tlist[n + i]), stamp, C, states);
-        }
+        split_step(a, wl, sh, s_defer, &s_ndefer, stamp, C, ldcg(&a.ctrl->n_touched[par]), a.tlist,
+                   ldcg(&a.ctrl->n_mid[par]), a.tlist + n, gw, nwarps, (int)blockIdx.x, (int)gridDim.x, states);
         if (!grid_sync(a.gb, tgt)) return;
     }
     if (edges) atomicAdd((unsigned long long*)&a.ctrl->edges, (unsigned long long)edges);
     if (states) atomicAdd((unsigned long long*)&a.ctrl->states, (unsigned long long)states);
     if (gtid == 0) a.ctrl->rounds = r;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64_g(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Hybrid schedule for one LTS. CTA 0 selects every splitter. A light round
+// (at most 32 members whose incoming transitions number at most light_edges)
+// is done by CTA 0 alone with CTA barriers; a heavy round is published
+// (cmd_C, cmd_stamp, then cmd_seq with release order) and done by the whole
+// grid with two grid barriers, exactly as k_frontier_main. The other CTAs
+// wait for commands; their wait is bounded by timeout_ns without progress,
+// where progress is a new command or a new heartbeat from CTA 0.
+__global__ void __launch_bounds__(1024) k_frontier_hybrid(FrontierArgs a, int light_edges) {
+    __shared__ CtaShared sh;
+    __shared__ int s_defer[32];
+    __shared__ int s_ndefer;
+    __shared__ int s_ns, s_nm, s_heavy;
+    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
+    const int32_t n = a.n;
+    const int64_t wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int64_t gw = gtid >> 5, nwarps = gsz >> 5;
+    bisim_ctrl* c = a.ctrl;
+    unsigned long long tgt = 0;
+    long long edges = 0, states = 0;
+    if (a.test_hook == 1 && blockIdx.x == 0) return;  // testing: never publish, never arrive
+    const Worklist wl{c->bq_tail, a.queue, (size_t)n, 0, n};
+    if (blockIdx.x == 0) {
+        if (threadIdx.x < BISIM_BUCKETS) sh.head[threadIdx.x] = 0;
+        int64_t r = 0;
+        unsigned long long seq = 0;
+        for (;;) {
+            r++;
+            const uint32_t stamp = a.stamp0 + (uint32_t)r;
+            int32_t C = select_splitter(wl, sh.head, sh);
+            if (C >= 0 && r > a.round_cap) {
+                if (threadIdx.x == 0) atomicOr(&c->status, ST_ROUNDS);
+                C = -1;
+            }
+            if (C < 0) {
+                if (threadIdx.x == 0) {
+                    c->cmd_C = -1;
+                    __threadfence();
+                    atomicAdd(&c->cmd_seq, 1ull);
+                    c->rounds = r;
+                }
+                break;
+            }
+            if (threadIdx.x == 0) a.unstable[C] = 0u;
+            // light or heavy?
+            if (threadIdx.x < 32) {
+                const int32_t b0 = ldcg(&a.bbeg[C]), e0 = ldcg(&a.bend[C]);
+                int heavy = 1;
+                if (e0 - b0 <= 32) {
+                    int deg = 0;
+                    if ((int)threadIdx.x < e0 - b0) {
+                        const int32_t t = ldcg(&a.elems[b0 + threadIdx.x]);
+                        deg = a.in_ptr[t + 1] - a.in_ptr[t];
+                    }
+                    heavy = __reduce_add_sync(0xffffffffu, deg) > light_edges;
+                }
+                if (threadIdx.x == 0) {
+                    s_heavy = heavy;
+                    s_ns = 0;
+                    s_nm = 0;
+                    if (heavy) {
+                        c->n_touched[0] = 0;
+                        c->n_mid[0] = 0;
+                        c->cmd_C = C;
+                        c->cmd_stamp = stamp;
+                        __threadfence();
+                        atomicAdd(&c->cmd_seq, 1ull);
+                    }
+                }
+            }
+            __syncthreads();
+            if (s_heavy) {
+                seq++;
+                mark_step(a, C, stamp, gw, nwarps, &c->n_touched[0], &c->n_mid[0], a.tlist, a.tlist + n, edges);
+                if (!grid_sync(a.gb, tgt)) return;
+                split_step(a, wl, sh, s_defer, &s_ndefer, stamp, C, ldcg(&c->n_touched[0]), a.tlist,
+                           ldcg(&c->n_mid[0]), a.tlist + n, gw, nwarps, 0, (int)gridDim.x, states);
+                if (!grid_sync(a.gb, tgt)) return;
+            } else {
+                mark_step(a, C, stamp, wid, nw, &s_ns, &s_nm, a.tlist, a.tlist + n, edges);
+                __syncthreads();
+                split_step(a, wl, sh, s_defer, &s_ndefer, stamp, C, s_ns, a.tlist, s_nm, a.tlist + n, wid, nw, 0, 1,
+                           states);
+                __syncthreads();
+                if (threadIdx.x == 0) *(volatile unsigned long long*)&c->heartbeat = (unsigned long long)r;
+            }
+            (void)seq;
+        }
+    } else {
+        __shared__ int s_cmd;
+        __shared__ unsigned s_stamp;
+        unsigned long long seen = 0;
+        for (;;) {
+            if (threadIdx.x == 0) {
+                int ab = 0;
+                unsigned long long t0 = 0, hb = ~0ull;
+                unsigned spins = 0;
+                while (ld_acquire_u64_g(&c->cmd_seq) == seen) {
+                    __nanosleep(64);
+                    if ((++spins & 31u) == 0) {
+                        const unsigned long long now = globaltimer_ns();
+                        const unsigned long long h = ldcg(&c->heartbeat);
+                        if (h != hb) {
+                            hb = h;
+                            t0 = now;
+                        } else if (now - t0 > a.gb.timeout_ns) {
+                            atomicOr(&c->status, ST_TIMEOUT);
+                            ab = 1;
+                            break;
+                        }
+                        if (ldcg(&c->status) & ST_ABORT_MASK) {
+                            ab = 1;
+                            break;
+                        }
+                    }
+                }
+                seen++;
+                s_cmd = ab ? -1 : ldcg(&c->cmd_C);
+                s_stamp = ldcg(&c->cmd_stamp);
+            }
+            __syncthreads();
+            const int32_t C = s_cmd;
+            const uint32_t stamp = s_stamp;
+            __syncthreads();
+            if (C < 0) break;
+            mark_step(a, C, stamp, gw, nwarps, &c->n_touched[0], &c->n_mid[0], a.tlist, a.tlist + n, edges);
+            if (!grid_sync(a.gb, tgt)) return;
+            split_step(a, wl, sh, s_defer, &s_ndefer, stamp, C, ldcg(&c->n_touched[0]), a.tlist,
+                       ldcg(&c->n_mid[0]), a.tlist + n, gw, nwarps, (int)blockIdx.x, (int)gridDim.x, states);
+            if (!grid_sync(a.gb, tgt)) return;
+        }
+    }
+    if (edges) atomicAdd((unsigned long long*)&c->edges, (unsigned long long)edges);
+    if (states) atomicAdd((unsigned long long*)&c->states, (unsigned long long)states);
 }
 
 // Many LTSs in one launch, one CTA per LTS at a time: the same rounds, with
@@ -460,6 +737,8 @@ struct BatchArgs {
 
 __global__ void __launch_bounds__(1024) k_frontier_batch(FrontierArgs a, BatchArgs bt) {
     __shared__ CtaShared sh;
+    __shared__ int s_defer[32];
+    __shared__ int s_ndefer;
     __shared__ unsigned long long s_tail[BISIM_BUCKETS];
     __shared__ int s_ns, s_nm, s_inst;
     const int64_t gw = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -502,9 +781,8 @@ __global__ void __launch_bounds__(1024) k_frontier_batch(FrontierArgs a, BatchAr
             __syncthreads();
             mark_step(a, C, stamp, gw, nwarps, &s_ns, &s_nm, a.tlist + s0, a.tlist + a.n + s0, edges);
             __syncthreads();
-            const int ns = s_ns, nm = s_nm;
-            for (int i = (int)gw; i < ns; i += (int)nwarps) warp_split(a, wl, ldcg(&a.tlist[s0 + i]), stamp, C, states);
-            for (int i = 0; i < nm; i++) cta_split(a, wl, sh, ldcg(&a.tlist[a.n + s0 + i]), stamp, C, states);
+            split_step(a, wl, sh, s_defer, &s_ndefer, stamp, C, s_ns, a.tlist + s0, s_nm, a.tlist + a.n + s0, gw,
+                       nwarps, 0, 1, states);
             __syncthreads();
         }
         if (threadIdx.x == 0) bt.inst_rounds[li] = r;
@@ -669,9 +947,13 @@ int refine_frontier(bisim_plan_s* p, bisim_stats* stats) {
     BISIM_TRY(frontier_setup(p, true));
     FrontierArgs a = make_args(p, base, cap);
     const int threads = p->opts.threads > 0 ? p->opts.threads : 512;
-    void* args[] = {&a};
+    int light = p->opts.light_edges == 0 ? 256 : p->opts.light_edges;
+    void* args[] = {&a, &light};
     int grid = 0;
-    BISIM_TRY(launch_persistent((const void*)k_frontier_main, args, threads, p, &grid));
+    if (light < 0)  // every round on the whole grid
+        BISIM_TRY(launch_persistent((const void*)k_frontier_main, args, threads, p, &grid));
+    else
+        BISIM_TRY(launch_persistent((const void*)k_frontier_hybrid, args, threads, p, &grid));
     BISIM_TRY(read_ctrl(p));
     p->stamp = base + (uint32_t)std::min<long long>(p->ctrl_h->rounds + 1, cap + 1);
     if (stats) {

@@ -216,3 +216,15 @@ def test_launch_shapes(engine):
     for threads, per_sm in ((128, 1), (256, 2), (1024, 1)):
         got, _ = run(lts, engine, threads=threads, ctas_per_sm=per_sm)
         assert got.tolist() == want.tolist(), (threads, per_sm)
+
+
+@pytest.mark.parametrize("light_edges", [-1, 0, 1 << 30], ids=["grid", "hybrid", "all-light"])
+def test_frontier_schedules(light_edges):
+    """Frontier rounds on the whole grid, hybrid (light rounds on one CTA),
+    and every eligible round light: same partitions."""
+    cases = [lts_gen.random_small(100 + s, 40, 1 + s % 3, 120, blocks=2) for s in range(30)]
+    cases += [lts_gen.kripke_uniform(), lts_gen.chain(n=2000), lts_gen.fan_out(200),
+              lts_gen.quotient_expansion(seed=6, classes=500, trans=5000, copies_hi=40)]
+    for lts in cases:
+        got, st = run(lts, bisim.ENGINE_FRONTIER, light_edges=light_edges)
+        assert got.tolist() == oracle.ks_lts(lts).tolist(), lts.name
