@@ -38,6 +38,8 @@ WORKLOADS = {
     "chain": ("deep-refinement chain (seed 2, n=50000)", lambda: lts_gen.chain(seed=2, n=50000)),
     "powerlaw": ("power-law LTS (seed 3, n=10M, m~100M, |Act|=32, 4 AP blocks)",
                  lambda: lts_gen.powerlaw(seed=3)),
+    "powerlaw2m": ("power-law LTS (seed 3, n=2M, m~20M, |Act|=32, 4 AP blocks)",
+                   lambda: lts_gen.powerlaw(seed=3, n=2_000_000)),
 }
 
 L2_BYTES = 129 * 1024 * 1024
@@ -138,6 +140,28 @@ def max_over_ranks(x, world, device=None):
     t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def recorded_traffic(kernel, workload):
+    """DRAM bytes per launch of `kernel` on `workload` from the committed ncu
+    record (profiles/ncu_traffic.json), or None when there is none or the
+    kernel's source has changed since the counters were taken."""
+    import hashlib
+
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        rec = json.load(f).get(f"{kernel}@{workload}")
+    if not rec:
+        return None
+    src = os.path.join(ROOT, rec["source"])
+    if not os.path.exists(src):
+        return None
+    with open(src, "rb") as f:
+        if hashlib.sha256(f.read()).hexdigest() != rec["source_sha256"]:
+            return None
+    return rec["dram_bytes_per_launch"]
 
 
 def dense_bytes_per_launch(st):
@@ -311,7 +335,8 @@ def run_stream(args, world, rank, local):
                        "l2": "inputs larger than L2",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "kernel": "k_frontier_batch", "achieved": achieved, "peak": hbm,
-                         "unit": "GB/s", "frac": achieved / hbm, "peak_kind": peak_kind, "traffic": None,
+                         "unit": "GB/s", "frac": achieved / hbm, "peak_kind": peak_kind,
+                         "traffic": recorded_traffic("k_frontier_batch", f"stream{k}"),
                          "kernel_ms": km, "bytes_per_launch": bytes_launch},
             "e2e": {"value": world * k * 1000.0 / e2e_ms, "unit": "LTS/s",
                     "h2d_bytes_per_step": int(src.nbytes + act.nbytes + dst.nbytes),
@@ -360,6 +385,8 @@ def main():
     ap.add_argument("--engine", default="auto", choices=["auto", "dense", "frontier"])
     ap.add_argument("--threads", type=int, default=0, help="threads per CTA (0 = library default)")
     ap.add_argument("--max-ctas", type=int, default=0, help="cap on persistent-kernel CTAs")
+    ap.add_argument("--light-edges", type=int, default=0,
+                    help="frontier: light-round threshold (0 = library default, <0 = grid only)")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -380,7 +407,8 @@ def main():
     bisim.load(build_if_missing=True)
     engine = {"auto": bisim.ENGINE_AUTO, "dense": bisim.ENGINE_DENSE,
               "frontier": bisim.ENGINE_FRONTIER}[args.engine]
-    opts = bisim.make_opts(engine=engine, threads=args.threads, max_ctas=args.max_ctas)
+    opts = bisim.make_opts(engine=engine, threads=args.threads, max_ctas=args.max_ctas,
+                           light_edges=args.light_edges)
     desc, make = WORKLOADS[args.workload]
     lts = make()
     src = torch.from_numpy(lts.src).to(dev)
@@ -442,9 +470,13 @@ def main():
     st = stats[-1]
     hbm, peak_kind = read_peaks()
     achieved = (sum(kernel_bytes) / len(kernel_bytes)) / (sum(kernel_ms) / len(kernel_ms) * 1e-3) / 1e9
-    roof = {"bound": "hbm", "kernel": "k_dense_main" if st.engine == bisim.ENGINE_DENSE
-            else "k_frontier_main", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm, "peak_kind": peak_kind, "traffic": None,
+    if st.engine == bisim.ENGINE_DENSE:
+        kname = "k_dense_main"
+    else:
+        kname = "k_frontier_main" if args.light_edges < 0 else "k_frontier_hybrid"
+    roof = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "peak_kind": peak_kind,
+            "traffic": recorded_traffic(kname, args.workload),
             "kernel_ms": sum(kernel_ms) / len(kernel_ms),
             "bytes_per_launch": sum(kernel_bytes) / len(kernel_bytes)}
 
