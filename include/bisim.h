@@ -76,6 +76,12 @@ typedef struct bisim_opts {
                             members and at most this many incoming transitions runs
                             on one CTA without grid barriers (0 = 256; negative =
                             every round on the whole grid) */
+    int32_t preprocess;  /* action-set preprocessing (Algorithm 5): 0 = auto (literal
+                            rounds for the dense engine, else direct grouping);
+                            1 = one round per label; 2 = direct grouping by
+                            (initial block, label set) when |Act| <= 128. Same
+                            partition; leader labels may differ */
+    int32_t reserved;
 } bisim_opts;
 
 typedef struct bisim_stats {

@@ -69,6 +69,10 @@ int bisim_plan(int32_t n, int64_t m, int32_t num_act, const int32_t* src, const 
         set_last_error("transitions given for an LTS without states");
         return BISIM_EINVAL;
     }
+    if (opts && (opts->threads < 0 || opts->threads > 1024 || (opts->threads & 31))) {
+        set_last_error("opts.threads must be a multiple of 32 in [32, 1024] (or 0)");
+        return BISIM_EINVAL;
+    }
     bisim_plan_s* p = new (std::nothrow) bisim_plan_s();
     if (!p) return BISIM_ENOMEM;
     p->n = n;

@@ -155,6 +155,10 @@ int bisim_batch_plan(int32_t k, const int64_t* state_off_h, const int64_t* trans
                      const bisim_opts* opts, void* stream, bisim_plan_t* out) {
     if (!out) return BISIM_EINVAL;
     *out = nullptr;
+    if (opts && (opts->threads < 0 || opts->threads > 1024 || (opts->threads & 31))) {
+        set_last_error("opts.threads must be a multiple of 32 in [32, 1024] (or 0)");
+        return BISIM_EINVAL;
+    }
     if (k < 1 || !state_off_h || !trans_off_h || !num_act_h) {
         set_last_error("bisim_batch_plan: need k >= 1 and the offset / label-count arrays");
         return BISIM_EINVAL;

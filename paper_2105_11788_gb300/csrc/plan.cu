@@ -112,8 +112,14 @@ __global__ void k_fill_i32(int32_t* p, int64_t n, int32_t v) {
 
 __global__ void k_init_min(const int32_t* __restrict__ init, int32_t n, int32_t* nl) {
     const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gsz)
-        atomicMin(&nl[init[i]], (int32_t)i);
+    // uniform trip count per warp (n rounded up), so every lane reaches the match
+    const int64_t lim = (n + 31) & ~(int64_t)31;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < lim; i += gsz) {
+        const int32_t v = i < n ? init[i] : -1;
+        // consecutive lanes hold consecutive states: one atomic per label per warp
+        const unsigned peers = __match_any_sync(0xffffffffu, v);
+        if (v >= 0 && (peers & lanemask_lt()) == 0u) atomicMin(&nl[v], (int32_t)i);
+    }
 }
 
 __global__ void k_init_relabel(const int32_t* __restrict__ init, int32_t n,
@@ -163,19 +169,41 @@ __global__ void k_label_rounds(LabelArgs a) {
         }
         const int w = lab >> 5;
         const uint32_t bit = 1u << (lab & 31);
-        for (int64_t s = gtid; s < a.n; s += gsz) {
-            const int32_t b = a.block[s];
-            bool ms, mb;
-            if (a.amask) {
-                ms = (a.amask[(size_t)s * a.mask_words + w] & bit) != 0u;
-                mb = (a.amask[(size_t)b * a.mask_words + w] & bit) != 0u;
-            } else {
-                ms = ldcg(&a.lmark[s]) == stamp;
-                mb = ldcg(&a.lmark[b]) == stamp;
+        // four states per thread per step, so their independent loads overlap;
+        // the loop test uses the warp's first state, so all lanes iterate
+        // together and reach the match below
+        const int64_t lane = threadIdx.x & 31;
+        for (int64_t s0 = gtid; s0 - lane < a.n; s0 += 4 * gsz) {
+            int32_t b[4];
+            bool ms[4], mb[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int64_t s = s0 + u * gsz;
+                b[u] = s < a.n ? a.block[s] : 0;
             }
-            const uint8_t sp = ms != mb;
-            a.split[s] = sp;
-            if (sp) atomicMin(&a.nl64[b], elect_key(stamp, (int32_t)s));
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int64_t s = s0 + u * gsz;
+                if (s >= a.n) {
+                    ms[u] = mb[u] = false;
+                } else if (a.amask) {
+                    ms[u] = (a.amask[(size_t)s * a.mask_words + w] & bit) != 0u;
+                    mb[u] = (a.amask[(size_t)b[u] * a.mask_words + w] & bit) != 0u;
+                } else {
+                    ms[u] = ldcg(&a.lmark[s]) == stamp;
+                    mb[u] = ldcg(&a.lmark[b[u]]) == stamp;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int64_t s = s0 + u * gsz;
+                const bool sp = s < a.n && ms[u] != mb[u];
+                if (s < a.n) a.split[s] = sp;
+                // lanes hold consecutive states: the lowest lane of each group of
+                // splitting states with the same block holds the group's minimum
+                const unsigned peers = __match_any_sync(0xffffffffu, sp ? b[u] : -1);
+                if (sp && (peers & lanemask_lt()) == 0u) atomicMin(&a.nl64[b[u]], elect_key(stamp, (int32_t)s));
+            }
         }
         if (!grid_sync(a.gb, tgt)) return;
         for (int64_t s = gtid; s < a.n; s += gsz)
@@ -213,7 +241,118 @@ __global__ void k_gather_ids(const int32_t* __restrict__ block, const int32_t* _
         out[i] = (int32_t)rank[first[block[i]]];
 }
 
+// key of state vals[i] for the sort pass over label-set word w (w < mask_words)
+// or over the block after the initial election (w == mask_words)
+__global__ void k_group_keys(const uint32_t* __restrict__ vals, const uint32_t* __restrict__ amask,
+                             const int32_t* __restrict__ block, int mask_words, int w, int32_t n,
+                             uint32_t* keys) {
+    const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gsz) {
+        const uint32_t s = vals[i];
+        keys[i] = w < mask_words ? amask[(size_t)s * mask_words + w] : (uint32_t)block[s];
+    }
+}
+
+// 1 where sorted position i starts a new (block, label set) group
+__global__ void k_group_starts(const uint32_t* __restrict__ vals, const uint32_t* __restrict__ amask,
+                               const int32_t* __restrict__ block, int mask_words, int32_t n,
+                               uint32_t* start) {
+    const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gsz) {
+        bool st = i == 0;
+        if (!st) {
+            const uint32_t s = vals[i], t = vals[i - 1];
+            st = block[s] != block[t];
+            for (int w = 0; w < mask_words && !st; w++)
+                st = amask[(size_t)s * mask_words + w] != amask[(size_t)t * mask_words + w];
+        }
+        start[i] = st;
+    }
+}
+
+// leader of each group = its first sorted state (the smallest, the sorts being
+// stable over states in increasing order). excl = exclusive scan of start, so
+// the group of position i is excl[i] + start[i] - 1.
+__global__ void k_group_first(const uint32_t* __restrict__ vals, const uint32_t* __restrict__ start,
+                              const uint32_t* __restrict__ excl, int32_t n, int32_t* first) {
+    const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gsz)
+        if (start[i]) first[excl[i]] = (int32_t)vals[i];
+}
+
+__global__ void k_group_assign(const uint32_t* __restrict__ vals, const uint32_t* __restrict__ start,
+                               const uint32_t* __restrict__ excl, const int32_t* __restrict__ first,
+                               int32_t n, int32_t* block) {
+    const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gsz)
+        block[vals[i]] = first[excl[i] + start[i] - 1u];
+}
+
+__global__ void k_iota(uint32_t* v, int32_t n) {
+    const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gsz) v[i] = (uint32_t)i;
+}
+
 }  // namespace
+
+namespace bisim {
+
+// Literal preprocessing rounds (Algorithm 5, one per label) are kept for the
+// dense engine, whose leader labels are checked against the lock-step
+// program, and on request; otherwise the rounds' result is computed directly.
+bool preprocess_fused(const bisim_plan_s* p) {
+    if (p->opts.preprocess == 1) return false;
+    if (p->opts.preprocess == 2) return true;
+    return p->opts.engine != BISIM_ENGINE_DENSE;
+}
+
+// block <- one block per (block, label set), led by its smallest state: the
+// partition every sequence of Algorithm 5's label rounds ends in. Stable LSD
+// radix sorts of the states by each label-set word and then by the block,
+// group boundaries, and a scan numbering the groups.
+int group_by_label_set(bisim_plan_s* p, const uint32_t* amask, int mask_words) {
+    const int32_t n = p->n;
+    cudaStream_t st = p->st;
+    const unsigned gn = grid_for(n, T);
+    DevMem keys, keys2, vals, vals2, flags;
+    BISIM_TRY(keys.alloc(4 * (size_t)n, st));
+    BISIM_TRY(keys2.alloc(4 * (size_t)n, st));
+    BISIM_TRY(vals.alloc(4 * (size_t)n, st));
+    BISIM_TRY(vals2.alloc(4 * (size_t)n, st));
+    BISIM_TRY(flags.alloc(4 * (size_t)n, st));
+    k_iota<<<gn, T, 0, st>>>(vals.as<uint32_t>(), n);
+    BISIM_LAUNCHED();
+    int32_t* block = p->block.as<int32_t>();
+    for (int w = 0; w <= mask_words; w++) {
+        k_group_keys<<<gn, T, 0, st>>>(vals.as<uint32_t>(), amask, block, mask_words, w, n, keys.as<uint32_t>());
+        BISIM_LAUNCHED();
+        BISIM_CUDA_TRY(cudaGetLastError());
+        bool alt = false;
+        const int bits = w < mask_words ? 32 : ceil_log2_u64((uint64_t)n);
+        BISIM_TRY(radix_sort_pairs<uint32_t, uint32_t>(keys.as<uint32_t>(), vals.as<uint32_t>(),
+                                                       keys2.as<uint32_t>(), vals2.as<uint32_t>(), n, bits, st,
+                                                       &alt));
+        if (alt) {
+            std::swap(vals.p, vals2.p);
+            std::swap(keys.p, keys2.p);
+        }
+    }
+    k_group_starts<<<gn, T, 0, st>>>(vals.as<uint32_t>(), amask, block, mask_words, n, flags.as<uint32_t>());
+    BISIM_LAUNCHED();
+    BISIM_CUDA_TRY(cudaGetLastError());
+    // keys <- number of group starts before each sorted position
+    BISIM_TRY(scan_exclusive_u32(flags.as<uint32_t>(), keys.as<uint32_t>(), n, nullptr, st));
+    k_group_first<<<gn, T, 0, st>>>(vals.as<uint32_t>(), flags.as<uint32_t>(), keys.as<uint32_t>(), n,
+                                    (int32_t*)keys2.p);
+    BISIM_LAUNCHED();
+    k_group_assign<<<gn, T, 0, st>>>(vals.as<uint32_t>(), flags.as<uint32_t>(), keys.as<uint32_t>(),
+                                     (const int32_t*)keys2.p, n, block);
+    BISIM_LAUNCHED();
+    BISIM_CUDA_TRY(cudaGetLastError());
+    return BISIM_OK;
+}
+
+}  // namespace bisim
 
 bisim_plan_s::~bisim_plan_s() {
     if (ctrl_h) cudaFreeHost(ctrl_h);
@@ -249,14 +388,15 @@ int reserve_stamps(bisim_plan_s* p, int64_t rounds, uint32_t* base) {
     return BISIM_OK;
 }
 
-int launch_persistent(const void* fn, void** args, int threads, bisim_plan_s* p, int* grid_out) {
+int launch_persistent(const void* fn, void** args, int threads, bisim_plan_s* p, int* grid_out,
+                      int per_sm_default) {
     int occ = 0;
     BISIM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, 0));
     if (occ < 1) {
         set_last_error("persistent kernel does not fit on an SM");
         return BISIM_ECUDA;
     }
-    int per_sm = p->opts.ctas_per_sm > 0 ? p->opts.ctas_per_sm : 1;
+    int per_sm = p->opts.ctas_per_sm > 0 ? p->opts.ctas_per_sm : per_sm_default;
     per_sm = std::min(per_sm, occ);
     int grid = p->sm_count * per_sm;
     if (p->opts.max_ctas > 0) grid = std::min(grid, p->opts.max_ctas);
@@ -467,13 +607,23 @@ int plan_build(bisim_plan_s* p, const int32_t* src, const int32_t* act, const in
             BISIM_CUDA_TRY(cudaGetLastError());
             a.amask = amask.as<uint32_t>();
         }
-        a.gb.counter = &p->ctrl.as<bisim_ctrl>()->barrier;
-        a.gb.status = status;
-        a.gb.timeout_ns = (unsigned long long)(p->opts.timeout_ms > 0 ? p->opts.timeout_ms : 2000) * 1000000ull;
-        void* args[] = {&a};
-        int grid = 0;
-        BISIM_TRY(launch_persistent((const void*)k_label_rounds, args, 512, p, &grid));
-        BISIM_TRY(persistent_ms(p, &p->t_pre_ms));
+        const bool fused = a.amask && preprocess_fused(p);
+        if (fused) {
+            // the partition after every label round: one block per (initial
+            // block, label set), led by its smallest state
+            BISIM_CUDA_TRY(cudaEventRecord(p->evk0, st));
+            BISIM_TRY(group_by_label_set(p, a.amask, a.mask_words));
+            BISIM_CUDA_TRY(cudaEventRecord(p->evk1, st));
+            BISIM_TRY(persistent_ms(p, &p->t_pre_ms));
+        } else {
+            a.gb.counter = &p->ctrl.as<bisim_ctrl>()->barrier;
+            a.gb.status = status;
+            a.gb.timeout_ns = (unsigned long long)(p->opts.timeout_ms > 0 ? p->opts.timeout_ms : 2000) * 1000000ull;
+            void* args[] = {&a};
+            int grid = 0;
+            BISIM_TRY(launch_persistent((const void*)k_label_rounds, args, 512, p, &grid, 4));
+            BISIM_TRY(persistent_ms(p, &p->t_pre_ms));
+        }
         p->stamp = base + (uint32_t)p->pre_rounds;
     }
     if (n) BISIM_CUDA_TRY(cudaMemcpyAsync(p->block0.p, p->block.p, 4 * (size_t)n,

@@ -77,7 +77,7 @@ struct bisim_plan_s {
     bisim::DevMem smark;     // uint32 [n]: round stamp of the last mark of each state
     bisim::DevMem kmark;     // uint32 [n]: round stamp of membership in a kept part
     bisim::DevMem tlist;     // int32 [2n]: touched-label lists (warp, CTA)
-    bisim::DevMem queue;     // int32 [n]: FIFO ring of unstable labels
+    bisim::DevMem queue;     // int32 [BISIM_BUCKETS * n]: FIFO rings of unstable labels
 
     // batch plans: k LTSs over disjoint state ranges of one union LTS
     int32_t batch_k = 0;
@@ -110,13 +110,16 @@ int refine_frontier(bisim_plan_s* p, bisim_stats* st);
 // CTA-per-LTS frontier rounds over a batch plan; rounds[i] = iterations of LTS i
 int refine_frontier_batch(bisim_plan_s* p, bisim_stats* st, std::vector<long long>& rounds);
 int write_output(bisim_plan_s* p, int32_t* out_block, int64_t* num_blocks);
+bool preprocess_fused(const bisim_plan_s* p);
+int group_by_label_set(bisim_plan_s* p, const uint32_t* amask, int mask_words);
 
 // Reserve `rounds` fresh stamps (resetting stamped arrays if the 32-bit
 // stamp space would wrap); returns the first stamp minus one.
 int reserve_stamps(bisim_plan_s* p, int64_t rounds, uint32_t* base);
 
 // Cooperative launch on one SM-multiple grid, bracketed by evk0 / evk1.
-int launch_persistent(const void* fn, void** args, int threads, bisim_plan_s* p, int* grid_out);
+int launch_persistent(const void* fn, void** args, int threads, bisim_plan_s* p, int* grid_out,
+                      int per_sm_default = 1);
 // Device time between evk0 and evk1 of the last persistent launch.
 int persistent_ms(bisim_plan_s* p, double* ms);
 int read_ctrl(bisim_plan_s* p);

@@ -118,10 +118,16 @@ __global__ void __launch_bounds__(RS_THREADS)
                  V* __restrict__ vout, int64_t n, int shift, const uint32_t* __restrict__ offs,
                  int ntiles) {
     __shared__ uint32_t wc[RS_WARPS][256];
+    __shared__ uint32_t dbase[256];  // first tile-local position of each digit
+    __shared__ uint32_t gbase[256];  // global position of the tile's first key of each digit
+    extern __shared__ __align__(16) unsigned char stage[];  // tile in digit order: keys then values
+    K* skey = reinterpret_cast<K*>(stage);
+    V* sval = reinterpret_cast<V*>(stage + sizeof(K) * RS_TILE);
     const unsigned lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < RS_WARPS * 256; i += RS_THREADS) (&wc[0][0])[i] = 0;
     __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * RS_TILE + (int64_t)w * RS_WTILE;
+    const int64_t tile0 = (int64_t)blockIdx.x * RS_TILE;
+    const int64_t base = tile0 + (int64_t)w * RS_WTILE;
     K kr[RS_ITEMS];
     V vr[RS_ITEMS];
     uint32_t lr[RS_ITEMS];
@@ -148,26 +154,54 @@ __global__ void __launch_bounds__(RS_THREADS)
         __syncwarp();
     }
     __syncthreads();
+    // per digit: warp offsets inside the digit, the digit's tile total, and
+    // (block-wide exclusive scan over digits) its first tile-local position
+    uint32_t dtot = 0;
     {
         const int d = threadIdx.x;
-        uint32_t acc = 0;
 #pragma unroll
         for (int ww = 0; ww < RS_WARPS; ww++) {
             uint32_t c = wc[ww][d];
-            wc[ww][d] = acc;
-            acc += c;
+            wc[ww][d] = dtot;
+            dtot += c;
         }
+        gbase[d] = offs[(int64_t)d * ntiles + blockIdx.x];
+    }
+    {
+        __shared__ uint32_t wsum[RS_WARPS];
+        uint32_t x = dtot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= (unsigned)o) x += y;
+        }
+        if (lane == 31) wsum[w] = x;
+        __syncthreads();
+        uint32_t wpre = 0;
+        for (unsigned ww = 0; ww < w; ww++) wpre += wsum[ww];
+        dbase[threadIdx.x] = wpre + x - dtot;
     }
     __syncthreads();
+    // stage the tile in digit order
 #pragma unroll
     for (int j = 0; j < RS_ITEMS; j++) {
         const int64_t idx = base + j * 32 + lane;
         if (idx < n) {
-            unsigned d = (unsigned)(kr[j] >> shift) & 255u;
-            uint32_t pos = offs[(int64_t)d * ntiles + blockIdx.x] + wc[w][d] + lr[j];
-            kout[pos] = kr[j];
-            vout[pos] = vr[j];
+            const unsigned d = (unsigned)(kr[j] >> shift) & 255u;
+            const uint32_t pos = dbase[d] + wc[w][d] + lr[j];
+            skey[pos] = kr[j];
+            sval[pos] = vr[j];
         }
+    }
+    __syncthreads();
+    // write runs of equal digits to consecutive global addresses
+    const int cnt = (int)(n - tile0 < RS_TILE ? n - tile0 : RS_TILE);
+    for (int i = threadIdx.x; i < cnt; i += RS_THREADS) {
+        const K k = skey[i];
+        const unsigned d = (unsigned)(k >> shift) & 255u;
+        const uint32_t pos = gbase[d] + (uint32_t)i - dbase[d];
+        kout[pos] = k;
+        vout[pos] = sval[i];
     }
 }
 
@@ -206,6 +240,8 @@ int radix_sort_pairs(K* keys, V* vals, K* keys_alt, V* vals_alt, int64_t n, int 
     const int ntiles = (int)((n + RS_TILE - 1) / RS_TILE);
     DevMem hist;
     BISIM_TRY(hist.alloc(sizeof(uint32_t) * 256u * (size_t)ntiles, st));
+    const size_t smem = (sizeof(K) + sizeof(V)) * RS_TILE;  // staging buffer of the scatter
+    BISIM_CUDA_TRY(cudaFuncSetAttribute(k_rs_scatter<K, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     K* kin = keys;
     V* vin = vals;
     K* kout = keys_alt;
@@ -217,8 +253,8 @@ int radix_sort_pairs(K* keys, V* vals, K* keys_alt, V* vals_alt, int64_t n, int 
         BISIM_CUDA_TRY(cudaGetLastError());
         BISIM_TRY(scan_exclusive_u32(hist.as<uint32_t>(), hist.as<uint32_t>(), 256ll * ntiles,
                                      nullptr, st));
-        k_rs_scatter<K, V><<<ntiles, RS_THREADS, 0, st>>>(kin, vin, kout, vout, n, shift,
-                                                          hist.as<uint32_t>(), ntiles);
+        k_rs_scatter<K, V><<<ntiles, RS_THREADS, smem, st>>>(kin, vin, kout, vout, n, shift,
+                                                             hist.as<uint32_t>(), ntiles);
         BISIM_LAUNCHED();
         BISIM_CUDA_TRY(cudaGetLastError());
         K* tk = kin; kin = kout; kout = tk;

@@ -88,8 +88,14 @@ __global__ void __launch_bounds__(1024) k_dense_main(DenseArgs a) {
             edges += j1 - a.in_ptr[t];
         }
         if (!grid_sync(a.gb, tgt)) return;
-        // compare and elect
-        for (int64_t s = gtid; s < n; s += gsz) {
+        // compare and elect (trip count rounded up to whole warps so that every
+        // lane reaches the match below)
+        const int64_t nlim = (n + 31) & ~(int64_t)31;
+        for (int64_t s = gtid; s < nlim; s += gsz) {
+            if (s >= n) {
+                __match_any_sync(0xffffffffu, -1);
+                continue;
+            }
             const int32_t b = a.block[s];
             const int32_t o = a.off[s];
             int32_t k = a.off[s + 1] - o;
@@ -104,7 +110,10 @@ __global__ void __launch_bounds__(1024) k_dense_main(DenseArgs a) {
                 sp |= (ldcg(&a.mark[o + q]) == stamp) != (ldcg(&a.mark[ob + q]) == stamp);
             states++;
             a.split[s] = sp;
-            if (sp) atomicMin(&a.nl64[b], elect_key(stamp, (int32_t)s));
+            // lanes hold consecutive states: the lowest lane of a group of
+            // splitting states with the same block holds the group's minimum
+            const unsigned peers = __match_any_sync(0xffffffffu, sp ? b : -1);
+            if (sp && (peers & lanemask_lt()) == 0u) atomicMin(&a.nl64[b], elect_key(stamp, (int32_t)s));
         }
         if (!grid_sync(a.gb, tgt)) return;
         // relabel

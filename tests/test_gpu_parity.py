@@ -228,3 +228,19 @@ def test_frontier_schedules(light_edges):
     for lts in cases:
         got, st = run(lts, bisim.ENGINE_FRONTIER, light_edges=light_edges)
         assert got.tolist() == oracle.ks_lts(lts).tolist(), lts.name
+
+
+@pytest.mark.parametrize("engine", ENGINES, ids=ENGINE_IDS)
+def test_preprocessing_rounds_and_direct_grouping_agree(engine):
+    """Algorithm 5 one label at a time and the direct grouping by (initial
+    block, label set) give the same partition and the same |pi_0'|."""
+    cases = [lts_gen.random_small(300 + s, 60, 1 + s % 5, 200, blocks=1 + s % 3) for s in range(25)]
+    cases += [lts_gen.quotient_expansion(seed=8, classes=400, trans=4000, num_act=20, copies_hi=20),
+              lts_gen.kripke_uniform(seed=3)]
+    for lts in cases:
+        want = oracle.ks_lts(lts).tolist()
+        got1, st1 = run(lts, engine, preprocess=1)
+        got2, st2 = run(lts, engine, preprocess=2)
+        assert got1.tolist() == want and got2.tolist() == want, lts.name
+        assert st1.initial_blocks == st2.initial_blocks
+        assert st1.pre_rounds == st2.pre_rounds
