@@ -19,6 +19,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import threading
 import time
 
@@ -238,7 +239,15 @@ def run_stream(args, world, rank, local):
     k = len(ltss)
     so, to, na, src, act, dst, init = bisim.pack_batch(ltss)
     N, M = int(so[-1]), int(to[-1])
-    opts = bisim.make_opts(threads=args.threads, max_ctas=args.max_ctas)
+    tuned = None
+    if args.threads == 0 and not args.no_autotune:
+        # launch shape picked by the autotuner, timed on this batch
+        from paper_2105_11788_gb300 import autotune
+
+        tuner = autotune.BatchTuner(cache_path=os.path.join(tempfile.gettempdir(), "bisim_bench_autotune.json"), repeats=1)
+        opts, tuned = tuner.tune(ltss, device=str(dev))
+    else:
+        opts = bisim.make_opts(threads=args.threads, max_ctas=args.max_ctas)
     d = lambda a: torch.from_numpy(a).to(dev)  # noqa: E731
     tsrc, tact, tdst = d(src), d(act), d(dst)
     out = torch.empty(N, dtype=torch.int32, device=dev)
@@ -332,6 +341,9 @@ def run_stream(args, world, rank, local):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": STREAM_DESC, "k": k, "n_total": N, "m_total": M,
+                       "threads": opts.threads, "ctas_per_sm": opts.ctas_per_sm,
+                       "wide_threads": opts.wide_threads, "wide_min_states": opts.wide_min_states,
+                       "autotune": tuned,
                        "l2": "inputs larger than L2",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "kernel": "k_frontier_batch", "achieved": achieved, "peak": hbm,
@@ -389,6 +401,7 @@ def main():
                     help="frontier: light-round threshold (0 = library default, <0 = grid only)")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="stream: skip the launch-shape tuner")
     args = ap.parse_args()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":

@@ -81,6 +81,10 @@ typedef struct bisim_opts {
                             1 = one round per label; 2 = direct grouping by
                             (initial block, label set) when |Act| <= 128. Same
                             partition; leader labels may differ */
+    int32_t wide_threads;    /* batch: threads per CTA of a second, concurrent launch
+                                that takes the largest LTSs (0 = single launch) */
+    int32_t wide_min_states; /* batch: LTSs with at least this many states go to the
+                                wide launch */
     int32_t reserved;
 } bisim_opts;
 

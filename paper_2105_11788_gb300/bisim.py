@@ -44,6 +44,8 @@ class bisim_opts(ctypes.Structure):
         ("max_ctas", ctypes.c_int32),
         ("light_edges", ctypes.c_int32),
         ("preprocess", ctypes.c_int32),
+        ("wide_threads", ctypes.c_int32),
+        ("wide_min_states", ctypes.c_int32),
         ("reserved", ctypes.c_int32),
     ]
 
@@ -143,9 +145,10 @@ def _check(code: int, where: str):
 def make_opts(engine: int = ENGINE_AUTO, rcpp_alg2: bool = False, raw_labels: bool = False,
               threads: int = 0, ctas_per_sm: int = 0, round_cap: int = 0, timeout_ms: int = 0,
               test_hook: int = 0, max_ctas: int = 0, light_edges: int = 0,
-              preprocess: int = 0) -> bisim_opts:
+              preprocess: int = 0, wide_threads: int = 0, wide_min_states: int = 0) -> bisim_opts:
     return bisim_opts(engine, int(rcpp_alg2), int(raw_labels), threads, ctas_per_sm, test_hook,
-                      round_cap, timeout_ms, max_ctas, light_edges, preprocess, 0)
+                      round_cap, timeout_ms, max_ctas, light_edges, preprocess, wide_threads,
+                      wide_min_states, 0)
 
 
 # ----------------------------------------------------------- C-ABI mirrors

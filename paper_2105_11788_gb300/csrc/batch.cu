@@ -123,6 +123,7 @@ int batch_plan_build(bisim_plan_s* p, int32_t k, const int64_t* state_off_h, con
         return wa > wb;
     });
     BISIM_CUDA_TRY(cudaMemcpyAsync(p->batch_order.p, order.data(), 4 * (size_t)k, cudaMemcpyHostToDevice, st));
+    p->batch_order_h = order;
     DevMem toff, usrc, uact, udst, uinit;
     BISIM_TRY(toff.alloc(8 * ((size_t)k + 1), st));
     BISIM_CUDA_TRY(cudaMemcpyAsync(toff.p, trans_off_h, 8 * ((size_t)k + 1), cudaMemcpyHostToDevice, st));
@@ -155,8 +156,9 @@ int bisim_batch_plan(int32_t k, const int64_t* state_off_h, const int64_t* trans
                      const bisim_opts* opts, void* stream, bisim_plan_t* out) {
     if (!out) return BISIM_EINVAL;
     *out = nullptr;
-    if (opts && (opts->threads < 0 || opts->threads > 1024 || (opts->threads & 31))) {
-        set_last_error("opts.threads must be a multiple of 32 in [32, 1024] (or 0)");
+    if (opts && (opts->threads < 0 || opts->threads > 1024 || (opts->threads & 31) || opts->wide_threads < 0 ||
+                 opts->wide_threads > 1024 || (opts->wide_threads & 31))) {
+        set_last_error("opts.threads / wide_threads must be multiples of 32 in [32, 1024] (or 0)");
         return BISIM_EINVAL;
     }
     if (k < 1 || !state_off_h || !trans_off_h || !num_act_h) {

@@ -360,6 +360,11 @@ bisim_plan_s::~bisim_plan_s() {
     if (ev1) cudaEventDestroy(ev1);
     if (evk0) cudaEventDestroy(evk0);
     if (evk1) cudaEventDestroy(evk1);
+    if (aux_event) cudaEventDestroy(aux_event);
+    if (aux_stream) {
+        cudaStreamSynchronize(aux_stream);
+        cudaStreamDestroy(aux_stream);
+    }
 }
 
 namespace bisim {

@@ -22,8 +22,8 @@ struct bisim_ctrl {
     int n_touched[2];            // frontier: warp-list length by round parity
     int n_mid[2];                // frontier: CTA-list length by round parity
     unsigned long long bq_tail[32];  // frontier worklist: pushes per size bucket
-    int next_inst;                   // batch engine: next LTS to take
-    int pad2;
+    int next_inst;                   // batch engine: next LTS to take (narrow launch)
+    int next_inst_wide;              // batch engine: next LTS of the wide launch
     // hybrid engine: CTA 0 publishes heavy rounds to the parked CTAs
     unsigned long long cmd_seq;      // number of commands published
     unsigned long long heartbeat;    // rounds CTA 0 has finished (progress for the parked CTAs' limit)
@@ -87,6 +87,9 @@ struct bisim_plan_s {
     bisim::DevMem batch_act;            // int32 [k]
     bisim::DevMem batch_order;          // int32 [k]: LTS indices, largest first
     bisim::DevMem inst_rounds;          // int64 [k]
+    std::vector<int32_t> batch_order_h; // [k]
+    cudaStream_t aux_stream = nullptr;  // second stream of the split batch schedule
+    cudaEvent_t aux_event = nullptr;
 
     uint32_t stamp = 0;      // last round stamp used (marks are never cleared)
     int64_t pre_rounds = 0;

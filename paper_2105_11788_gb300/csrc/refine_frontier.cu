@@ -986,16 +986,52 @@ int refine_frontier_batch(bisim_plan_s* p, bisim_stats* stats, std::vector<long 
     bt.inst_rounds = p->inst_rounds.as<long long>();
     bt.block0 = p->block0.as<int32_t>();
     const int threads = p->opts.threads > 0 ? p->opts.threads : 256;
-    int occ = 0;
-    BISIM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_frontier_batch, threads, 0));
-    int per_sm = p->opts.ctas_per_sm > 0 ? std::min(p->opts.ctas_per_sm, occ) : occ;
-    int grid = std::max(1, std::min(k, p->sm_count * std::max(per_sm, 1)));
-    if (p->opts.max_ctas > 0) grid = std::min(grid, p->opts.max_ctas);
+    // optional split schedule: the LTSs with at least wide_min_states states
+    // (a prefix of the largest-first order) run in a second launch of wide
+    // CTAs on an auxiliary stream, concurrently with the narrow launch
+    int32_t kw = 0;
+    if (p->opts.wide_threads > 0 && p->opts.wide_min_states > 0)
+        while (kw < k) {
+            const int32_t li = p->batch_order_h[(size_t)kw];
+            if (p->state_off_h[li + 1] - p->state_off_h[li] < p->opts.wide_min_states) break;
+            kw++;
+        }
+    auto grid_of = [&](int thr, int cnt, int* g) -> int {
+        int occ = 0;
+        BISIM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_frontier_batch, thr, 0));
+        int per_sm = p->opts.ctas_per_sm > 0 ? std::min(p->opts.ctas_per_sm, occ) : occ;
+        int gg = std::max(1, std::min(cnt, p->sm_count * std::max(per_sm, 1)));
+        if (p->opts.max_ctas > 0) gg = std::min(gg, p->opts.max_ctas);
+        *g = gg;
+        return BISIM_OK;
+    };
+    int grid = 0, gridw = 0;
     BISIM_CUDA_TRY(cudaEventRecord(p->evk0, st));
-    k_frontier_batch<<<grid, threads, 0, st>>>(a, bt);
-    BISIM_LAUNCHED();
-    BISIM_CUDA_TRY(cudaGetLastError());
+    if (kw > 0) {
+        if (!p->aux_stream) BISIM_CUDA_TRY(cudaStreamCreateWithFlags(&p->aux_stream, cudaStreamNonBlocking));
+        if (!p->aux_event) BISIM_CUDA_TRY(cudaEventCreateWithFlags(&p->aux_event, cudaEventDisableTiming));
+        BISIM_CUDA_TRY(cudaStreamWaitEvent(p->aux_stream, p->evk0, 0));
+        BISIM_TRY(grid_of(p->opts.wide_threads, kw, &gridw));
+        BatchArgs bw = bt;
+        bw.k = kw;
+        bw.next = &p->ctrl.as<bisim_ctrl>()->next_inst_wide;
+        k_frontier_batch<<<gridw, p->opts.wide_threads, 0, p->aux_stream>>>(a, bw);
+        BISIM_LAUNCHED();
+        BISIM_CUDA_TRY(cudaGetLastError());
+        BISIM_CUDA_TRY(cudaEventRecord(p->aux_event, p->aux_stream));
+    }
+    if (kw < k) {
+        BISIM_TRY(grid_of(threads, k - kw, &grid));
+        BatchArgs bn = bt;
+        bn.k = k - kw;
+        bn.order = bt.order + kw;
+        k_frontier_batch<<<grid, threads, 0, st>>>(a, bn);
+        BISIM_LAUNCHED();
+        BISIM_CUDA_TRY(cudaGetLastError());
+    }
+    if (kw > 0) BISIM_CUDA_TRY(cudaStreamWaitEvent(st, p->aux_event, 0));
     BISIM_CUDA_TRY(cudaEventRecord(p->evk1, st));
+    grid += gridw;
     rounds.assign((size_t)k, 0);
     if (k) BISIM_CUDA_TRY(cudaMemcpyAsync(rounds.data(), p->inst_rounds.p, 8 * (size_t)k, cudaMemcpyDeviceToHost, st));
     BISIM_TRY(read_ctrl(p));

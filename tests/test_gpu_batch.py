@@ -103,3 +103,16 @@ def test_batch_refine_twice_on_one_plan():
     assert np.array_equal(first, second)
     for i, l in enumerate(ltss):
         assert first[so[i]:so[i + 1]].tolist() == oracle.ks_lts(l).tolist()
+
+
+def test_split_schedule_matches_single_launch():
+    """Largest LTSs in a concurrent wide launch: same results."""
+    rng = np.random.default_rng(31)
+    ltss = [lts_gen.stream_instance(rng, n_lo=100, n_hi=30000, idx=i) for i in range(64)]
+    want = bisim.reduce_batch(ltss)
+    for wthr, wmin in ((1024, 5000), (512, 1), (256, 1 << 30)):
+        got = bisim.reduce_batch(ltss, bisim.make_opts(threads=128, wide_threads=wthr, wide_min_states=wmin))
+        for a, b in zip(got, want):
+            assert np.array_equal(a, b)
+    for l, g in zip(ltss[:16], want[:16]):
+        assert g.tolist() == oracle.ks_lts(l).tolist()
