@@ -343,6 +343,7 @@ def run_stream(args, world, rank, local):
             "config": {"workload": STREAM_DESC, "k": k, "n_total": N, "m_total": M,
                        "threads": opts.threads, "ctas_per_sm": opts.ctas_per_sm,
                        "wide_threads": opts.wide_threads, "wide_min_states": opts.wide_min_states,
+                       "splitters": opts.splitters, "split_budget": opts.split_budget,
                        "autotune": tuned,
                        "l2": "inputs larger than L2",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
@@ -530,7 +531,7 @@ def main():
             "cpu_baseline": cpu,
             "gpu_launches": int(sum(s.launches for s in stats)),
             "clocks": clk,
-            "detail": {"rounds": st.rounds, "pre_rounds": st.pre_rounds,
+            "detail": {"rounds": st.rounds, "steps": st.steps, "pre_rounds": st.pre_rounds,
                        "initial_blocks": st.initial_blocks, "num_blocks": st.num_blocks,
                        "mark_length": st.mark_length, "t_plan_ms": st.t_plan_ms,
                        "t_refine_ms": st.t_refine_ms, "t_pre_ms": st.t_pre_ms,

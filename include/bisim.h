@@ -85,6 +85,15 @@ typedef struct bisim_opts {
                                 that takes the largest LTSs (0 = single launch) */
     int32_t wide_min_states; /* batch: LTSs with at least this many states go to the
                                 wide launch */
+    int32_t splitters;       /* frontier engine: most splitters per round (0 = 8192 for
+                                one LTS, at most 8 per thread of a CTA; 0 = 1 for a
+                                batch, at most 128 per CTA; 1 = one splitter per round,
+                                as in Algorithm 3).
+                                Splitters whose touched blocks overlap are deferred to
+                                a later round */
+    int32_t split_budget;    /* frontier engine, rounds with several splitters: at most
+                                this many splitter states per warp (0 = 1 on the grid,
+                                8 per CTA of a batch) */
     int32_t reserved;
 } bisim_opts;
 
@@ -104,6 +113,8 @@ typedef struct bisim_stats {
     int64_t launches;       /* kernels launched by bisim_plan + the last bisim_refine */
     int32_t engine;         /* engine that ran */
     int32_t grid_ctas;      /* CTAs of the persistent launch */
+    int64_t steps;          /* barrier-separated rounds incl. the final empty one; equals
+                               rounds when every round takes one splitter */
 } bisim_stats;
 
 typedef struct bisim_plan_s* bisim_plan_t;

@@ -6,7 +6,7 @@ ones want wide CTAs (a round's touched blocks spread over more warps), and a
 batch with both can use the split schedule (the largest LTSs in a concurrent
 launch of wide CTAs). The tuner times `bisim_batch_refine` on the batch for
 each candidate (threads per CTA, CTAs per SM, wide-launch threads and
-threshold), keeps the fastest, and caches the choice in a JSON file keyed by
+threshold, splitters per round and their state budget), keeps the fastest, and caches the choice in a JSON file keyed by
 the batch's shape bucket:
 
     (log2 of the LTS count, log2 of the largest LTS's states, log2 of the mean
@@ -26,11 +26,17 @@ import numpy as np
 
 from . import bisim
 
-# (threads, ctas_per_sm, wide_threads, wide_min_states)
-CANDIDATES: Tuple[Tuple[int, int, int, int], ...] = (
-    (128, 0, 0, 0), (256, 0, 0, 0), (512, 0, 0, 0), (1024, 0, 0, 0),
-    (256, 0, 1024, 1 << 15), (256, 0, 1024, 1 << 16), (128, 0, 1024, 1 << 15), (256, 0, 512, 1 << 14),
+# (threads, ctas_per_sm, wide_threads, wide_min_states, splitters, split_budget)
+CANDIDATES: Tuple[Tuple[int, int, int, int, int, int], ...] = (
+    (128, 0, 0, 0, 1, 0), (256, 0, 0, 0, 1, 0), (512, 0, 0, 0, 1, 0), (1024, 0, 0, 0, 1, 0),
+    (256, 0, 1024, 1 << 15, 1, 0), (256, 0, 1024, 1 << 16, 1, 0), (128, 0, 1024, 1 << 15, 1, 0),
+    (256, 0, 0, 0, 16, 2), (256, 0, 0, 0, 64, 4), (512, 0, 0, 0, 64, 4), (256, 0, 1024, 1 << 15, 64, 4),
 )
+KEYS = ("threads", "ctas_per_sm", "wide_threads", "wide_min_states", "splitters", "split_budget")
+
+
+def _name(c) -> str:
+    return "t{}x{}+w{}@{}+s{}b{}".format(*c)
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "bisim_gb300_autotune.json")
 
 
@@ -65,9 +71,7 @@ class BatchTuner:
         rec = self.cache.get(shape_key(ltss))
         if rec is None:
             return None
-        return bisim.make_opts(threads=rec["threads"], ctas_per_sm=rec["ctas_per_sm"],
-                               wide_threads=rec.get("wide_threads", 0),
-                               wide_min_states=rec.get("wide_min_states", 0))
+        return bisim.make_opts(**{k: rec.get(k, 0) for k in KEYS})
 
     def tune(self, ltss: Sequence, device: str = "cuda") -> Tuple[bisim.bisim_opts, dict]:
         """Time every candidate on this batch; record and return the best."""
@@ -80,11 +84,11 @@ class BatchTuner:
         out = torch.empty(max(n_total, 1), dtype=torch.int32, device=device)
         stream = int(torch.cuda.current_stream().cuda_stream)
         timings = {}
-        for threads, per_sm, wthr, wmin in self.candidates:
+        for cand in self.candidates:
             # the options (and with them the launch shape) belong to a plan,
             # so every candidate gets its own plan of the same batch
             best = math.inf
-            opts = bisim.make_opts(threads=threads, ctas_per_sm=per_sm, wide_threads=wthr, wide_min_states=wmin)
+            opts = bisim.make_opts(**dict(zip(KEYS, cand)))
             hc = bisim.bisim_batch_plan(len(ltss), so, to, na, tsrc.data_ptr(), tact.data_ptr(), tdst.data_ptr(),
                                         tinit.data_ptr() if tinit is not None else None, opts, stream)
             try:
@@ -93,16 +97,15 @@ class BatchTuner:
                     best = min(best, st.t_refine_ms)
             finally:
                 bisim.bisim_plan_destroy(hc)
-            timings[f"{threads}x{per_sm}+{wthr}@{wmin}"] = best
-        name = min(timings, key=timings.get)
-        head, wide = name.split("+")
-        threads, per_sm = (int(x) for x in head.split("x"))
-        wthr, wmin = (int(x) for x in wide.split("@"))
-        rec = {"threads": threads, "ctas_per_sm": per_sm, "wide_threads": wthr, "wide_min_states": wmin,
-               "refine_ms": timings[name], "timings_ms": timings, "when": time.strftime("%Y-%m-%dT%H:%M:%S")}
+            timings[_name(cand)] = (best, cand)
+        name = min(timings, key=lambda k: timings[k][0])
+        ms, cand = timings[name]
+        rec = dict(zip(KEYS, cand))
+        rec.update({"refine_ms": ms, "timings_ms": {k: v[0] for k, v in timings.items()},
+                    "when": time.strftime("%Y-%m-%dT%H:%M:%S")})
         self.cache[shape_key(ltss)] = rec
         self.save()
-        return bisim.make_opts(threads=threads, ctas_per_sm=per_sm, wide_threads=wthr, wide_min_states=wmin), rec
+        return bisim.make_opts(**dict(zip(KEYS, cand))), rec
 
     def opts_for(self, ltss: Sequence, device: str = "cuda") -> bisim.bisim_opts:
         """Cached choice for this batch shape, tuning on a miss."""

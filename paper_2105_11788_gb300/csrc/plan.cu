@@ -385,6 +385,7 @@ int reserve_stamps(bisim_plan_s* p, int64_t rounds, uint32_t* base) {
             if (p->frontier_ready) {
                 BISIM_CUDA_TRY(cudaMemsetAsync(p->smark.p, 0, sizeof(uint32_t) * p->n, p->st));
                 BISIM_CUDA_TRY(cudaMemsetAsync(p->kmark.p, 0, sizeof(uint32_t) * p->n, p->st));
+                BISIM_CUDA_TRY(cudaMemsetAsync(p->claim.p, 0xff, sizeof(uint64_t) * p->n, p->st));
             }
         }
         p->stamp = 0;
@@ -394,9 +395,11 @@ int reserve_stamps(bisim_plan_s* p, int64_t rounds, uint32_t* base) {
 }
 
 int launch_persistent(const void* fn, void** args, int threads, bisim_plan_s* p, int* grid_out,
-                      int per_sm_default) {
+                      int per_sm_default, size_t dyn_smem) {
     int occ = 0;
-    BISIM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, 0));
+    if (dyn_smem > 48 * 1024)
+        BISIM_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem));
+    BISIM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, dyn_smem));
     if (occ < 1) {
         set_last_error("persistent kernel does not fit on an SM");
         return BISIM_ECUDA;
@@ -407,7 +410,7 @@ int launch_persistent(const void* fn, void** args, int threads, bisim_plan_s* p,
     if (p->opts.max_ctas > 0) grid = std::min(grid, p->opts.max_ctas);
     *grid_out = grid;
     BISIM_CUDA_TRY(cudaEventRecord(p->evk0, p->st));
-    BISIM_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(threads), args, 0, p->st));
+    BISIM_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(threads), args, dyn_smem, p->st));
     BISIM_LAUNCHED();
     BISIM_CUDA_TRY(cudaEventRecord(p->evk1, p->st));
     return BISIM_OK;

@@ -27,9 +27,17 @@ struct bisim_ctrl {
     // hybrid engine: CTA 0 publishes heavy rounds to the parked CTAs
     unsigned long long cmd_seq;      // number of commands published
     unsigned long long heartbeat;    // rounds CTA 0 has finished (progress for the parked CTAs' limit)
-    int cmd_C;                       // splitter of the published heavy round, -1 = stop
+    int cmd_C;                       // splitter of the published heavy round, -1 = stop, -2 = several
     unsigned cmd_stamp;              // its round stamp
+    int cmd_K;                       // number of splitters of a published multi-splitter round
+    int pad3;
+    long long commits;               // splitter iterations carried out (multi-splitter schedules)
 };
+
+// Most splitters one multi-splitter round takes: grid rounds of the hybrid
+// schedule, and CTA rounds of the batch schedule.
+constexpr int BISIM_KMAX_GRID = 8192;
+constexpr int BISIM_KMAX_CTA = 128;
 
 // Frontier worklist: one FIFO ring of n entries per size bucket
 // floor(log2(block size)); the splitter is taken from the lowest non-empty
@@ -78,6 +86,10 @@ struct bisim_plan_s {
     bisim::DevMem kmark;     // uint32 [n]: round stamp of membership in a kept part
     bisim::DevMem tlist;     // int32 [2n]: touched-label lists (warp, CTA)
     bisim::DevMem queue;     // int32 [BISIM_BUCKETS * n]: FIFO rings of unstable labels
+    bisim::DevMem claim;     // uint64 [n]: per label, (~stamp << 32 | splitter index) of the round's claim
+    bisim::DevMem bspl;      // int32 [n]: per touched label, the splitter that touched it
+    bisim::DevMem msel;      // int32 [2 * KMAX_GRID + 1] + uint32 [KMAX_GRID]: published splitters,
+                             // their size prefix, and the round in which each lost a claim
 
     // batch plans: k LTSs over disjoint state ranges of one union LTS
     int32_t batch_k = 0;
@@ -122,7 +134,7 @@ int reserve_stamps(bisim_plan_s* p, int64_t rounds, uint32_t* base);
 
 // Cooperative launch on one SM-multiple grid, bracketed by evk0 / evk1.
 int launch_persistent(const void* fn, void** args, int threads, bisim_plan_s* p, int* grid_out,
-                      int per_sm_default = 1);
+                      int per_sm_default = 1, size_t dyn_smem = 0);
 // Device time between evk0 and evk1 of the last persistent launch.
 int persistent_ms(bisim_plan_s* p, double* ms);
 int read_ctrl(bisim_plan_s* p);

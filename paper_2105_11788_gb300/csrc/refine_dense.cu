@@ -177,6 +177,7 @@ int refine_dense(bisim_plan_s* p, bisim_stats* stats) {
     p->stamp = base + (uint32_t)std::min<long long>(p->ctrl_h->rounds + 1, cap + 1);
     if (stats) {
         stats->rounds = p->ctrl_h->rounds;
+        stats->steps = p->ctrl_h->rounds;
         stats->edges_visited = p->ctrl_h->edges;
         stats->states_visited = p->ctrl_h->states;
         stats->engine = BISIM_ENGINE_DENSE;

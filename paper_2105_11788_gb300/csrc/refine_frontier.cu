@@ -31,6 +31,7 @@ using namespace bisim;
 namespace {
 
 constexpr int WARP_MAX = 64;  // blocks up to this size are split by one warp
+constexpr int32_t MULTI = -2;  // splitter argument of a round with several splitters
 
 struct FrontierArgs {
     int32_t n;
@@ -51,6 +52,8 @@ struct FrontierArgs {
     uint32_t* kmark;  // [n] per state: stamp of the round it was in a kept part
     int32_t* tlist;   // [2n]: warp list, CTA list
     int32_t* queue;   // [n]
+    unsigned long long* claim;  // [n] per label: (~stamp << 32) | index of the claiming splitter
+    int32_t* bspl;    // [n] per touched label: its splitter (multi-splitter rounds)
     bisim_ctrl* ctrl;
     GridBarrier gb;
     uint32_t stamp0;
@@ -90,7 +93,8 @@ __device__ __forceinline__ void set_unstable(const FrontierArgs& a, const Workli
 __device__ __forceinline__ void finish_split_warp(const FrontierArgs& a, const Worklist& wl, int32_t b,
                                                   int32_t leader, int32_t C) {
     const unsigned lane = threadIdx.x & 31u;
-    const int32_t lab = lane == 0 ? b : lane == 1 ? leader : (lane == 2 && !a.alg2) ? C : -1;
+    int32_t lab = lane == 0 ? b : lane == 1 ? leader : (lane == 2 && !a.alg2) ? C : -1;
+    if (lab == MULTI) lab = ldcg(&a.bspl[b]);  // the splitter that touched b this round
     if (lab >= 0) set_unstable(a, wl, lab);
 }
 
@@ -174,6 +178,8 @@ struct CtaShared {
     int mn;
     unsigned lmask;
     int C;
+    int bx[BISIM_BUCKETS];  // select_many: entries before each bucket
+    int bn[BISIM_BUCKETS];  // select_many: entries taken from each bucket at most
     unsigned long long head[BISIM_BUCKETS];  // this CTA's copy of the worklist heads
 };
 
@@ -197,6 +203,36 @@ __device__ __forceinline__ int cta_rank(bool p, CtaShared& sh, int& total) {
     }
     __syncthreads();
     const int r = sh.wcnt[wid] + __popc(bal & lanemask_lt());
+    total = sh.total;
+    __syncthreads();
+    return r;
+}
+
+// Block-wide exclusive prefix sum of v and the block total.
+__device__ __forceinline__ int cta_scan(int v, CtaShared& sh, int& total) {
+    const unsigned lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
+    const unsigned nw = blockDim.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if ((int)lane >= o) x += y;
+    }
+    if (lane == 31) sh.wcnt[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        const int c = (int)lane < (int)nw ? sh.wcnt[lane] : 0;
+        int y = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int z = __shfl_up_sync(0xffffffffu, y, o);
+            if ((int)lane >= o) y += z;
+        }
+        if ((int)lane < (int)nw) sh.wcnt[lane] = y - c;
+        if (lane == 31) sh.total = y;
+    }
+    __syncthreads();
+    const int r = sh.wcnt[wid] + x - v;
     total = sh.total;
     __syncthreads();
     return r;
@@ -483,32 +519,206 @@ __device__ void split_step(const FrontierArgs& a, const Worklist& wl, CtaShared&
 // of C, lanes over its incoming transitions. The first mark of a source s in
 // the round ranks it among the marked members of its block; the first marked
 // member of a block appends the block to the warp list or the CTA list.
+// Marks of one member t of a splitter, by one warp (lanes over t's incoming
+// transitions). Cw >= 0 is recorded as the splitter of each newly touched
+// block (rounds with several splitters).
+__device__ __forceinline__ void mark_member(const FrontierArgs& a, int32_t t, uint32_t stamp, int32_t Cw,
+                                            int* n_small, int* n_mid, int32_t* small_list, int32_t* mid_list,
+                                            long long& edges) {
+    const int lane = threadIdx.x & 31;
+    const int32_t j0 = a.in_ptr[t], j1 = a.in_ptr[t + 1];
+    if (lane == 0) edges += j1 - j0;
+    for (int32_t j = j0 + lane; j < j1; j += 32) {
+        const unsigned long long e = a.in_edge[j];
+        const int32_t s = (int32_t)(e >> 32);
+        a.mark[(uint32_t)e] = stamp;
+        const int32_t b = ldcg(&a.block[s]);  // issued before the atomic: both depend on s only
+        if (atomicExch(&a.smark[s], stamp) == stamp) continue;
+        const int32_t bb = ldcg(&a.bbeg[b]), be = ldcg(&a.bend[b]);
+        if (be - bb <= 1) continue;
+        const int32_t rk = atomicAdd(&a.mcnt[b], 1);
+        a.mscr[be - 1 - rk] = s;
+        if (rk == 0) {
+            if (Cw >= 0) a.bspl[b] = Cw;
+            if (be - bb <= WARP_MAX)
+                small_list[atomicAdd(n_small, 1)] = b;
+            else
+                mid_list[atomicAdd(n_mid, 1)] = b;
+        }
+    }
+}
+
 __device__ __forceinline__ void mark_step(const FrontierArgs& a, int32_t C, uint32_t stamp, int64_t gw,
                                           int64_t nwarps, int* n_small, int* n_mid, int32_t* small_list,
                                           int32_t* mid_list, long long& edges) {
-    const int lane = threadIdx.x & 31;
     const int32_t b0 = ldcg(&a.bbeg[C]), e0 = ldcg(&a.bend[C]);
-    for (int64_t idx = b0 + gw; idx < e0; idx += nwarps) {
-        const int32_t t = ldcg(&a.elems[idx]);
+    for (int64_t idx = b0 + gw; idx < e0; idx += nwarps)
+        mark_member(a, ldcg(&a.elems[idx]), stamp, -1, n_small, n_mid, small_list, mid_list, edges);
+}
+
+// ------------------------------------------- rounds with several splitters
+//
+// A round may take K splitters C_0 .. C_{K-1} at once. The splitter rounds
+// of Algorithm 3 for C_i and C_j touch disjoint data, and so may run
+// concurrently with the effect of running them one after the other, when
+// neither C_j nor any block holding a predecessor of C_j is C_i or a block
+// holding a predecessor of C_i. (Blocks of one state are exempt: they are
+// read, never split.) Before marking, every splitter claims its block and
+// the blocks of its predecessors with atomicMin on a per-label word
+// (~stamp << 32 | j); a splitter that meets a claim of a smaller index, or
+// whose claim is displaced by one, has lost and goes back to the worklist.
+// Splitter 0 never loses, so every round carries out at least one splitter
+// iteration. The winners then mark with one shared stamp (their marked
+// slots are disjoint) and split exactly as in a one-splitter round.
+
+// loads that read shared memory, or global memory past L1, through a generic pointer
+__device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t* p) { return *(volatile const uint32_t*)p; }
+__device__ __forceinline__ int ld_volatile_i32(const int* p) { return *(volatile const int*)p; }
+
+// entries of a multi-splitter selection per thread at most
+constexpr int SEL_E = 8;
+
+// Pops up to kmax labels (lowest size bucket first, FIFO inside a bucket;
+// at most SEL_E per thread of the CTA) while their blocks hold at most
+// `budget` states together; the first is always taken. selC[0..K) gets the
+// labels, selP[0..K] the exclusive prefix of their block sizes. Returns K to
+// every thread (0: the worklist is empty). Thread t handles the entries
+// [t*E, t*E + E), so its queue and size loads are issued together.
+__device__ int select_many(const FrontierArgs& a, const Worklist& wl, unsigned long long* head, CtaShared& sh,
+                           int32_t* selC, int32_t* selP, int kmax, int32_t budget) {
+    const unsigned lane = threadIdx.x & 31u;
+    kmax = min(kmax, SEL_E * (int)blockDim.x);
+    if (threadIdx.x < 32) {
+        const unsigned long long h = head[lane];
+        const unsigned long long t = *(volatile const unsigned long long*)&wl.tail[lane];
+        const int av = (int)min(t - h, (unsigned long long)kmax);
+        int x = av;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if ((int)lane >= o) x += y;
+        }
+        sh.bx[lane] = x - av;
+        sh.bn[lane] = av;
+        if (lane == 31) sh.total = min(x, kmax);
+    }
+    __syncthreads();
+    const int k0 = sh.total;
+    const int E = (k0 + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int j0 = (int)threadIdx.x * E;
+    int32_t cs[SEL_E];
+    int sz[SEL_E];
+    int bk = 0;
+#pragma unroll
+    for (int e = 0; e < SEL_E; e++) {
+        const int j = j0 + e;
+        cs[e] = -1;
+        if (e < E && j < k0) {
+            while (j >= sh.bx[bk] + sh.bn[bk]) bk++;
+            const unsigned long long q = head[bk] + (unsigned long long)(j - sh.bx[bk]);
+            cs[e] = ldcg(&wl.queue[(size_t)bk * wl.stride + wl.base + q % (unsigned long long)wl.cap]);
+        }
+    }
+    int mine = 0;
+#pragma unroll
+    for (int e = 0; e < SEL_E; e++) {
+        sz[e] = cs[e] >= 0 ? ldcg(&a.bend[cs[e]]) - ldcg(&a.bbeg[cs[e]]) : 0;
+        mine += sz[e];
+    }
+    int tot;
+    int ex = cta_scan(mine, sh, tot);
+    // sizes are positive, so the taken entries are a prefix
+    int taken = 0;
+#pragma unroll
+    for (int e = 0; e < SEL_E; e++) {
+        const int j = j0 + e;
+        if (cs[e] >= 0 && (j == 0 || ex + sz[e] <= budget)) {
+            selC[j] = cs[e];
+            selP[j] = ex;
+            selP[j + 1] = ex + sz[e];  // the next entry's prefix (same value if it is taken)
+            taken++;
+        }
+        ex += sz[e];
+    }
+    int K;
+    cta_scan(taken, sh, K);
+    if (threadIdx.x < 32) head[lane] += (unsigned long long)max(0, min(sh.bn[lane], K - sh.bx[lane]));
+    __syncthreads();
+    return K;
+}
+
+// index j of the splitter whose member range holds item i (selP[0] = 0)
+__device__ __forceinline__ int find_sel(const int32_t* selP, int K, int32_t i) {
+    int lo = 0, hi = K - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (selP[mid] <= i)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void claim_label(const FrontierArgs& a, int32_t b, unsigned long long key,
+                                            uint32_t* lost, uint32_t stamp) {
+    const unsigned long long old = atomicMin(&a.claim[b], key);
+    if ((old >> 32) == (key >> 32)) {
+        const uint32_t jo = (uint32_t)old, j = (uint32_t)key;
+        if (jo < j)
+            lost[j] = stamp;
+        else if (jo > j)
+            lost[jo] = stamp;
+    }
+}
+
+// Claim phase: splitter j claims its own block and every block of more than
+// one state that holds a predecessor of one of its members. Items (members
+// of the K splitters, in order) go to warps gw, gw + nwarps, ...
+__device__ void claim_step(const FrontierArgs& a, const int32_t* selC, const int32_t* selP, int K, uint32_t* lost,
+                           uint32_t stamp, int64_t gw, int64_t nwarps) {
+    const int lane = threadIdx.x & 31;
+    const int32_t tot = selP[K];
+    const unsigned long long hi = (unsigned long long)(~stamp) << 32;
+    for (int64_t i = gw; i < tot; i += nwarps) {
+        const int j = find_sel(selP, K, (int32_t)i);
+        const int32_t C = selC[j];
+        const unsigned long long key = hi | (unsigned)j;
+        if (i == selP[j] && lane == 0 && ldcg(&a.bend[C]) - ldcg(&a.bbeg[C]) > 1) claim_label(a, C, key, lost, stamp);
+        const int32_t t = ldcg(&a.elems[ldcg(&a.bbeg[C]) + (int32_t)i - selP[j]]);
         const int32_t j0 = a.in_ptr[t], j1 = a.in_ptr[t + 1];
-        if (lane == 0) edges += j1 - j0;
-        for (int32_t j = j0 + lane; j < j1; j += 32) {
-            const unsigned long long e = a.in_edge[j];
-            const int32_t s = (int32_t)(e >> 32);
-            a.mark[(uint32_t)e] = stamp;
-            const int32_t b = ldcg(&a.block[s]);  // issued before the atomic: both depend on s only
-            if (atomicExch(&a.smark[s], stamp) == stamp) continue;
-            const int32_t bb = ldcg(&a.bbeg[b]), be = ldcg(&a.bend[b]);
-            if (be - bb <= 1) continue;
-            const int32_t rk = atomicAdd(&a.mcnt[b], 1);
-            a.mscr[be - 1 - rk] = s;
-            if (rk == 0) {
-                if (be - bb <= WARP_MAX)
-                    small_list[atomicAdd(n_small, 1)] = b;
-                else
-                    mid_list[atomicAdd(n_mid, 1)] = b;
+        for (int32_t q = j0 + lane; q < j1; q += 32) {
+            const int32_t s = (int32_t)(a.in_edge[q] >> 32);
+            const int32_t b = ldcg(&a.block[s]);
+            if (ldcg(&a.bend[b]) - ldcg(&a.bbeg[b]) > 1) claim_label(a, b, key, lost, stamp);
+        }
+    }
+}
+
+// Mark phase of a round with several splitters: a splitter that lost a claim
+// goes back to the worklist (its unstable flag is still set); a winner
+// clears its unstable flag (Algorithm 3, line 23) and marks as mark_step.
+__device__ void mark_many(const FrontierArgs& a, const Worklist& wl, const int32_t* selC, const int32_t* selP,
+                          int K, const uint32_t* lost, uint32_t stamp, int64_t gw, int64_t nwarps, int* n_small,
+                          int* n_mid, int32_t* small_list, int32_t* mid_list, long long& edges,
+                          long long& commits) {
+    const int lane = threadIdx.x & 31;
+    const int32_t tot = selP[K];
+    for (int64_t i = gw; i < tot; i += nwarps) {
+        const int j = find_sel(selP, K, (int32_t)i);
+        const int32_t C = selC[j];
+        const bool lose = ld_volatile_u32(&lost[j]) == stamp;
+        if (i == selP[j] && lane == 0) {
+            if (lose) {
+                push(a, wl, C);
+            } else {
+                a.unstable[C] = 0u;
+                commits++;
             }
         }
+        if (lose) continue;
+        const int32_t t = ldcg(&a.elems[ldcg(&a.bbeg[C]) + (int32_t)i - selP[j]]);
+        mark_member(a, t, stamp, C, n_small, n_mid, small_list, mid_list, edges);
     }
 }
 
@@ -574,7 +784,10 @@ __global__ void __launch_bounds__(1024) k_frontier_main(FrontierArgs a) {
     }
     if (edges) atomicAdd((unsigned long long*)&a.ctrl->edges, (unsigned long long)edges);
     if (states) atomicAdd((unsigned long long*)&a.ctrl->states, (unsigned long long)states);
-    if (gtid == 0) a.ctrl->rounds = r;
+    if (gtid == 0) {
+        a.ctrl->rounds = r;
+        a.ctrl->commits = r - 1;  // one splitter per round
+    }
 }
 
 __device__ __forceinline__ unsigned long long ld_acquire_u64_g(const unsigned long long* p) {
@@ -590,11 +803,55 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64_g(const unsigned lo
 // grid with two grid barriers, exactly as k_frontier_main. The other CTAs
 // wait for commands; their wait is bounded by timeout_ns without progress,
 // where progress is a new command or a new heartbeat from CTA 0.
-__global__ void __launch_bounds__(1024) k_frontier_hybrid(FrontierArgs a, int light_edges) {
+struct HybridArgs {
+    int light_edges;   // a one-splitter round with at most 32 members and this many
+                       // incoming transitions runs on CTA 0 alone
+    int kmax;          // most splitters per round (1: one per round); the dynamic shared
+                       // memory holds kmax labels and kmax + 1 prefix entries
+    int budget;        // states of a round's splitters at most (grid rounds)
+    int local_budget;  // rounds with several splitters and at most this many states (<= 32)
+                       // run on CTA 0
+    int32_t* g_selC;   // [BISIM_KMAX_GRID] published splitters
+    int32_t* g_selP;   // [BISIM_KMAX_GRID + 1] their size prefix
+    uint32_t* g_lost;  // [BISIM_KMAX_GRID] round in which each lost a claim
+};
+
+// The three phases of a round with several splitters, by the warps gw,
+// gw + nwarps, ... of the grid (sync = grid barrier) or of one CTA.
+template <typename Sync>
+__device__ __forceinline__ bool multi_round(const FrontierArgs& a, const Worklist& wl, CtaShared& sh, int* defer,
+                                            int* ndefer, const int32_t* selC, const int32_t* selP, int K,
+                                            uint32_t* lost, uint32_t stamp, int64_t gw, int64_t nwarps, int* n_small,
+                                            int* n_mid, int32_t* small_list, int32_t* mid_list, int cta, int ncta,
+                                            long long& edges, long long& states, long long& commits, Sync sync) {
+    claim_step(a, selC, selP, K, lost, stamp, gw, nwarps);
+    if (!sync()) return false;
+    mark_many(a, wl, selC, selP, K, lost, stamp, gw, nwarps, n_small, n_mid, small_list, mid_list, edges, commits);
+    if (!sync()) return false;
+    split_step(a, wl, sh, defer, ndefer, stamp, MULTI, ld_volatile_i32(n_small), small_list, ld_volatile_i32(n_mid), mid_list, gw,
+               nwarps, cta, ncta, states);
+    return sync();
+}
+
+// Hybrid schedule for one LTS. CTA 0 selects the splitters of every round.
+// A round of one light splitter (at most 32 members whose incoming
+// transitions number at most light_edges), or of several splitters with at
+// most local_budget states together, is done by CTA 0 alone with CTA
+// barriers; other rounds are published (cmd_C, cmd_K, cmd_stamp and the
+// splitter list, then cmd_seq with release order) and done by the whole grid
+// with grid barriers, as in k_frontier_main. The other CTAs wait for
+// commands; their wait is bounded by timeout_ns without progress, where
+// progress is a new command or a new heartbeat from CTA 0.
+__global__ void __launch_bounds__(1024) k_frontier_hybrid(FrontierArgs a, HybridArgs h) {
     __shared__ CtaShared sh;
     __shared__ int s_defer[32];
     __shared__ int s_ndefer;
     __shared__ int s_ns, s_nm, s_heavy;
+    __shared__ uint32_t s_lost[32];  // rounds on CTA 0 alone take at most 32 splitters
+    extern __shared__ int32_t s_dyn[];
+    const int kmax = max(h.kmax, 1);
+    int32_t* s_selC = s_dyn;
+    int32_t* s_selP = s_dyn + kmax;
     const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
     const int32_t n = a.n;
@@ -602,22 +859,36 @@ __global__ void __launch_bounds__(1024) k_frontier_hybrid(FrontierArgs a, int li
     const int64_t gw = gtid >> 5, nwarps = gsz >> 5;
     bisim_ctrl* c = a.ctrl;
     unsigned long long tgt = 0;
-    long long edges = 0, states = 0;
+    long long edges = 0, states = 0, commits = 0;
     if (a.test_hook == 1 && blockIdx.x == 0) return;  // testing: never publish, never arrive
     const Worklist wl{c->bq_tail, a.queue, (size_t)n, 0, n};
+    auto gsync = [&]() { return grid_sync(a.gb, tgt); };
+    auto csync = [&]() {
+        __syncthreads();
+        return true;
+    };
     if (blockIdx.x == 0) {
         if (threadIdx.x < BISIM_BUCKETS) sh.head[threadIdx.x] = 0;
+        if (threadIdx.x < 32) s_lost[threadIdx.x] = 0u;
+        __syncthreads();
         int64_t r = 0;
-        unsigned long long seq = 0;
         for (;;) {
             r++;
             const uint32_t stamp = a.stamp0 + (uint32_t)r;
-            int32_t C = select_splitter(wl, sh.head, sh);
-            if (C >= 0 && r > a.round_cap) {
-                if (threadIdx.x == 0) atomicOr(&c->status, ST_ROUNDS);
-                C = -1;
+            int K;
+            int32_t C;
+            if (kmax > 1) {
+                K = select_many(a, wl, sh.head, sh, s_selC, s_selP, kmax, h.budget);
+                C = K > 0 ? s_selC[0] : -1;
+            } else {
+                C = select_splitter(wl, sh.head, sh);
+                K = C >= 0 ? 1 : 0;
             }
-            if (C < 0) {
+            if (K > 0 && r > a.round_cap) {
+                if (threadIdx.x == 0) atomicOr(&c->status, ST_ROUNDS);
+                K = 0;
+            }
+            if (K == 0) {
                 if (threadIdx.x == 0) {
                     c->cmd_C = -1;
                     __threadfence();
@@ -626,7 +897,43 @@ __global__ void __launch_bounds__(1024) k_frontier_hybrid(FrontierArgs a, int li
                 }
                 break;
             }
-            if (threadIdx.x == 0) a.unstable[C] = 0u;
+            if (K > 1) {
+                if (s_selP[K] <= h.local_budget) {
+                    if (threadIdx.x == 0) {
+                        s_ns = 0;
+                        s_nm = 0;
+                    }
+                    __syncthreads();
+                    multi_round(a, wl, sh, s_defer, &s_ndefer, s_selC, s_selP, K, s_lost, stamp, wid, nw, &s_ns,
+                                &s_nm, a.tlist, a.tlist + n, 0, 1, edges, states, commits, csync);
+                    if (threadIdx.x == 0) *(volatile unsigned long long*)&c->heartbeat = (unsigned long long)r;
+                } else {
+                    for (int i = threadIdx.x; i <= K; i += blockDim.x) {
+                        if (i < K) h.g_selC[i] = s_selC[i];
+                        h.g_selP[i] = s_selP[i];
+                    }
+                    __threadfence();
+                    __syncthreads();
+                    if (threadIdx.x == 0) {
+                        c->n_touched[0] = 0;
+                        c->n_mid[0] = 0;
+                        c->cmd_C = MULTI;
+                        c->cmd_K = K;
+                        c->cmd_stamp = stamp;
+                        __threadfence();
+                        atomicAdd(&c->cmd_seq, 1ull);
+                    }
+                    if (!multi_round(a, wl, sh, s_defer, &s_ndefer, s_selC, s_selP, K, h.g_lost, stamp, gw, nwarps,
+                                     &c->n_touched[0], &c->n_mid[0], a.tlist, a.tlist + n, 0, (int)gridDim.x, edges,
+                                     states, commits, gsync))
+                        return;
+                }
+                continue;
+            }
+            if (threadIdx.x == 0) {
+                a.unstable[C] = 0u;
+                commits++;
+            }
             // light or heavy?
             if (threadIdx.x < 32) {
                 const int32_t b0 = ldcg(&a.bbeg[C]), e0 = ldcg(&a.bend[C]);
@@ -637,7 +944,7 @@ __global__ void __launch_bounds__(1024) k_frontier_hybrid(FrontierArgs a, int li
                         const int32_t t = ldcg(&a.elems[b0 + threadIdx.x]);
                         deg = a.in_ptr[t + 1] - a.in_ptr[t];
                     }
-                    heavy = __reduce_add_sync(0xffffffffu, deg) > light_edges;
+                    heavy = __reduce_add_sync(0xffffffffu, deg) > h.light_edges;
                 }
                 if (threadIdx.x == 0) {
                     s_heavy = heavy;
@@ -655,7 +962,6 @@ __global__ void __launch_bounds__(1024) k_frontier_hybrid(FrontierArgs a, int li
             }
             __syncthreads();
             if (s_heavy) {
-                seq++;
                 mark_step(a, C, stamp, gw, nwarps, &c->n_touched[0], &c->n_mid[0], a.tlist, a.tlist + n, edges);
                 if (!grid_sync(a.gb, tgt)) return;
                 split_step(a, wl, sh, s_defer, &s_ndefer, stamp, C, ldcg(&c->n_touched[0]), a.tlist,
@@ -669,10 +975,9 @@ __global__ void __launch_bounds__(1024) k_frontier_hybrid(FrontierArgs a, int li
                 __syncthreads();
                 if (threadIdx.x == 0) *(volatile unsigned long long*)&c->heartbeat = (unsigned long long)r;
             }
-            (void)seq;
         }
     } else {
-        __shared__ int s_cmd;
+        __shared__ int s_cmd, s_K;
         __shared__ unsigned s_stamp;
         unsigned long long seen = 0;
         for (;;) {
@@ -684,9 +989,9 @@ __global__ void __launch_bounds__(1024) k_frontier_hybrid(FrontierArgs a, int li
                     __nanosleep(64);
                     if ((++spins & 31u) == 0) {
                         const unsigned long long now = globaltimer_ns();
-                        const unsigned long long h = ldcg(&c->heartbeat);
-                        if (h != hb) {
-                            hb = h;
+                        const unsigned long long hbv = ldcg(&c->heartbeat);
+                        if (hbv != hb) {
+                            hb = hbv;
                             t0 = now;
                         } else if (now - t0 > a.gb.timeout_ns) {
                             atomicOr(&c->status, ST_TIMEOUT);
@@ -702,12 +1007,26 @@ __global__ void __launch_bounds__(1024) k_frontier_hybrid(FrontierArgs a, int li
                 seen++;
                 s_cmd = ab ? -1 : ldcg(&c->cmd_C);
                 s_stamp = ldcg(&c->cmd_stamp);
+                s_K = ldcg(&c->cmd_K);
             }
             __syncthreads();
             const int32_t C = s_cmd;
             const uint32_t stamp = s_stamp;
+            const int K = s_K;
             __syncthreads();
-            if (C < 0) break;
+            if (C == -1) break;
+            if (C == MULTI) {
+                for (int i = threadIdx.x; i <= K; i += blockDim.x) {
+                    if (i < K) s_selC[i] = ldcg(&h.g_selC[i]);
+                    s_selP[i] = ldcg(&h.g_selP[i]);
+                }
+                __syncthreads();
+                if (!multi_round(a, wl, sh, s_defer, &s_ndefer, s_selC, s_selP, K, h.g_lost, stamp, gw, nwarps,
+                                 &c->n_touched[0], &c->n_mid[0], a.tlist, a.tlist + n, (int)blockIdx.x,
+                                 (int)gridDim.x, edges, states, commits, gsync))
+                    return;
+                continue;
+            }
             mark_step(a, C, stamp, gw, nwarps, &c->n_touched[0], &c->n_mid[0], a.tlist, a.tlist + n, edges);
             if (!grid_sync(a.gb, tgt)) return;
             split_step(a, wl, sh, s_defer, &s_ndefer, stamp, C, ldcg(&c->n_touched[0]), a.tlist,
@@ -717,6 +1036,7 @@ __global__ void __launch_bounds__(1024) k_frontier_hybrid(FrontierArgs a, int li
     }
     if (edges) atomicAdd((unsigned long long*)&c->edges, (unsigned long long)edges);
     if (states) atomicAdd((unsigned long long*)&c->states, (unsigned long long)states);
+    if (commits) atomicAdd((unsigned long long*)&c->commits, (unsigned long long)commits);
 }
 
 // Many LTSs in one launch, one CTA per LTS at a time: the same rounds, with
@@ -731,8 +1051,10 @@ struct BatchArgs {
     const int32_t* __restrict__ order;      // [k] LTS indices, largest first
     const int32_t* __restrict__ num_act;    // [k]
     int* next;                              // LTS counter
-    long long* inst_rounds;                 // [k] out
+    long long* inst_rounds;                 // [k] out: splitter iterations + 1
     int32_t* block0;
+    int kmax;                               // most splitters per round (1: one per round)
+    int budget_per_warp;                    // states of a round's splitters per warp at most
 };
 
 __global__ void __launch_bounds__(1024) k_frontier_batch(FrontierArgs a, BatchArgs bt) {
@@ -741,8 +1063,14 @@ __global__ void __launch_bounds__(1024) k_frontier_batch(FrontierArgs a, BatchAr
     __shared__ int s_ndefer;
     __shared__ unsigned long long s_tail[BISIM_BUCKETS];
     __shared__ int s_ns, s_nm, s_inst;
+    __shared__ int32_t s_selC[BISIM_KMAX_CTA];
+    __shared__ int32_t s_selP[BISIM_KMAX_CTA + 1];
+    __shared__ uint32_t s_lost[BISIM_KMAX_CTA];
+    __shared__ unsigned long long s_commits;
     const int64_t gw = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    long long edges = 0, states = 0;
+    const int kmax = min(max(bt.kmax, 1), BISIM_KMAX_CTA);
+    const int32_t budget = bt.budget_per_warp * (int32_t)nwarps;
+    long long edges = 0, states = 0, steps = 0;
     for (;;) {
         if (threadIdx.x == 0) s_inst = atomicAdd(bt.next, 1);
         __syncthreads();
@@ -756,6 +1084,9 @@ __global__ void __launch_bounds__(1024) k_frontier_batch(FrontierArgs a, BatchAr
             s_tail[threadIdx.x] = 0;
             sh.head[threadIdx.x] = 0;
         }
+        // the round stamps restart with every LTS: forget this CTA's last losses
+        for (int i = threadIdx.x; i < BISIM_KMAX_CTA; i += blockDim.x) s_lost[i] = 0u;
+        if (threadIdx.x == 0) s_commits = 0;
         __syncthreads();
         const Worklist wl{s_tail, a.queue, (size_t)a.n, s0, max(ni, 1)};
         // Algorithm 3, lines 1-3: every label of this LTS is unstable
@@ -764,32 +1095,58 @@ __global__ void __launch_bounds__(1024) k_frontier_batch(FrontierArgs a, BatchAr
         __syncthreads();
         const int64_t cap = 3ll * ni + bt.num_act[li] + 2;
         int64_t r = 0;
+        long long commits = 0;
         for (;;) {
             r++;
             const uint32_t stamp = a.stamp0 + (uint32_t)r;
-            const int32_t C = select_splitter(wl, sh.head, sh);
-            if (C < 0) break;
+            int K;
+            int32_t C;
+            if (kmax > 1) {
+                K = select_many(a, wl, sh.head, sh, s_selC, s_selP, kmax, budget);
+                C = K > 0 ? s_selC[0] : -1;
+            } else {
+                C = select_splitter(wl, sh.head, sh);
+                K = C >= 0 ? 1 : 0;
+            }
+            if (K == 0) break;
             if (r > cap) {
                 if (threadIdx.x == 0) atomicOr(&a.ctrl->status, ST_ROUNDS);
                 break;
             }
             if (threadIdx.x == 0) {
-                a.unstable[C] = 0u;
+                if (K == 1) {
+                    a.unstable[C] = 0u;
+                    commits++;
+                }
                 s_ns = 0;
                 s_nm = 0;
             }
             __syncthreads();
-            mark_step(a, C, stamp, gw, nwarps, &s_ns, &s_nm, a.tlist + s0, a.tlist + a.n + s0, edges);
-            __syncthreads();
-            split_step(a, wl, sh, s_defer, &s_ndefer, stamp, C, s_ns, a.tlist + s0, s_nm, a.tlist + a.n + s0, gw,
-                       nwarps, 0, 1, states);
+            if (K == 1) {
+                mark_step(a, C, stamp, gw, nwarps, &s_ns, &s_nm, a.tlist + s0, a.tlist + a.n + s0, edges);
+                __syncthreads();
+                split_step(a, wl, sh, s_defer, &s_ndefer, stamp, C, s_ns, a.tlist + s0, s_nm, a.tlist + a.n + s0,
+                           gw, nwarps, 0, 1, states);
+            } else {
+                claim_step(a, s_selC, s_selP, K, s_lost, stamp, gw, nwarps);
+                __syncthreads();
+                mark_many(a, wl, s_selC, s_selP, K, s_lost, stamp, gw, nwarps, &s_ns, &s_nm, a.tlist + s0,
+                          a.tlist + a.n + s0, edges, commits);
+                __syncthreads();
+                split_step(a, wl, sh, s_defer, &s_ndefer, stamp, MULTI, s_ns, a.tlist + s0, s_nm,
+                           a.tlist + a.n + s0, gw, nwarps, 0, 1, states);
+            }
             __syncthreads();
         }
-        if (threadIdx.x == 0) bt.inst_rounds[li] = r;
+        if (commits) atomicAdd(&s_commits, (unsigned long long)commits);
+        __syncthreads();
+        if (threadIdx.x == 0) bt.inst_rounds[li] = (long long)s_commits + 1;
+        steps += r;
         __syncthreads();
     }
     if (edges) atomicAdd((unsigned long long*)&a.ctrl->edges, (unsigned long long)edges);
     if (states) atomicAdd((unsigned long long*)&a.ctrl->states, (unsigned long long)states);
+    if (threadIdx.x == 0 && steps) atomicAdd((unsigned long long*)&a.ctrl->rounds, (unsigned long long)steps);
 }
 
 // ---------------------------------------------------------------- set-up
@@ -848,6 +1205,10 @@ int ensure_frontier(bisim_plan_s* p) {
     BISIM_TRY(p->kmark.alloc(4 * n, st));
     BISIM_TRY(p->tlist.alloc(8 * n, st));
     BISIM_TRY(p->queue.alloc(4 * n * BISIM_BUCKETS, st));
+    BISIM_TRY(p->claim.alloc(8 * n, st));
+    BISIM_TRY(p->bspl.alloc(4 * n, st));
+    BISIM_TRY(p->msel.alloc(4 * (3 * (size_t)BISIM_KMAX_GRID + 1), st));
+    BISIM_CUDA_TRY(cudaMemsetAsync(p->claim.p, 0xff, 8 * n, st));  // older than every round
     BISIM_CUDA_TRY(cudaMemsetAsync(p->smark.p, 0, 4 * n, st));
     BISIM_CUDA_TRY(cudaMemsetAsync(p->kmark.p, 0, 4 * n, st));
     p->frontier_ready = true;
@@ -863,6 +1224,7 @@ int frontier_setup(bisim_plan_s* p, bool fill_queue) {
     bisim_ctrl* c = p->ctrl.as<bisim_ctrl>();
     BISIM_CUDA_TRY(cudaMemsetAsync(c, 0, sizeof(bisim_ctrl), st));
     BISIM_CUDA_TRY(cudaMemsetAsync(p->mcnt.p, 0, 4 * (size_t)n, st));
+    BISIM_CUDA_TRY(cudaMemsetAsync(p->msel.p, 0, p->msel.bytes, st));
     DevMem keys, vals, keys2, flags;
     BISIM_TRY(keys.alloc(4 * (size_t)n, st));
     BISIM_TRY(vals.alloc(4 * (size_t)n, st));
@@ -915,6 +1277,8 @@ FrontierArgs make_args(bisim_plan_s* p, uint32_t base, int64_t cap) {
     a.kmark = p->kmark.as<uint32_t>();
     a.tlist = p->tlist.as<int32_t>();
     a.queue = p->queue.as<int32_t>();
+    a.claim = p->claim.as<unsigned long long>();
+    a.bspl = p->bspl.as<int32_t>();
     a.ctrl = c;
     a.gb.counter = &c->barrier;
     a.gb.status = &c->status;
@@ -947,18 +1311,39 @@ int refine_frontier(bisim_plan_s* p, bisim_stats* stats) {
     BISIM_TRY(frontier_setup(p, true));
     FrontierArgs a = make_args(p, base, cap);
     const int threads = p->opts.threads > 0 ? p->opts.threads : 512;
-    int light = p->opts.light_edges == 0 ? 256 : p->opts.light_edges;
-    void* args[] = {&a, &light};
+    const int light = p->opts.light_edges == 0 ? 256 : p->opts.light_edges;
     int grid = 0;
-    if (light < 0)  // every round on the whole grid
+    if (light < 0) {  // every round on the whole grid, one splitter per round
+        void* args[] = {&a};
         BISIM_TRY(launch_persistent((const void*)k_frontier_main, args, threads, p, &grid));
-    else
-        BISIM_TRY(launch_persistent((const void*)k_frontier_hybrid, args, threads, p, &grid));
+    } else {
+        HybridArgs h;
+        h.light_edges = light;
+        h.kmax = p->opts.splitters > 0 ? std::min(p->opts.splitters, BISIM_KMAX_GRID) : BISIM_KMAX_GRID;
+        h.kmax = std::min(h.kmax, SEL_E * threads);
+        h.local_budget = std::min(threads / 32, 32);
+        h.g_selC = p->msel.as<int32_t>();
+        h.g_selP = h.g_selC + BISIM_KMAX_GRID;
+        h.g_lost = reinterpret_cast<uint32_t*>(h.g_selP + BISIM_KMAX_GRID + 1);
+        h.budget = 0;  // set from the grid size below
+        void* args[] = {&a, &h};
+        int occ = 0;
+        BISIM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_frontier_hybrid, threads, 0));
+        // (an estimate for the budget only; launch_persistent sizes the grid)
+        int per_sm = p->opts.ctas_per_sm > 0 ? std::min(p->opts.ctas_per_sm, std::max(occ, 1)) : 1;
+        int g = p->sm_count * per_sm;
+        if (p->opts.max_ctas > 0) g = std::min(g, p->opts.max_ctas);
+        const int per_warp = p->opts.split_budget > 0 ? p->opts.split_budget : 1;
+        h.budget = (int)std::min<int64_t>((int64_t)per_warp * g * (threads / 32), 1 << 30);
+        BISIM_TRY(launch_persistent((const void*)k_frontier_hybrid, args, threads, p, &grid, 1,
+                                    sizeof(int32_t) * (2 * (size_t)h.kmax + 1)));
+    }
     BISIM_TRY(read_ctrl(p));
     p->stamp = base + (uint32_t)std::min<long long>(p->ctrl_h->rounds + 1, cap + 1);
     if (stats) {
         BISIM_TRY(persistent_ms(p, &stats->t_main_ms));
-        stats->rounds = p->ctrl_h->rounds;
+        stats->rounds = p->ctrl_h->commits + 1;
+        stats->steps = p->ctrl_h->rounds;
         stats->edges_visited = p->ctrl_h->edges;
         stats->states_visited = p->ctrl_h->states;
         stats->engine = BISIM_ENGINE_FRONTIER;
@@ -985,6 +1370,8 @@ int refine_frontier_batch(bisim_plan_s* p, bisim_stats* stats, std::vector<long 
     bt.next = &p->ctrl.as<bisim_ctrl>()->next_inst;
     bt.inst_rounds = p->inst_rounds.as<long long>();
     bt.block0 = p->block0.as<int32_t>();
+    bt.kmax = p->opts.splitters > 0 ? std::min(p->opts.splitters, BISIM_KMAX_CTA) : 1;
+    bt.budget_per_warp = p->opts.split_budget > 0 ? std::min(p->opts.split_budget, 1 << 20) : 8;
     const int threads = p->opts.threads > 0 ? p->opts.threads : 256;
     // optional split schedule: the LTSs with at least wide_min_states states
     // (a prefix of the largest-first order) run in a second launch of wide
@@ -1044,6 +1431,7 @@ int refine_frontier_batch(bisim_plan_s* p, bisim_stats* stats, std::vector<long 
     if (stats) {
         BISIM_TRY(persistent_ms(p, &stats->t_main_ms));
         stats->rounds = rsum;
+        stats->steps = p->ctrl_h->rounds;
         stats->edges_visited = p->ctrl_h->edges;
         stats->states_visited = p->ctrl_h->states;
         stats->engine = BISIM_ENGINE_FRONTIER;

@@ -16,6 +16,7 @@ WORKLOADS = {
     "kripke": lambda: lts_gen.kripke_uniform(seed=0),
     "qexp": lambda: lts_gen.quotient_expansion(seed=1),
     "chain": lambda: lts_gen.chain(seed=2, n=50000),
+    "powerlaw2m": lambda: lts_gen.powerlaw(seed=3, n=2_000_000),
 }
 
 
@@ -46,6 +47,24 @@ def shapes(workloads=("kripke", "qexp", "chain"), repeats: int = 3):
                                   "us_per_round": 1000 * best / max(st.rounds, 1)}), flush=True)
 
 
+def splitters(workloads=("qexp", "powerlaw2m"), repeats: int = 2):
+    """Main-loop time against the splitters-per-round cap and the per-warp
+    state budget of rounds with several splitters."""
+    for wl in workloads:
+        lts = WORKLOADS[wl]()
+        for threads in (512, 1024):
+            for kmax in (1, 64, 1024, 4096, 8192):
+                for budget in ((1,) if kmax == 1 else (1, 2, 4)):
+                    best, st = None, None
+                    for _ in range(repeats):
+                        _, st = bisim.reduce(lts, bisim.make_opts(engine=bisim.ENGINE_FRONTIER, threads=threads,
+                                                                  splitters=kmax, split_budget=budget),
+                                             return_stats=True)
+                        best = st.t_main_ms if best is None else min(best, st.t_main_ms)
+                    print(json.dumps({"workload": wl, "threads": threads, "splitters": kmax, "budget": budget,
+                                      "main_ms": best, "rounds": st.rounds, "steps": st.steps}), flush=True)
+
+
 def main(argv):
     import torch
 
@@ -56,6 +75,8 @@ def main(argv):
         barrier()
     elif what == "shapes":
         shapes(tuple(argv[2:]) or ("kripke", "qexp", "chain"))
+    elif what == "splitters":
+        splitters(tuple(argv[2:]) or ("qexp", "powerlaw2m"))
     else:
         raise SystemExit(f"unknown diagnostic {what}")
 

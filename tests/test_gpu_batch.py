@@ -116,3 +116,19 @@ def test_split_schedule_matches_single_launch():
             assert np.array_equal(a, b)
     for l, g in zip(ltss[:16], want[:16]):
         assert g.tolist() == oracle.ks_lts(l).tolist()
+
+
+@pytest.mark.parametrize("splitters", [1, 4, 0], ids=["one", "four", "default"])
+def test_batch_several_splitters_per_round(splitters):
+    """CTA rounds with several splitters: oracle partitions, identical to one
+    splitter per round, and the per-LTS iteration bounds hold."""
+    rng = np.random.default_rng(77)
+    ltss = [lts_gen.stream_instance(rng, n_lo=100, n_hi=8000, idx=i) for i in range(40)]
+    ltss += _random_batch(12, 60)
+    parts, st, inst = bisim.reduce_batch(ltss, bisim.make_opts(splitters=splitters), return_stats=True)
+    for i, (l, got) in enumerate(zip(ltss, parts)):
+        want = oracle.ks_lts(l)
+        assert got.tolist() == want.tolist(), i
+        B = int(want.max()) + 1 if l.n else 0
+        assert B + 1 <= inst[i].rounds <= 3 * l.n + l.num_act + 2
+    assert st.steps <= st.rounds

@@ -244,3 +244,33 @@ def test_preprocessing_rounds_and_direct_grouping_agree(engine):
         assert got1.tolist() == want and got2.tolist() == want, lts.name
         assert st1.initial_blocks == st2.initial_blocks
         assert st1.pre_rounds == st2.pre_rounds
+
+
+@pytest.mark.parametrize("splitters", [1, 2, 7, 0], ids=["one", "two", "seven", "default"])
+def test_several_splitters_per_round(splitters):
+    """Rounds that take several splitters at once (deferring those whose
+    touched blocks overlap) give the oracle's partition; the splitter
+    iterations still obey B + 1 <= rounds <= 3B - |pi_0'| + 1, and there are
+    never more barrier rounds than splitter iterations."""
+    cases = [lts_gen.random_small(500 + s, 50, 1 + s % 4, 160, blocks=1 + s % 3) for s in range(30)]
+    cases += [lts_gen.kripke_uniform(), lts_gen.chain(n=3000), lts_gen.fan_out(150),
+              lts_gen.quotient_expansion(seed=6, classes=500, trans=5000, copies_hi=40),
+              lts_gen.powerlaw(seed=3, n=20000)]
+    for lts in cases:
+        got, st = run(lts, bisim.ENGINE_FRONTIER, splitters=splitters)
+        want = oracle.ks_lts(lts)
+        assert got.tolist() == want.tolist(), lts.name
+        B = defs.num_blocks(want)
+        assert B + 1 <= st.rounds <= 3 * B - st.initial_blocks + 1, lts.name
+        assert st.steps <= st.rounds
+        if splitters == 1:
+            assert st.steps == st.rounds
+
+
+def test_several_splitters_large_worklist():
+    """A power-law LTS whose refinement keeps thousands of small blocks
+    unstable at once: rounds with up to 1024 splitters on the whole grid."""
+    lts = lts_gen.powerlaw(seed=3, n=200000)
+    got, st = run(lts, bisim.ENGINE_FRONTIER)
+    assert got.tolist() == oracle.ks_lts(lts).tolist()
+    assert st.steps * 4 < st.rounds  # many splitters per barrier round
