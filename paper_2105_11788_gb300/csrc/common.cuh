@@ -74,6 +74,7 @@ inline unsigned grid_for(int64_t work, int threads, unsigned cap = 152u * 32u) {
 __device__ __forceinline__ int ldcg(const int* p) { return __ldcg(p); }
 __device__ __forceinline__ unsigned ldcg(const unsigned* p) { return __ldcg(p); }
 __device__ __forceinline__ unsigned long long ldcg(const unsigned long long* p) { return __ldcg(p); }
+__device__ __forceinline__ int4 ldcg(const int4* p) { return __ldcg(p); }
 __device__ __forceinline__ unsigned char ldcg(const unsigned char* p) {
     return (unsigned char)__ldcg((const char*)p);
 }

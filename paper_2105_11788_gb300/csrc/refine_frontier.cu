@@ -50,7 +50,7 @@ struct FrontierArgs {
     int32_t* yscr;    // [n] by position: scratch for the swap pairing
     uint32_t* smark;  // [n] per state: stamp of the round that last marked it
     uint32_t* kmark;  // [n] per state: stamp of the round it was in a kept part
-    int32_t* tlist;   // [2n]: warp list, CTA list
+    int4* tlist;      // [2n]: warp list, CTA list of touched blocks (label, range begin, range end, 0)
     int32_t* queue;   // [n]
     unsigned long long* claim;  // [n] per label: (~stamp << 32) | index of the claiming splitter
     int32_t* bspl;    // [n] per touched label: its splitter (multi-splitter rounds)
@@ -76,72 +76,93 @@ struct Worklist {
     int32_t cap;
 };
 
-// append a label to the FIFO ring of its size bucket
-__device__ __forceinline__ void push(const FrontierArgs& a, const Worklist& wl, int32_t label) {
-    const int bk = size_bucket(ldcg(&a.bend[label]) - ldcg(&a.bbeg[label]));
+// append a label whose block has `size` states to the FIFO ring of its size bucket
+__device__ __forceinline__ void push_sized(const Worklist& wl, int32_t label, int32_t size) {
+    const int bk = size_bucket(size);
     const unsigned long long pos = atomicAdd(&wl.tail[bk], 1ull);
     wl.queue[(size_t)bk * wl.stride + wl.base + pos % (unsigned long long)wl.cap] = label;
 }
 
-// unstable_label := true; enqueue it if it was stable
-__device__ __forceinline__ void set_unstable(const FrontierArgs& a, const Worklist& wl, int32_t label) {
-    if (atomicExch(&a.unstable[label], 1u) == 0u) push(a, wl, label);
+__device__ __forceinline__ void push(const FrontierArgs& a, const Worklist& wl, int32_t label) {
+    push_sized(wl, label, ldcg(&a.bend[label]) - ldcg(&a.bbeg[label]));
+}
+
+// unstable_label := true; enqueue it if it was stable (size < 0: look it up)
+__device__ __forceinline__ void set_unstable(const FrontierArgs& a, const Worklist& wl, int32_t label,
+                                             int32_t size = -1) {
+    if (atomicExch(&a.unstable[label], 1u) == 0u) {
+        if (size < 0) size = ldcg(&a.bend[label]) - ldcg(&a.bbeg[label]);
+        push_sized(wl, label, size);
+    }
 }
 
 // finish_split by a whole warp: the (up to) three labels are pushed by three
-// lanes at once. The caller's stores of the new ranges precede a __syncwarp.
+// lanes at once; the kept part b has szb states and the split part szl. The
+// caller's stores of the new ranges precede a __syncwarp.
 __device__ __forceinline__ void finish_split_warp(const FrontierArgs& a, const Worklist& wl, int32_t b,
-                                                  int32_t leader, int32_t C) {
+                                                  int32_t szb, int32_t leader, int32_t szl, int32_t C) {
     const unsigned lane = threadIdx.x & 31u;
     int32_t lab = lane == 0 ? b : lane == 1 ? leader : (lane == 2 && !a.alg2) ? C : -1;
     if (lab == MULTI) lab = ldcg(&a.bspl[b]);  // the splitter that touched b this round
-    if (lab >= 0) set_unstable(a, wl, lab);
+    if (lab >= 0) set_unstable(a, wl, lab, lane == 0 ? szb : lane == 1 ? szl : -1);
 }
 
-// Does s have the same marks as the leader (lo = off[leader], k slots)?
-__device__ __forceinline__ bool same_marks(const FrontierArgs& a, int32_t s, int32_t lo, int32_t k,
-                                           unsigned lmask, uint32_t stamp) {
-    const int32_t os = a.off[s];
-    int32_t ks = a.off[s + 1] - os;
+// Does a member with mark slots [os, os + ks) have the same marks as the
+// leader (slots [lo, lo + k); for k <= 32 their marks are the bits of
+// lmask)? Loads go out eight at a time.
+__device__ __forceinline__ bool same_marks_at(const FrontierArgs& a, int32_t os, int32_t ks, int32_t lo, int32_t k,
+                                              unsigned lmask, uint32_t stamp) {
     if (ks != k) {  // members must share the leader's label set (preprocessing invariant)
         atomicOr(&a.ctrl->status, ST_INTERNAL);
         ks = min(ks, k);
     }
     bool diff = false;
-    if (k <= 32) {
-        for (int32_t q = 0; q < ks; q++)
-            diff |= (ldcg(&a.mark[os + q]) == stamp) != (bool)((lmask >> q) & 1u);
-    } else {
-        for (int32_t q = 0; q < ks; q++)
-            diff |= (ldcg(&a.mark[os + q]) == stamp) != (ldcg(&a.mark[lo + q]) == stamp);
+    for (int32_t q0 = 0; q0 < ks; q0 += 8) {
+        uint32_t v[8], w[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            v[u] = q0 + u < ks ? ldcg(&a.mark[os + q0 + u]) : 0u;
+            w[u] = k > 32 && q0 + u < ks ? ldcg(&a.mark[lo + q0 + u]) : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; u++)
+            if (q0 + u < ks)
+                diff |= (v[u] == stamp) != (k <= 32 ? (bool)((lmask >> (q0 + u)) & 1u) : w[u] == stamp);
     }
     return !diff;
 }
 
-// One warp splits block b (at most 64 members) from the members themselves.
-__device__ void warp_split(const FrontierArgs& a, const Worklist& wl, int32_t b, uint32_t stamp, int32_t C,
-                           long long& states) {
+__device__ __forceinline__ bool same_marks(const FrontierArgs& a, int32_t s, int32_t lo, int32_t k,
+                                           unsigned lmask, uint32_t stamp) {
+    const int32_t os = a.off[s];
+    return same_marks_at(a, os, a.off[s + 1] - os, lo, k, lmask, stamp);
+}
+
+// One warp splits block b (range [b0, e0), at most 64 members) from the
+// members themselves. The loads are grouped by what they depend on: b and
+// its range; then the members; then the members' marks.
+__device__ void warp_split(const FrontierArgs& a, const Worklist& wl, int32_t b, int32_t b0, int32_t e0,
+                           uint32_t stamp, int32_t C, long long& states) {
     const unsigned lane = threadIdx.x & 31u;
     const unsigned lt = lanemask_lt();
-    const int32_t b0 = ldcg(&a.bbeg[b]), e0 = ldcg(&a.bend[b]);
     const int32_t sz = e0 - b0;
-    if (lane == 0) a.mcnt[b] = 0;
     const int32_t lo = a.off[b];
     const int32_t k = a.off[b + 1] - lo;
     const bool lead_marked = ldcg(&a.smark[b]) == stamp;
-    unsigned lmask = 0;
-    if (lead_marked && k <= 32)
-        lmask = __ballot_sync(0xffffffffu, (int)lane < k && ldcg(&a.mark[lo + lane]) == stamp);
     const int32_t s0 = (int)lane < sz ? ldcg(&a.elems[b0 + lane]) : -1;
     const int32_t s1 = (int)lane + 32 < sz ? ldcg(&a.elems[b0 + 32 + lane]) : -1;
-    bool p0 = false, p1 = false;  // splits off
-    if (s0 >= 0) {
-        const bool mk = ldcg(&a.smark[s0]) == stamp;
-        p0 = lead_marked ? !(mk && same_marks(a, s0, lo, k, lmask, stamp)) : mk;
-    }
-    if (s1 >= 0) {
-        const bool mk = ldcg(&a.smark[s1]) == stamp;
-        p1 = lead_marked ? !(mk && same_marks(a, s1, lo, k, lmask, stamp)) : mk;
+    if (lane == 0) a.mcnt[b] = 0;
+    const bool mk0 = s0 >= 0 && ldcg(&a.smark[s0]) == stamp;
+    const bool mk1 = s1 >= 0 && ldcg(&a.smark[s1]) == stamp;
+    bool p0 = mk0, p1 = mk1;  // splits off (leader unmarked: exactly the marked members)
+    if (lead_marked) {
+        // slot ranges of the members, issued with the leader's marks
+        const int32_t o0 = s0 >= 0 ? a.off[s0] : 0, q0 = s0 >= 0 ? a.off[s0 + 1] : 0;
+        const int32_t o1 = s1 >= 0 ? a.off[s1] : 0, q1 = s1 >= 0 ? a.off[s1 + 1] : 0;
+        unsigned lmask = 0;
+        if (k <= 32) lmask = __ballot_sync(0xffffffffu, (int)lane < k && ldcg(&a.mark[lo + lane]) == stamp);
+        p0 = s0 >= 0 && !(mk0 && same_marks_at(a, o0, q0 - o0, lo, k, lmask, stamp));
+        p1 = s1 >= 0 && !(mk1 && same_marks_at(a, o1, q1 - o1, lo, k, lmask, stamp));
     }
     const unsigned m0 = __ballot_sync(0xffffffffu, p0), m1 = __ballot_sync(0xffffffffu, p1);
     if (lane == 0) states += sz;
@@ -168,7 +189,7 @@ __device__ void warp_split(const FrontierArgs& a, const Worklist& wl, int32_t b,
         a.bend[leader] = e0;
     }
     __syncwarp();
-    finish_split_warp(a, wl, b, leader, C);
+    finish_split_warp(a, wl, b, nkeep, leader, sz - nkeep, C);
 }
 
 struct CtaShared {
@@ -180,6 +201,7 @@ struct CtaShared {
     int C;
     int bx[BISIM_BUCKETS];  // select_many: entries before each bucket
     int bn[BISIM_BUCKETS];  // select_many: entries taken from each bucket at most
+    int hp[BISIM_BUCKETS];  // select_many: ring position of each bucket's head
     unsigned long long head[BISIM_BUCKETS];  // this CTA's copy of the worklist heads
 };
 
@@ -334,7 +356,7 @@ __device__ void cta_split(const FrontierArgs& a, const Worklist& wl, CtaShared& 
                 a.bend[leader] = e0;
             }
             __syncwarp();
-            finish_split_warp(a, wl, b, leader, C);
+            finish_split_warp(a, wl, b, t0 - b0, leader, e0 - t0, C);
         }
         __syncthreads();
         return;
@@ -379,7 +401,7 @@ __device__ void cta_split(const FrontierArgs& a, const Worklist& wl, CtaShared& 
             a.bend[leader] = e0;
         }
         __syncwarp();
-        finish_split_warp(a, wl, b, leader, C);
+        finish_split_warp(a, wl, b, kk, leader, e0 - b0 - kk, C);
     }
     __syncthreads();
 }
@@ -421,10 +443,9 @@ __device__ __forceinline__ void warp_gather(const FrontierArgs& a, int32_t s, in
 
 // One warp splits block b (more than WARP_MAX members) that has at most 32
 // marked members this round.
-__device__ void warp_split_sparse(const FrontierArgs& a, const Worklist& wl, int32_t b, int32_t km,
-                                  uint32_t stamp, int32_t C, long long& states) {
+__device__ void warp_split_sparse(const FrontierArgs& a, const Worklist& wl, int32_t b, int32_t b0, int32_t e0,
+                                  int32_t km, uint32_t stamp, int32_t C, long long& states) {
     const unsigned lane = threadIdx.x & 31u;
-    const int32_t b0 = ldcg(&a.bbeg[b]), e0 = ldcg(&a.bend[b]);
     const int32_t t0 = e0 - km;  // marked members listed in mscr[t0 .. e0)
     const int32_t lo = a.off[b];
     const int32_t k = a.off[b + 1] - lo;
@@ -444,7 +465,7 @@ __device__ void warp_split_sparse(const FrontierArgs& a, const Worklist& wl, int
             a.bend[leader] = e0;
         }
         __syncwarp();
-        finish_split_warp(a, wl, b, leader, C);
+        finish_split_warp(a, wl, b, t0 - b0, leader, e0 - t0, C);
         return;
     }
     // leader marked: kept part = marked members with the leader's marks
@@ -477,7 +498,7 @@ __device__ void warp_split_sparse(const FrontierArgs& a, const Worklist& wl, int
         a.bend[leader] = e0;
     }
     __syncwarp();
-    finish_split_warp(a, wl, b, leader, C);
+    finish_split_warp(a, wl, b, kk, leader, e0 - b0 - kk, C);
 }
 
 // Split step of a round for the touched blocks listed by the mark step:
@@ -486,12 +507,15 @@ __device__ void warp_split_sparse(const FrontierArgs& a, const Worklist& wl, int
 // `ncta` takes its share; `defer` is a CTA-local list of at least
 // blockDim/32 entries.
 __device__ void split_step(const FrontierArgs& a, const Worklist& wl, CtaShared& sh, int* defer, int* ndefer,
-                           uint32_t stamp, int32_t C, int ns, const int32_t* small_list, int nm,
-                           const int32_t* mid_list, int64_t gw, int64_t nwarps, int cta, int ncta,
+                           uint32_t stamp, int32_t C, int ns, const int4* small_list, int nm,
+                           const int4* mid_list, int64_t gw, int64_t nwarps, int cta, int ncta,
                            long long& states) {
     const int wid = (int)(threadIdx.x >> 5);
     const int nw = (int)(blockDim.x >> 5);
-    for (int64_t i = gw; i < ns; i += nwarps) warp_split(a, wl, ldcg(&small_list[i]), stamp, C, states);
+    for (int64_t i = gw; i < ns; i += nwarps) {
+        const int4 t = ldcg(&small_list[i]);
+        warp_split(a, wl, t.x, t.y, t.z, stamp, C, states);
+    }
     // entry i goes to CTA i % ncta, so the first ncta entries land on
     // different CTAs; inside a CTA its entries go to different warps
     for (int base = 0; base < nm; base += ncta * nw) {
@@ -499,10 +523,11 @@ __device__ void split_step(const FrontierArgs& a, const Worklist& wl, CtaShared&
         __syncthreads();
         const int i = base + wid * ncta + cta;
         if (i < nm) {
-            const int32_t b = ldcg(&mid_list[i]);
+            const int4 t = ldcg(&mid_list[i]);
+            const int32_t b = t.x;
             const int32_t km = ldcg(&a.mcnt[b]);
             if (km <= 32) {
-                warp_split_sparse(a, wl, b, km, stamp, C, states);
+                warp_split_sparse(a, wl, b, t.y, t.z, km, stamp, C, states);
             } else if ((threadIdx.x & 31) == 0) {
                 defer[atomicAdd(ndefer, 1)] = b;
             }
@@ -522,8 +547,26 @@ __device__ void split_step(const FrontierArgs& a, const Worklist& wl, CtaShared&
 // Marks of one member t of a splitter, by one warp (lanes over t's incoming
 // transitions). Cw >= 0 is recorded as the splitter of each newly touched
 // block (rounds with several splitters).
+// The part of a mark step after the first mark of a source s in its block b
+// (range [bb, be)): rank s among the block's marked members and list b when
+// it is the first. Blocks of one state cannot split and are skipped.
+__device__ __forceinline__ void rank_marked(const FrontierArgs& a, int32_t s, int32_t b, int32_t bb, int32_t be,
+                                            int32_t Cw, int* n_small, int* n_mid, int4* small_list,
+                                            int4* mid_list) {
+    if (be - bb <= 1) return;
+    const int32_t rk = atomicAdd(&a.mcnt[b], 1);
+    a.mscr[be - 1 - rk] = s;
+    if (rk == 0) {
+        if (Cw >= 0) a.bspl[b] = Cw;
+        if (be - bb <= WARP_MAX)
+            small_list[atomicAdd(n_small, 1)] = make_int4(b, bb, be, 0);
+        else
+            mid_list[atomicAdd(n_mid, 1)] = make_int4(b, bb, be, 0);
+    }
+}
+
 __device__ __forceinline__ void mark_member(const FrontierArgs& a, int32_t t, uint32_t stamp, int32_t Cw,
-                                            int* n_small, int* n_mid, int32_t* small_list, int32_t* mid_list,
+                                            int* n_small, int* n_mid, int4* small_list, int4* mid_list,
                                             long long& edges) {
     const int lane = threadIdx.x & 31;
     const int32_t j0 = a.in_ptr[t], j1 = a.in_ptr[t + 1];
@@ -534,23 +577,13 @@ __device__ __forceinline__ void mark_member(const FrontierArgs& a, int32_t t, ui
         a.mark[(uint32_t)e] = stamp;
         const int32_t b = ldcg(&a.block[s]);  // issued before the atomic: both depend on s only
         if (atomicExch(&a.smark[s], stamp) == stamp) continue;
-        const int32_t bb = ldcg(&a.bbeg[b]), be = ldcg(&a.bend[b]);
-        if (be - bb <= 1) continue;
-        const int32_t rk = atomicAdd(&a.mcnt[b], 1);
-        a.mscr[be - 1 - rk] = s;
-        if (rk == 0) {
-            if (Cw >= 0) a.bspl[b] = Cw;
-            if (be - bb <= WARP_MAX)
-                small_list[atomicAdd(n_small, 1)] = b;
-            else
-                mid_list[atomicAdd(n_mid, 1)] = b;
-        }
+        rank_marked(a, s, b, ldcg(&a.bbeg[b]), ldcg(&a.bend[b]), Cw, n_small, n_mid, small_list, mid_list);
     }
 }
 
 __device__ __forceinline__ void mark_step(const FrontierArgs& a, int32_t C, uint32_t stamp, int64_t gw,
-                                          int64_t nwarps, int* n_small, int* n_mid, int32_t* small_list,
-                                          int32_t* mid_list, long long& edges) {
+                                          int64_t nwarps, int* n_small, int* n_mid, int4* small_list,
+                                          int4* mid_list, long long& edges) {
     const int32_t b0 = ldcg(&a.bbeg[C]), e0 = ldcg(&a.bend[C]);
     for (int64_t idx = b0 + gw; idx < e0; idx += nwarps)
         mark_member(a, ldcg(&a.elems[idx]), stamp, -1, n_small, n_mid, small_list, mid_list, edges);
@@ -582,8 +615,10 @@ constexpr int SEL_E = 8;
 // at most SEL_E per thread of the CTA) while their blocks hold at most
 // `budget` states together; the first is always taken. selC[0..K) gets the
 // labels, selP[0..K] the exclusive prefix of their block sizes. Returns K to
-// every thread (0: the worklist is empty). Thread t handles the entries
-// [t*E, t*E + E), so its queue and size loads are issued together.
+// every thread (0: the worklist is empty). The labels are read with
+// consecutive threads on consecutive ring entries; the sizes of bucket-0
+// entries are known without a load (blocks only shrink and are never empty,
+// so a label pushed with one state still has one).
 __device__ int select_many(const FrontierArgs& a, const Worklist& wl, unsigned long long* head, CtaShared& sh,
                            int32_t* selC, int32_t* selP, int kmax, int32_t budget) {
     const unsigned lane = threadIdx.x & 31u;
@@ -600,29 +635,47 @@ __device__ int select_many(const FrontierArgs& a, const Worklist& wl, unsigned l
         }
         sh.bx[lane] = x - av;
         sh.bn[lane] = av;
+        sh.hp[lane] = (int)(h % (unsigned long long)wl.cap);
         if (lane == 31) sh.total = min(x, kmax);
     }
     __syncthreads();
     const int k0 = sh.total;
+    {
+        // all of this thread's ring loads are issued before the first store
+        int32_t lv[SEL_E];
+        int bk = 0;
+#pragma unroll
+        for (int e = 0; e < SEL_E; e++) {
+            const int j = e * (int)blockDim.x + (int)threadIdx.x;
+            lv[e] = -1;
+            if (j < k0) {
+                while (j >= sh.bx[bk] + sh.bn[bk]) bk++;
+                int pos = sh.hp[bk] + (j - sh.bx[bk]);  // < 2 cap: the bucket holds at most cap entries
+                if (pos >= wl.cap) pos -= wl.cap;
+                lv[e] = ldcg(&wl.queue[(size_t)bk * wl.stride + wl.base + pos]);
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < SEL_E; e++) {
+            const int j = e * (int)blockDim.x + (int)threadIdx.x;
+            if (j < k0) selC[j] = lv[e];
+        }
+    }
+    __syncthreads();
+    const int n0 = sh.bn[0];  // entries [0, n0) come from bucket 0
     const int E = (k0 + (int)blockDim.x - 1) / (int)blockDim.x;
     const int j0 = (int)threadIdx.x * E;
     int32_t cs[SEL_E];
     int sz[SEL_E];
-    int bk = 0;
 #pragma unroll
     for (int e = 0; e < SEL_E; e++) {
         const int j = j0 + e;
-        cs[e] = -1;
-        if (e < E && j < k0) {
-            while (j >= sh.bx[bk] + sh.bn[bk]) bk++;
-            const unsigned long long q = head[bk] + (unsigned long long)(j - sh.bx[bk]);
-            cs[e] = ldcg(&wl.queue[(size_t)bk * wl.stride + wl.base + q % (unsigned long long)wl.cap]);
-        }
+        cs[e] = e < E && j < k0 ? selC[j] : -1;
     }
     int mine = 0;
 #pragma unroll
     for (int e = 0; e < SEL_E; e++) {
-        sz[e] = cs[e] >= 0 ? ldcg(&a.bend[cs[e]]) - ldcg(&a.bbeg[cs[e]]) : 0;
+        sz[e] = cs[e] < 0 ? 0 : j0 + e < n0 ? 1 : ldcg(&a.bend[cs[e]]) - ldcg(&a.bbeg[cs[e]]);
         mine += sz[e];
     }
     int tot;
@@ -633,7 +686,6 @@ __device__ int select_many(const FrontierArgs& a, const Worklist& wl, unsigned l
     for (int e = 0; e < SEL_E; e++) {
         const int j = j0 + e;
         if (cs[e] >= 0 && (j == 0 || ex + sz[e] <= budget)) {
-            selC[j] = cs[e];
             selP[j] = ex;
             selP[j + 1] = ex + sz[e];  // the next entry's prefix (same value if it is taken)
             taken++;
@@ -700,7 +752,7 @@ __device__ void claim_step(const FrontierArgs& a, const int32_t* selC, const int
 // clears its unstable flag (Algorithm 3, line 23) and marks as mark_step.
 __device__ void mark_many(const FrontierArgs& a, const Worklist& wl, const int32_t* selC, const int32_t* selP,
                           int K, const uint32_t* lost, uint32_t stamp, int64_t gw, int64_t nwarps, int* n_small,
-                          int* n_mid, int32_t* small_list, int32_t* mid_list, long long& edges,
+                          int* n_mid, int4* small_list, int4* mid_list, long long& edges,
                           long long& commits) {
     const int lane = threadIdx.x & 31;
     const int32_t tot = selP[K];
@@ -803,6 +855,84 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64_g(const unsigned lo
 // grid with two grid barriers, exactly as k_frontier_main. The other CTAs
 // wait for commands; their wait is bounded by timeout_ns without progress,
 // where progress is a new command or a new heartbeat from CTA 0.
+// One item per warp (a round's splitters hold at most as many states as
+// there are warps): the claim pass keeps what it loaded in registers for the
+// mark pass - the member t, its incoming-transition range and, one per
+// lane, the first 32 transitions with their source's block and its range
+// (nothing changes them between the two passes).
+struct ItemCarry {
+    int32_t j;  // splitter index, -1: this warp has no item
+    int32_t C;
+    int32_t j0, j1;
+    unsigned long long e;  // this lane's transition j0 + lane, when < j1
+    int32_t b, bb, be;     // its source's block and block range
+};
+
+__device__ __forceinline__ void claim_item(const FrontierArgs& a, const int32_t* selC, const int32_t* selP, int K,
+                                           uint32_t* lost, uint32_t stamp, int64_t i, ItemCarry& ic) {
+    const int lane = threadIdx.x & 31;
+    ic.j = -1;
+    if (i >= selP[K]) return;
+    const int j = find_sel(selP, K, (int32_t)i);
+    const int32_t C = selC[j];
+    ic.j = j;
+    ic.C = C;
+    const unsigned long long key = ((unsigned long long)(~stamp) << 32) | (unsigned)j;
+    const int32_t cb = ldcg(&a.bbeg[C]);
+    if (i == selP[j] && lane == 0 && ldcg(&a.bend[C]) - cb > 1) claim_label(a, C, key, lost, stamp);
+    const int32_t t = ldcg(&a.elems[cb + (int32_t)i - selP[j]]);
+    ic.j0 = a.in_ptr[t];
+    ic.j1 = a.in_ptr[t + 1];
+    const bool has = ic.j0 + lane < ic.j1;
+    if (has) {
+        ic.e = a.in_edge[ic.j0 + lane];
+        ic.b = ldcg(&a.block[(int32_t)(ic.e >> 32)]);
+        ic.bb = ldcg(&a.bbeg[ic.b]);
+        ic.be = ldcg(&a.bend[ic.b]);
+    }
+    // one claim per distinct block of the warp (sources often share a block)
+    const bool cl = has && ic.be - ic.bb > 1;
+    const unsigned peers = __match_any_sync(0xffffffffu, cl ? ic.b : -1 - lane);  // every lane gets here
+    if (cl && (peers & lanemask_lt()) == 0u) claim_label(a, ic.b, key, lost, stamp);
+    for (int32_t q = ic.j0 + 32 + lane; q < ic.j1; q += 32) {
+        const int32_t b = ldcg(&a.block[(int32_t)(a.in_edge[q] >> 32)]);
+        if (ldcg(&a.bend[b]) - ldcg(&a.bbeg[b]) > 1) claim_label(a, b, key, lost, stamp);
+    }
+}
+
+__device__ __forceinline__ void mark_item(const FrontierArgs& a, const Worklist& wl, const int32_t* selP,
+                                          const uint32_t* lost, uint32_t stamp, int64_t i, const ItemCarry& ic,
+                                          int* n_small, int* n_mid, int4* small_list, int4* mid_list,
+                                          long long& edges, long long& commits) {
+    const int lane = threadIdx.x & 31;
+    if (ic.j < 0) return;
+    const bool lose = ld_volatile_u32(&lost[ic.j]) == stamp;
+    if (i == selP[ic.j] && lane == 0) {
+        if (lose) {
+            push(a, wl, ic.C);
+        } else {
+            a.unstable[ic.C] = 0u;
+            commits++;
+        }
+    }
+    if (lose) return;
+    if (lane == 0) edges += ic.j1 - ic.j0;
+    if (ic.j0 + lane < ic.j1) {
+        const int32_t s = (int32_t)(ic.e >> 32);
+        a.mark[(uint32_t)ic.e] = stamp;
+        if (atomicExch(&a.smark[s], stamp) != stamp)
+            rank_marked(a, s, ic.b, ic.bb, ic.be, ic.C, n_small, n_mid, small_list, mid_list);
+    }
+    for (int32_t q = ic.j0 + 32 + lane; q < ic.j1; q += 32) {
+        const unsigned long long e = a.in_edge[q];
+        const int32_t s = (int32_t)(e >> 32);
+        a.mark[(uint32_t)e] = stamp;
+        const int32_t b = ldcg(&a.block[s]);
+        if (atomicExch(&a.smark[s], stamp) == stamp) continue;
+        rank_marked(a, s, b, ldcg(&a.bbeg[b]), ldcg(&a.bend[b]), ic.C, n_small, n_mid, small_list, mid_list);
+    }
+}
+
 struct HybridArgs {
     int light_edges;   // a one-splitter round with at most 32 members and this many
                        // incoming transitions runs on CTA 0 alone
@@ -822,11 +952,19 @@ template <typename Sync>
 __device__ __forceinline__ bool multi_round(const FrontierArgs& a, const Worklist& wl, CtaShared& sh, int* defer,
                                             int* ndefer, const int32_t* selC, const int32_t* selP, int K,
                                             uint32_t* lost, uint32_t stamp, int64_t gw, int64_t nwarps, int* n_small,
-                                            int* n_mid, int32_t* small_list, int32_t* mid_list, int cta, int ncta,
+                                            int* n_mid, int4* small_list, int4* mid_list, int cta, int ncta,
                                             long long& edges, long long& states, long long& commits, Sync sync) {
-    claim_step(a, selC, selP, K, lost, stamp, gw, nwarps);
-    if (!sync()) return false;
-    mark_many(a, wl, selC, selP, K, lost, stamp, gw, nwarps, n_small, n_mid, small_list, mid_list, edges, commits);
+    if (selP[K] <= nwarps) {
+        ItemCarry ic;
+        claim_item(a, selC, selP, K, lost, stamp, gw, ic);
+        if (!sync()) return false;
+        mark_item(a, wl, selP, lost, stamp, gw, ic, n_small, n_mid, small_list, mid_list, edges, commits);
+    } else {
+        claim_step(a, selC, selP, K, lost, stamp, gw, nwarps);
+        if (!sync()) return false;
+        mark_many(a, wl, selC, selP, K, lost, stamp, gw, nwarps, n_small, n_mid, small_list, mid_list, edges,
+                  commits);
+    }
     if (!sync()) return false;
     split_step(a, wl, sh, defer, ndefer, stamp, MULTI, ld_volatile_i32(n_small), small_list, ld_volatile_i32(n_mid), mid_list, gw,
                nwarps, cta, ncta, states);
@@ -842,7 +980,8 @@ __device__ __forceinline__ bool multi_round(const FrontierArgs& a, const Worklis
 // with grid barriers, as in k_frontier_main. The other CTAs wait for
 // commands; their wait is bounded by timeout_ns without progress, where
 // progress is a new command or a new heartbeat from CTA 0.
-__global__ void __launch_bounds__(1024) k_frontier_hybrid(FrontierArgs a, HybridArgs h) {
+template <int MAXT>  // most threads per CTA (sets the register budget)
+__global__ void __launch_bounds__(MAXT, 1) k_frontier_hybrid(FrontierArgs a, HybridArgs h) {
     __shared__ CtaShared sh;
     __shared__ int s_defer[32];
     __shared__ int s_ndefer;
@@ -1016,9 +1155,19 @@ __global__ void __launch_bounds__(1024) k_frontier_hybrid(FrontierArgs a, Hybrid
             __syncthreads();
             if (C == -1) break;
             if (C == MULTI) {
-                for (int i = threadIdx.x; i <= K; i += blockDim.x) {
-                    if (i < K) s_selC[i] = ldcg(&h.g_selC[i]);
-                    s_selP[i] = ldcg(&h.g_selP[i]);
+                // K <= SEL_E * blockDim: every load is issued before the first store
+                int32_t vc[SEL_E], vp[SEL_E + 1];
+#pragma unroll
+                for (int e = 0; e <= SEL_E; e++) {
+                    const int i = e * (int)blockDim.x + (int)threadIdx.x;
+                    if (e < SEL_E) vc[e] = i < K ? ldcg(&h.g_selC[i]) : 0;
+                    vp[e] = i <= K ? ldcg(&h.g_selP[i]) : 0;
+                }
+#pragma unroll
+                for (int e = 0; e <= SEL_E; e++) {
+                    const int i = e * (int)blockDim.x + (int)threadIdx.x;
+                    if (e < SEL_E && i < K) s_selC[i] = vc[e];
+                    if (i <= K) s_selP[i] = vp[e];
                 }
                 __syncthreads();
                 if (!multi_round(a, wl, sh, s_defer, &s_ndefer, s_selC, s_selP, K, h.g_lost, stamp, gw, nwarps,
@@ -1203,7 +1352,7 @@ int ensure_frontier(bisim_plan_s* p) {
     BISIM_TRY(p->yscr.alloc(4 * n, st));
     BISIM_TRY(p->smark.alloc(4 * n, st));
     BISIM_TRY(p->kmark.alloc(4 * n, st));
-    BISIM_TRY(p->tlist.alloc(8 * n, st));
+    BISIM_TRY(p->tlist.alloc(32 * n, st));
     BISIM_TRY(p->queue.alloc(4 * n * BISIM_BUCKETS, st));
     BISIM_TRY(p->claim.alloc(8 * n, st));
     BISIM_TRY(p->bspl.alloc(4 * n, st));
@@ -1275,7 +1424,7 @@ FrontierArgs make_args(bisim_plan_s* p, uint32_t base, int64_t cap) {
     a.yscr = p->yscr.as<int32_t>();
     a.smark = p->smark.as<uint32_t>();
     a.kmark = p->kmark.as<uint32_t>();
-    a.tlist = p->tlist.as<int32_t>();
+    a.tlist = p->tlist.as<int4>();
     a.queue = p->queue.as<int32_t>();
     a.claim = p->claim.as<unsigned long long>();
     a.bspl = p->bspl.as<int32_t>();
@@ -1327,15 +1476,16 @@ int refine_frontier(bisim_plan_s* p, bisim_stats* stats) {
         h.g_lost = reinterpret_cast<uint32_t*>(h.g_selP + BISIM_KMAX_GRID + 1);
         h.budget = 0;  // set from the grid size below
         void* args[] = {&a, &h};
+        const void* fn = threads <= 512 ? (const void*)k_frontier_hybrid<512> : (const void*)k_frontier_hybrid<1024>;
         int occ = 0;
-        BISIM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_frontier_hybrid, threads, 0));
+        BISIM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, 0));
         // (an estimate for the budget only; launch_persistent sizes the grid)
         int per_sm = p->opts.ctas_per_sm > 0 ? std::min(p->opts.ctas_per_sm, std::max(occ, 1)) : 1;
         int g = p->sm_count * per_sm;
         if (p->opts.max_ctas > 0) g = std::min(g, p->opts.max_ctas);
         const int per_warp = p->opts.split_budget > 0 ? p->opts.split_budget : 1;
         h.budget = (int)std::min<int64_t>((int64_t)per_warp * g * (threads / 32), 1 << 30);
-        BISIM_TRY(launch_persistent((const void*)k_frontier_hybrid, args, threads, p, &grid, 1,
+        BISIM_TRY(launch_persistent(fn, args, threads, p, &grid, 1,
                                     sizeof(int32_t) * (2 * (size_t)h.kmax + 1)));
     }
     BISIM_TRY(read_ctrl(p));
