@@ -32,6 +32,7 @@ struct bisim_ctrl {
     int cmd_K;                       // number of splitters of a published multi-splitter round
     int pad3;
     long long commits;               // splitter iterations carried out (multi-splitter schedules)
+    unsigned long long cmd_heads[32];  // worklist heads after the published round's selection
 };
 
 // Most splitters one multi-splitter round takes: grid rounds of the hybrid

@@ -971,21 +971,27 @@ __device__ __forceinline__ bool multi_round(const FrontierArgs& a, const Worklis
     return sync();
 }
 
-// Hybrid schedule for one LTS. CTA 0 selects the splitters of every round.
-// A round of one light splitter (at most 32 members whose incoming
-// transitions number at most light_edges), or of several splitters with at
-// most local_budget states together, is done by CTA 0 alone with CTA
-// barriers; other rounds are published (cmd_C, cmd_K, cmd_stamp and the
-// splitter list, then cmd_seq with release order) and done by the whole grid
-// with grid barriers, as in k_frontier_main. The other CTAs wait for
-// commands; their wait is bounded by timeout_ns without progress, where
-// progress is a new command or a new heartbeat from CTA 0.
+// Hybrid schedule for one LTS. A round of one light splitter (at most 32
+// members whose incoming transitions number at most light_edges), or of
+// several splitters with at most local_budget states together, is done by
+// CTA 0 alone with CTA barriers; every other round is done by the whole grid
+// with grid barriers. After a grid round every CTA selects the next round's
+// splitters itself: the selection reads only what the barrier made visible
+// (worklist tails and entries, block ranges) and each CTA's copy of the
+// worklist heads, so all CTAs choose the same round. When that round is a
+// CTA-0 round the other CTAs park; CTA 0 then publishes the next grid round
+// (cmd_C, cmd_K, cmd_stamp, the splitter list and its worklist heads, then
+// cmd_seq with release order), which brings them back in step. A parked
+// CTA's wait is bounded by timeout_ns without progress, where progress is a
+// new command or a new heartbeat from CTA 0. The touched-block counters of
+// grid rounds alternate by round parity; CTA 0 clears the next round's pair.
 template <int MAXT>  // most threads per CTA (sets the register budget)
 __global__ void __launch_bounds__(MAXT, 1) k_frontier_hybrid(FrontierArgs a, HybridArgs h) {
     __shared__ CtaShared sh;
     __shared__ int s_defer[32];
     __shared__ int s_ndefer;
-    __shared__ int s_ns, s_nm, s_heavy;
+    __shared__ int s_ns, s_nm, s_heavy, s_cmd, s_K;
+    __shared__ unsigned s_stamp;
     __shared__ uint32_t s_lost[32];  // rounds on CTA 0 alone take at most 32 splitters
     extern __shared__ int32_t s_dyn[];
     const int kmax = max(h.kmax, 1);
@@ -996,135 +1002,44 @@ __global__ void __launch_bounds__(MAXT, 1) k_frontier_hybrid(FrontierArgs a, Hyb
     const int32_t n = a.n;
     const int64_t wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int64_t gw = gtid >> 5, nwarps = gsz >> 5;
+    const bool lead = blockIdx.x == 0;
     bisim_ctrl* c = a.ctrl;
     unsigned long long tgt = 0;
     long long edges = 0, states = 0, commits = 0;
-    if (a.test_hook == 1 && blockIdx.x == 0) return;  // testing: never publish, never arrive
+    if (a.test_hook == 1 && lead) return;  // testing: never publish, never arrive
     const Worklist wl{c->bq_tail, a.queue, (size_t)n, 0, n};
     auto gsync = [&]() { return grid_sync(a.gb, tgt); };
     auto csync = [&]() {
         __syncthreads();
         return true;
     };
-    if (blockIdx.x == 0) {
-        if (threadIdx.x < BISIM_BUCKETS) sh.head[threadIdx.x] = 0;
-        if (threadIdx.x < 32) s_lost[threadIdx.x] = 0u;
-        __syncthreads();
-        int64_t r = 0;
-        for (;;) {
-            r++;
-            const uint32_t stamp = a.stamp0 + (uint32_t)r;
-            int K;
-            int32_t C;
-            if (kmax > 1) {
-                K = select_many(a, wl, sh.head, sh, s_selC, s_selP, kmax, h.budget);
-                C = K > 0 ? s_selC[0] : -1;
-            } else {
-                C = select_splitter(wl, sh.head, sh);
-                K = C >= 0 ? 1 : 0;
-            }
-            if (K > 0 && r > a.round_cap) {
-                if (threadIdx.x == 0) atomicOr(&c->status, ST_ROUNDS);
-                K = 0;
-            }
-            if (K == 0) {
-                if (threadIdx.x == 0) {
-                    c->cmd_C = -1;
-                    __threadfence();
-                    atomicAdd(&c->cmd_seq, 1ull);
-                    c->rounds = r;
-                }
-                break;
-            }
-            if (K > 1) {
-                if (s_selP[K] <= h.local_budget) {
-                    if (threadIdx.x == 0) {
-                        s_ns = 0;
-                        s_nm = 0;
-                    }
-                    __syncthreads();
-                    multi_round(a, wl, sh, s_defer, &s_ndefer, s_selC, s_selP, K, s_lost, stamp, wid, nw, &s_ns,
-                                &s_nm, a.tlist, a.tlist + n, 0, 1, edges, states, commits, csync);
-                    if (threadIdx.x == 0) *(volatile unsigned long long*)&c->heartbeat = (unsigned long long)r;
-                } else {
-                    for (int i = threadIdx.x; i <= K; i += blockDim.x) {
-                        if (i < K) h.g_selC[i] = s_selC[i];
-                        h.g_selP[i] = s_selP[i];
-                    }
-                    __threadfence();
-                    __syncthreads();
-                    if (threadIdx.x == 0) {
-                        c->n_touched[0] = 0;
-                        c->n_mid[0] = 0;
-                        c->cmd_C = MULTI;
-                        c->cmd_K = K;
-                        c->cmd_stamp = stamp;
-                        __threadfence();
-                        atomicAdd(&c->cmd_seq, 1ull);
-                    }
-                    if (!multi_round(a, wl, sh, s_defer, &s_ndefer, s_selC, s_selP, K, h.g_lost, stamp, gw, nwarps,
-                                     &c->n_touched[0], &c->n_mid[0], a.tlist, a.tlist + n, 0, (int)gridDim.x, edges,
-                                     states, commits, gsync))
-                        return;
-                }
-                continue;
-            }
-            if (threadIdx.x == 0) {
-                a.unstable[C] = 0u;
-                commits++;
-            }
-            // light or heavy?
-            if (threadIdx.x < 32) {
-                const int32_t b0 = ldcg(&a.bbeg[C]), e0 = ldcg(&a.bend[C]);
-                int heavy = 1;
-                if (e0 - b0 <= 32) {
-                    int deg = 0;
-                    if ((int)threadIdx.x < e0 - b0) {
-                        const int32_t t = ldcg(&a.elems[b0 + threadIdx.x]);
-                        deg = a.in_ptr[t + 1] - a.in_ptr[t];
-                    }
-                    heavy = __reduce_add_sync(0xffffffffu, deg) > h.light_edges;
-                }
-                if (threadIdx.x == 0) {
-                    s_heavy = heavy;
-                    s_ns = 0;
-                    s_nm = 0;
-                    if (heavy) {
-                        c->n_touched[0] = 0;
-                        c->n_mid[0] = 0;
-                        c->cmd_C = C;
-                        c->cmd_stamp = stamp;
-                        __threadfence();
-                        atomicAdd(&c->cmd_seq, 1ull);
-                    }
-                }
-            }
-            __syncthreads();
-            if (s_heavy) {
-                mark_step(a, C, stamp, gw, nwarps, &c->n_touched[0], &c->n_mid[0], a.tlist, a.tlist + n, edges);
-                if (!grid_sync(a.gb, tgt)) return;
-                split_step(a, wl, sh, s_defer, &s_ndefer, stamp, C, ldcg(&c->n_touched[0]), a.tlist,
-                           ldcg(&c->n_mid[0]), a.tlist + n, gw, nwarps, 0, (int)gridDim.x, states);
-                if (!grid_sync(a.gb, tgt)) return;
-            } else {
-                mark_step(a, C, stamp, wid, nw, &s_ns, &s_nm, a.tlist, a.tlist + n, edges);
-                __syncthreads();
-                split_step(a, wl, sh, s_defer, &s_ndefer, stamp, C, s_ns, a.tlist, s_nm, a.tlist + n, wid, nw, 0, 1,
-                           states);
-                __syncthreads();
-                if (threadIdx.x == 0) *(volatile unsigned long long*)&c->heartbeat = (unsigned long long)r;
-            }
-        }
-    } else {
-        __shared__ int s_cmd, s_K;
-        __shared__ unsigned s_stamp;
-        unsigned long long seen = 0;
-        for (;;) {
+    // a grid round: K > 1 splitters in selC / selP, or the single splitter C
+    auto grid_round = [&](int K, int32_t C, uint32_t stamp, int par) -> bool {
+        int* ns = &c->n_touched[par];
+        int* nm = &c->n_mid[par];
+        if (K > 1)
+            return multi_round(a, wl, sh, s_defer, &s_ndefer, s_selC, s_selP, K, h.g_lost, stamp, gw, nwarps, ns, nm,
+                               a.tlist, a.tlist + n, (int)blockIdx.x, (int)gridDim.x, edges, states, commits, gsync);
+        mark_step(a, C, stamp, gw, nwarps, ns, nm, a.tlist, a.tlist + n, edges);
+        if (!gsync()) return false;
+        split_step(a, wl, sh, s_defer, &s_ndefer, stamp, C, ld_volatile_i32(ns), a.tlist, ld_volatile_i32(nm),
+                   a.tlist + n, gw, nwarps, (int)blockIdx.x, (int)gridDim.x, states);
+        return gsync();
+    };
+    if (threadIdx.x < BISIM_BUCKETS) sh.head[threadIdx.x] = 0;
+    if (threadIdx.x < 32) s_lost[threadIdx.x] = 0u;
+    __syncthreads();
+    bool in_step = true;  // the other CTAs follow the selection (CTA 0: they are not parked)
+    unsigned long long seen = 0;
+    int64_t r = 0;
+    for (;;) {
+        if (!lead && !in_step) {
+            // parked: wait for CTA 0's next grid round
             if (threadIdx.x == 0) {
                 int ab = 0;
-                unsigned long long t0 = 0, hb = ~0ull;
+                unsigned long long t0 = 0, hb = ~0ull, v;
                 unsigned spins = 0;
-                while (ld_acquire_u64_g(&c->cmd_seq) == seen) {
+                while ((v = ld_acquire_u64_g(&c->cmd_seq)) == seen) {
                     __nanosleep(64);
                     if ((++spins & 31u) == 0) {
                         const unsigned long long now = globaltimer_ns();
@@ -1143,7 +1058,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_frontier_hybrid(FrontierArgs a, Hyb
                         }
                     }
                 }
-                seen++;
+                seen = v;
                 s_cmd = ab ? -1 : ldcg(&c->cmd_C);
                 s_stamp = ldcg(&c->cmd_stamp);
                 s_K = ldcg(&c->cmd_K);
@@ -1152,8 +1067,8 @@ __global__ void __launch_bounds__(MAXT, 1) k_frontier_hybrid(FrontierArgs a, Hyb
             const int32_t C = s_cmd;
             const uint32_t stamp = s_stamp;
             const int K = s_K;
-            __syncthreads();
             if (C == -1) break;
+            if (threadIdx.x < BISIM_BUCKETS) sh.head[threadIdx.x] = ldcg(&c->cmd_heads[threadIdx.x]);
             if (C == MULTI) {
                 // K <= SEL_E * blockDim: every load is issued before the first store
                 int32_t vc[SEL_E], vp[SEL_E + 1];
@@ -1169,19 +1084,113 @@ __global__ void __launch_bounds__(MAXT, 1) k_frontier_hybrid(FrontierArgs a, Hyb
                     if (e < SEL_E && i < K) s_selC[i] = vc[e];
                     if (i <= K) s_selP[i] = vp[e];
                 }
-                __syncthreads();
-                if (!multi_round(a, wl, sh, s_defer, &s_ndefer, s_selC, s_selP, K, h.g_lost, stamp, gw, nwarps,
-                                 &c->n_touched[0], &c->n_mid[0], a.tlist, a.tlist + n, (int)blockIdx.x,
-                                 (int)gridDim.x, edges, states, commits, gsync))
-                    return;
+            }
+            __syncthreads();
+            r = (int64_t)(stamp - a.stamp0);
+            if (!grid_round(C == MULTI ? K : 1, C, stamp, (int)(r & 1))) return;
+            in_step = true;
+            continue;
+        }
+        r++;
+        const uint32_t stamp = a.stamp0 + (uint32_t)r;
+        const int par = (int)(r & 1);
+        int K;
+        int32_t C;
+        if (kmax > 1) {
+            K = select_many(a, wl, sh.head, sh, s_selC, s_selP, kmax, h.budget);
+            C = K > 0 ? s_selC[0] : -1;
+        } else {
+            C = select_splitter(wl, sh.head, sh);
+            K = C >= 0 ? 1 : 0;
+        }
+        if (K > 0 && r > a.round_cap) {
+            if (lead && threadIdx.x == 0) atomicOr(&c->status, ST_ROUNDS);
+            K = 0;
+        }
+        if (K == 0) {
+            if (lead && threadIdx.x == 0) {
+                if (!in_step) {
+                    c->cmd_C = -1;
+                    __threadfence();
+                    atomicAdd(&c->cmd_seq, 1ull);
+                }
+                c->rounds = r;
+            }
+            break;
+        }
+        // CTA 0 alone, or the grid?
+        bool local;
+        if (K > 1) {
+            local = s_selP[K] <= h.local_budget;
+        } else {
+            if (threadIdx.x < 32) {
+                const int32_t b0 = ldcg(&a.bbeg[C]), e0 = ldcg(&a.bend[C]);
+                int heavy = 1;
+                if (e0 - b0 <= 32) {
+                    int deg = 0;
+                    if ((int)threadIdx.x < e0 - b0) {
+                        const int32_t t = ldcg(&a.elems[b0 + threadIdx.x]);
+                        deg = a.in_ptr[t + 1] - a.in_ptr[t];
+                    }
+                    heavy = __reduce_add_sync(0xffffffffu, deg) > h.light_edges;
+                }
+                if (threadIdx.x == 0) s_heavy = heavy;
+            }
+            __syncthreads();
+            local = !s_heavy;
+        }
+        if (lead && threadIdx.x == 0) {
+            c->n_touched[par ^ 1] = 0;  // the next grid round's counters
+            c->n_mid[par ^ 1] = 0;
+            if (K == 1) {
+                a.unstable[C] = 0u;
+                commits++;
+            }
+        }
+        if (local) {
+            if (!lead) {
+                in_step = false;  // park until CTA 0 publishes a grid round
                 continue;
             }
-            mark_step(a, C, stamp, gw, nwarps, &c->n_touched[0], &c->n_mid[0], a.tlist, a.tlist + n, edges);
-            if (!grid_sync(a.gb, tgt)) return;
-            split_step(a, wl, sh, s_defer, &s_ndefer, stamp, C, ldcg(&c->n_touched[0]), a.tlist,
-                       ldcg(&c->n_mid[0]), a.tlist + n, gw, nwarps, (int)blockIdx.x, (int)gridDim.x, states);
-            if (!grid_sync(a.gb, tgt)) return;
+            if (threadIdx.x == 0) {
+                s_ns = 0;
+                s_nm = 0;
+            }
+            __syncthreads();
+            if (K > 1) {
+                multi_round(a, wl, sh, s_defer, &s_ndefer, s_selC, s_selP, K, s_lost, stamp, wid, nw, &s_ns, &s_nm,
+                            a.tlist, a.tlist + n, 0, 1, edges, states, commits, csync);
+            } else {
+                mark_step(a, C, stamp, wid, nw, &s_ns, &s_nm, a.tlist, a.tlist + n, edges);
+                __syncthreads();
+                split_step(a, wl, sh, s_defer, &s_ndefer, stamp, C, s_ns, a.tlist, s_nm, a.tlist + n, wid, nw, 0, 1,
+                           states);
+                __syncthreads();
+            }
+            if (threadIdx.x == 0) *(volatile unsigned long long*)&c->heartbeat = (unsigned long long)r;
+            in_step = false;
+            continue;
         }
+        if (lead && !in_step) {
+            // wake the parked CTAs with this round and the heads after its selection
+            if (K > 1)
+                for (int i = threadIdx.x; i <= K; i += blockDim.x) {
+                    if (i < K) h.g_selC[i] = s_selC[i];
+                    h.g_selP[i] = s_selP[i];
+                }
+            if (threadIdx.x < BISIM_BUCKETS) c->cmd_heads[threadIdx.x] = sh.head[threadIdx.x];
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                c->cmd_C = K > 1 ? MULTI : C;
+                c->cmd_K = K;
+                c->cmd_stamp = stamp;
+                __threadfence();
+                atomicAdd(&c->cmd_seq, 1ull);
+            }
+        }
+        in_step = true;
+        if (!grid_round(K, C, stamp, par)) return;
     }
     if (edges) atomicAdd((unsigned long long*)&c->edges, (unsigned long long)edges);
     if (states) atomicAdd((unsigned long long*)&c->states, (unsigned long long)states);
