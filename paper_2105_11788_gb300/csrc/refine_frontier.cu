@@ -508,33 +508,37 @@ __device__ void warp_split_sparse(const FrontierArgs& a, const Worklist& wl, int
 // blockDim/32 entries.
 __device__ void split_step(const FrontierArgs& a, const Worklist& wl, CtaShared& sh, int* defer, int* ndefer,
                            uint32_t stamp, int32_t C, int ns, const int4* small_list, int nm,
-                           const int4* mid_list, int64_t gw, int64_t nwarps, int cta, int ncta,
+                           const int4* mid_list, int cta, int ncta,
                            long long& states) {
     const int wid = (int)(threadIdx.x >> 5);
     const int nw = (int)(blockDim.x >> 5);
-    for (int64_t i = gw; i < ns; i += nwarps) {
-        const int4 t = ldcg(&small_list[i]);
-        warp_split(a, wl, t.x, t.y, t.z, stamp, C, states);
-    }
-    // entry i goes to CTA i % ncta, so the first ncta entries land on
-    // different CTAs; inside a CTA its entries go to different warps
-    for (int base = 0; base < nm; base += ncta * nw) {
-        if (threadIdx.x == 0) *ndefer = 0;
-        __syncthreads();
-        const int i = base + wid * ncta + cta;
-        if (i < nm) {
-            const int4 t = ldcg(&mid_list[i]);
-            const int32_t b = t.x;
-            const int32_t km = ldcg(&a.mcnt[b]);
-            if (km <= 32) {
-                warp_split_sparse(a, wl, b, t.y, t.z, km, stamp, C, states);
-            } else if ((threadIdx.x & 31) == 0) {
-                defer[atomicAdd(ndefer, 1)] = b;
+    // entry i of either list goes to CTA i % ncta, so the first ncta entries
+    // land on different CTAs; inside a CTA, warp-list entries take the first
+    // warps and CTA-list entries the last, and the first pass over the CTA
+    // list runs alongside the warp list
+    auto mid_entry = [&](int i) {
+        const int4 t = ldcg(&mid_list[i]);
+        const int32_t km = ldcg(&a.mcnt[t.x]);
+        if (km <= 32)
+            warp_split_sparse(a, wl, t.x, t.y, t.z, km, stamp, C, states);
+        else if ((threadIdx.x & 31) == 0)
+            defer[atomicAdd(ndefer, 1)] = t.x;
+    };
+    if (threadIdx.x == 0) *ndefer = 0;
+    __syncthreads();
+    for (int base = 0; base < max(nm, 1); base += ncta * nw) {
+        const int i = base + (nw - 1 - wid) * ncta + cta;
+        if (i < nm) mid_entry(i);
+        if (base == 0)
+            for (int64_t q = cta + (int64_t)wid * ncta; q < ns; q += (int64_t)ncta * nw) {
+                const int4 t = ldcg(&small_list[q]);
+                warp_split(a, wl, t.x, t.y, t.z, stamp, C, states);
             }
-        }
         __syncthreads();
         const int nd = *ndefer;
-        for (int j = 0; j < nd; j++) cta_split(a, wl, sh, defer[j], stamp, C, states);
+        for (int jd = 0; jd < nd; jd++) cta_split(a, wl, sh, defer[jd], stamp, C, states);
+        __syncthreads();
+        if (threadIdx.x == 0) *ndefer = 0;
         __syncthreads();
     }
 }
@@ -831,7 +835,7 @@ __global__ void __launch_bounds__(1024) k_frontier_main(FrontierArgs a) {
                   a.tlist + n, edges);
         if (!grid_sync(a.gb, tgt)) return;
         split_step(a, wl, sh, s_defer, &s_ndefer, stamp, C, ldcg(&a.ctrl->n_touched[par]), a.tlist,
-                   ldcg(&a.ctrl->n_mid[par]), a.tlist + n, gw, nwarps, (int)blockIdx.x, (int)gridDim.x, states);
+                   ldcg(&a.ctrl->n_mid[par]), a.tlist + n, (int)blockIdx.x, (int)gridDim.x, states);
         if (!grid_sync(a.gb, tgt)) return;
     }
     if (edges) atomicAdd((unsigned long long*)&a.ctrl->edges, (unsigned long long)edges);
@@ -966,8 +970,8 @@ __device__ __forceinline__ bool multi_round(const FrontierArgs& a, const Worklis
                   commits);
     }
     if (!sync()) return false;
-    split_step(a, wl, sh, defer, ndefer, stamp, MULTI, ld_volatile_i32(n_small), small_list, ld_volatile_i32(n_mid), mid_list, gw,
-               nwarps, cta, ncta, states);
+    split_step(a, wl, sh, defer, ndefer, stamp, MULTI, ld_volatile_i32(n_small), small_list, ld_volatile_i32(n_mid),
+               mid_list, cta, ncta, states);
     return sync();
 }
 
@@ -1023,7 +1027,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_frontier_hybrid(FrontierArgs a, Hyb
         mark_step(a, C, stamp, gw, nwarps, ns, nm, a.tlist, a.tlist + n, edges);
         if (!gsync()) return false;
         split_step(a, wl, sh, s_defer, &s_ndefer, stamp, C, ld_volatile_i32(ns), a.tlist, ld_volatile_i32(nm),
-                   a.tlist + n, gw, nwarps, (int)blockIdx.x, (int)gridDim.x, states);
+                   a.tlist + n, (int)blockIdx.x, (int)gridDim.x, states);
         return gsync();
     };
     if (threadIdx.x < BISIM_BUCKETS) sh.head[threadIdx.x] = 0;
@@ -1163,8 +1167,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_frontier_hybrid(FrontierArgs a, Hyb
             } else {
                 mark_step(a, C, stamp, wid, nw, &s_ns, &s_nm, a.tlist, a.tlist + n, edges);
                 __syncthreads();
-                split_step(a, wl, sh, s_defer, &s_ndefer, stamp, C, s_ns, a.tlist, s_nm, a.tlist + n, wid, nw, 0, 1,
-                           states);
+                split_step(a, wl, sh, s_defer, &s_ndefer, stamp, C, s_ns, a.tlist, s_nm, a.tlist + n, 0, 1, states);
                 __syncthreads();
             }
             if (threadIdx.x == 0) *(volatile unsigned long long*)&c->heartbeat = (unsigned long long)r;
@@ -1284,7 +1287,7 @@ __global__ void __launch_bounds__(1024) k_frontier_batch(FrontierArgs a, BatchAr
                 mark_step(a, C, stamp, gw, nwarps, &s_ns, &s_nm, a.tlist + s0, a.tlist + a.n + s0, edges);
                 __syncthreads();
                 split_step(a, wl, sh, s_defer, &s_ndefer, stamp, C, s_ns, a.tlist + s0, s_nm, a.tlist + a.n + s0,
-                           gw, nwarps, 0, 1, states);
+                           0, 1, states);
             } else {
                 claim_step(a, s_selC, s_selP, K, s_lost, stamp, gw, nwarps);
                 __syncthreads();
@@ -1292,7 +1295,7 @@ __global__ void __launch_bounds__(1024) k_frontier_batch(FrontierArgs a, BatchAr
                           a.tlist + a.n + s0, edges, commits);
                 __syncthreads();
                 split_step(a, wl, sh, s_defer, &s_ndefer, stamp, MULTI, s_ns, a.tlist + s0, s_nm,
-                           a.tlist + a.n + s0, gw, nwarps, 0, 1, states);
+                           a.tlist + a.n + s0, 0, 1, states);
             }
             __syncthreads();
         }
