@@ -667,6 +667,14 @@ __device__ int select_many(const FrontierArgs& a, const Worklist& wl, unsigned l
     }
     __syncthreads();
     const int n0 = sh.bn[0];  // entries [0, n0) come from bucket 0
+    if (n0 >= k0) {
+        // every entry is a block of one state: prefix j, the budget caps the count
+        const int K = k0 > 0 ? min(k0, max(budget, 1)) : 0;
+        for (int j = threadIdx.x; j <= K; j += blockDim.x) selP[j] = j;
+        if (threadIdx.x == 0) head[0] += (unsigned long long)K;
+        __syncthreads();
+        return K;
+    }
     const int E = (k0 + (int)blockDim.x - 1) / (int)blockDim.x;
     const int j0 = (int)threadIdx.x * E;
     int32_t cs[SEL_E];
@@ -882,9 +890,12 @@ __device__ __forceinline__ void claim_item(const FrontierArgs& a, const int32_t*
     ic.j = j;
     ic.C = C;
     const unsigned long long key = ((unsigned long long)(~stamp) << 32) | (unsigned)j;
-    const int32_t cb = ldcg(&a.bbeg[C]);
-    if (i == selP[j] && lane == 0 && ldcg(&a.bend[C]) - cb > 1) claim_label(a, C, key, lost, stamp);
-    const int32_t t = ldcg(&a.elems[cb + (int32_t)i - selP[j]]);
+    int32_t t = C;  // a block of one state holds its label only
+    if (selP[j + 1] - selP[j] > 1) {
+        const int32_t cb = ldcg(&a.bbeg[C]);
+        if (i == selP[j] && lane == 0) claim_label(a, C, key, lost, stamp);
+        t = ldcg(&a.elems[cb + (int32_t)i - selP[j]]);
+    }
     ic.j0 = a.in_ptr[t];
     ic.j1 = a.in_ptr[t + 1];
     const bool has = ic.j0 + lane < ic.j1;
