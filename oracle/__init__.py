@@ -69,7 +69,8 @@ def _load():
             lib.oracle_plan.argtypes = [i32, i64, i32, P, P, P, P, P, P, P, P, P]
             lib.oracle_pram.argtypes = [i32, i64, i32, P, P, P, P, i32, i32, i64, P, P, P]
             lib.oracle_pram_step.argtypes = [i32, i64, i32, P, P, P, P, P, i32, i32, P, P]
-            for f in (lib.oracle_ks, lib.oracle_plan, lib.oracle_pram, lib.oracle_pram_step):
+            lib.oracle_pair.argtypes = [i32, i64, i32, P, P, P, P, i64, P, P]
+            for f in (lib.oracle_ks, lib.oracle_plan, lib.oracle_pram, lib.oracle_pram_step, lib.oracle_pair):
                 f.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -158,9 +159,28 @@ def pram_step(n, num_act, src, act, dst, block, unstable, C, alg2=False):
     return blk, uns.astype(bool), marks[:nm].astype(bool)
 
 
+def pair(n, num_act, src, act, dst, init=None, round_cap=0):
+    """(C, a)-pair splitters (Algorithm 2 one label at a time) under the
+    priority rule. Returns (raw leader labels, iterations counting the final
+    empty one)."""
+    lib = _load()
+    src, act, dst, init = _c32(src), _c32(act), _c32(dst), _c32(init)
+    out = np.empty(max(n, 1), dtype=np.int32)
+    r = np.zeros(1, dtype=np.int64)
+    rc = lib.oracle_pair(n, src.shape[0], num_act, _ptr(src), _ptr(act), _ptr(dst), _ptr(init),
+                         int(round_cap), _ptr(out), _ptr(r))
+    if rc:
+        raise OracleError(f"oracle_pair failed: {rc}")
+    return out[:n], int(r[0])
+
+
 def ks_lts(lts, **kw):
     return ks(lts.n, lts.num_act, lts.src, lts.act, lts.dst, lts.init, **kw)
 
 
 def pram_lts(lts, **kw):
     return pram(lts.n, lts.num_act, lts.src, lts.act, lts.dst, lts.init, **kw)
+
+
+def pair_lts(lts, **kw):
+    return pair(lts.n, lts.num_act, lts.src, lts.act, lts.dst, lts.init, **kw)

@@ -29,6 +29,21 @@
  *
  *  oracle_pram_step  One iteration of the main loop with a given splitter C
  *                  (used to replay the worked example of Figure 1).
+ *
+ *  oracle_pair     (C, a)-pair splitters: Algorithm 2 applied with one action
+ *                  label at a time. The priority rule picks the smallest
+ *                  unstable label C; then one iteration per label a that
+ *                  occurs, in increasing order, marks the states with an
+ *                  a-transition into C (one flag per state), splits every
+ *                  block into the states whose flag equals the leader's and
+ *                  the rest, and elects the smallest state of the rest as its
+ *                  leader; both labels of a split block become unstable (as
+ *                  in Algorithm 2, the splitter is not set unstable again).
+ *                  No action-set preprocessing is needed: the first
+ *                  selection of every block splits it by each label. With a
+ *                  single label this is Algorithm 2 exactly. Returns the raw
+ *                  block labels and the number of iterations, one per
+ *                  (C, a) pair plus the final one that finds no splitter.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -453,4 +468,75 @@ int oracle_pram_step(int32_t n, int64_t m, int32_t A, const int32_t* src, const 
     *mark_length = p.L;
     pram_free(&p);
     return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* (C, a)-pair splitters                                                       */
+/* ------------------------------------------------------------------------- */
+
+int oracle_pair(int32_t n, int64_t m, int32_t A, const int32_t* src, const int32_t* act,
+                const int32_t* dst, const int32_t* init, int64_t round_cap, int32_t* out_labels,
+                int64_t* out_rounds) {
+    int rc = check_input(n, m, A, src, act, dst, init);
+    if (rc) return rc;
+    size_t nn = (size_t)(n ? n : 1);
+    int32_t* block = malloc(sizeof(int32_t) * nn);
+    int32_t* leader = malloc(sizeof(int32_t) * nn);
+    char* mark = malloc(nn);
+    char* split = malloc(nn);
+    char* unstable = malloc(nn);
+    char* occurs = calloc((size_t)A, 1);
+    if (!block || !leader || !mark || !split || !unstable || !occurs) {
+        free(block); free(leader); free(mark); free(split); free(unstable); free(occurs);
+        return OR_ENOMEM;
+    }
+    for (int64_t k = 0; k < m; k++) occurs[act ? act[k] : 0] = 1;
+    /* initial leaders: the smallest state of every initial block */
+    for (int32_t i = 0; i < n; i++) leader[i] = -1;
+    for (int32_t i = 0; i < n; i++) {
+        int32_t b = init ? init[i] : 0;
+        if (leader[b] < 0) leader[b] = i;
+    }
+    for (int32_t i = 0; i < n; i++) block[i] = leader[init ? init[i] : 0];
+    for (int32_t i = 0; i < n; i++) unstable[i] = block[i] == i;
+    int32_t nlab = 0;
+    for (int32_t a = 0; a < A; a++) nlab += occurs[a];
+    int64_t rounds = 0;
+    for (;;) {
+        rounds++;
+        if (round_cap > 0 && rounds > round_cap) { rc = OR_EROUNDS; break; }
+        int32_t C = -1;
+        for (int32_t i = 0; i < n; i++)
+            if (unstable[i]) { C = i; break; }
+        if (C < 0) break;
+        unstable[C] = 0;
+        int32_t done = 0;
+        for (int32_t a = 0; a < A; a++) {
+            if (!occurs[a]) continue;
+            if (done++ > 0) {
+                rounds++;
+                if (round_cap > 0 && rounds > round_cap) { rc = OR_EROUNDS; break; }
+            }
+            /* mark: s -a-> t with t in C */
+            memset(mark, 0, nn);
+            for (int64_t k = 0; k < m; k++)
+                if ((act ? act[k] : 0) == a && block[dst[k]] == C) mark[src[k]] = 1;
+            /* split: the flag differs from the leader's */
+            for (int32_t i = 0; i < n; i++) split[i] = mark[i] != mark[block[i]];
+            /* priority election of the new leader, then relabelling */
+            for (int32_t i = n - 1; i >= 0; i--)
+                if (split[i]) leader[block[i]] = i;
+            for (int32_t i = 0; i < n; i++)
+                if (split[i]) unstable[block[i]] = 1;
+            for (int32_t i = 0; i < n; i++)
+                if (split[i]) block[i] = leader[block[i]];
+            for (int32_t i = 0; i < n; i++)
+                if (split[i]) unstable[block[i]] = 1;
+        }
+        if (rc) break;
+    }
+    memcpy(out_labels, block, sizeof(int32_t) * (size_t)n);
+    *out_rounds = rounds;
+    free(block); free(leader); free(mark); free(split); free(unstable); free(occurs);
+    return rc;
 }

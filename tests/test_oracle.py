@@ -112,6 +112,8 @@ def test_fig1_final_partition():
     for alg2 in (False, True):
         labels, _, _ = oracle.pram(5, 1, src, act, dst, init, alg2=alg2)
         assert defs.canonical(labels).tolist() == want.tolist()
+    labels, _ = oracle.pair(5, 1, src, act, dst, init)
+    assert defs.canonical(labels).tolist() == want.tolist()
 
 
 # ------------------------------------------------------------ brute force
@@ -135,7 +137,27 @@ def _check_all(n, A, src, act, dst, init, enum=True):
         labels2, rounds2, _ = oracle.pram(n, A, src, act, dst, init, alg2=True)
         assert defs.canonical(labels2).tolist() == want.tolist()
         assert B + 1 <= rounds2 <= 2 * B - p0 + 1  # Theorem 2 plus the empty iteration
+    _check_pair(n, A, src, act, dst, init, want)
     return want
+
+
+def _check_pair(n, A, src, act, dst, init, want):
+    """(C, a)-pair splitters: the same partition; every final block is
+    selected at least once and a label becomes unstable only when it is
+    created or its block splits, so B * nl + 1 <= iterations <=
+    (2B - |pi_0|) * nl + 1 with nl = max(1, labels that occur); with one
+    label it is Algorithm 2 without preprocessing, iteration for iteration."""
+    labels, rounds = oracle.pair(n, A, src, act, dst, init)
+    assert defs.canonical(labels).tolist() == want.tolist()
+    assert all(labels[labels[s]] == labels[s] for s in range(n))
+    B = defs.num_blocks(want)
+    pi0 = defs.num_blocks(init) if init is not None and n else min(n, 1)
+    nl = max(1, len(set(np.asarray(act).tolist())))
+    assert B * nl + 1 <= rounds <= (2 * B - pi0) * nl + 1
+    if A == 1:
+        labels2, rounds2, pre2 = oracle.pram(n, A, src, act, dst, init, alg2=True, skip_preprocess=True)
+        assert pre2 == 0
+        assert labels.tolist() == labels2.tolist() and rounds == rounds2
 
 
 @pytest.mark.parametrize("n,A", [(1, 1), (1, 2), (2, 1), (2, 2), (3, 1)])
@@ -290,3 +312,24 @@ def test_invalid_inputs_rejected():
         oracle.ks(3, 1, z, np.array([0, 1], np.int32), z)
     with pytest.raises(oracle.OracleError):
         oracle.ks(3, 1, z, z, z, np.array([0, 0, 9], np.int32))
+
+
+def test_pair_splitters_one_label_at_a_time():
+    """Two labels that separate states only together: s0 -a-> s2, s1 -b-> s2,
+    s2 without transitions. The (C, a)-pair rounds must use each label on its
+    own: the result is discrete (s0 and s1 have different action sets)."""
+    src, act, dst = _arrays([(0, 0, 2), (1, 1, 2)])
+    labels, rounds = oracle.pair(3, 2, src, act, dst)
+    assert defs.canonical(labels).tolist() == [0, 1, 2]
+    # selections, two iterations each: C = 0 ({0,1,2}; a splits off {1,2}
+    # led by 1, b splits nothing: s1's b-target s2 left block 0), C = 0 again
+    # ({0}, re-marked by its split), C = 1 ({1,2}; b splits off {2}), C = 1
+    # ({1}), C = 2 ({2}); then the empty iteration
+    assert rounds == 5 * 2 + 1
+
+
+def test_pair_random_medium_matches_ks():
+    for seed in range(6):
+        lts = lts_gen.random_small(40 + seed, 200, 4, 600, blocks=2)
+        labels, rounds = oracle.pair_lts(lts)
+        assert defs.canonical(labels).tolist() == oracle.ks_lts(lts).tolist()
