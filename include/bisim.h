@@ -56,6 +56,13 @@ extern "C" {
  * elected by compare-and-swap (the arbitrary write rule). Same partition;
  * round count may differ and may vary between runs. */
 #define BISIM_ENGINE_FRONTIER 2
+/* (C, a)-pair rounds: Algorithm 2 applied with one action label at a time,
+ * one mark flag per state, every write under the priority rule (splitter =
+ * smallest unstable label, labels in increasing order, new leader =
+ * smallest splitting state). Needs no action-set preprocessing (pre_rounds
+ * is 0) and up to |Act| times as many rounds; a second, independent engine
+ * for cross-checks. Single LTSs only (bisim_batch_plan rejects it). */
+#define BISIM_ENGINE_PAIR 3
 
 typedef struct bisim_opts {
     int32_t engine;      /* BISIM_ENGINE_* (0 = auto) */

@@ -28,9 +28,10 @@ from . import bisim
 
 # (threads, ctas_per_sm, wide_threads, wide_min_states, splitters, split_budget)
 CANDIDATES: Tuple[Tuple[int, int, int, int, int, int], ...] = (
-    (128, 0, 0, 0, 1, 0), (256, 0, 0, 0, 1, 0), (512, 0, 0, 0, 1, 0), (1024, 0, 0, 0, 1, 0),
-    (256, 0, 1024, 1 << 15, 1, 0), (256, 0, 1024, 1 << 16, 1, 0), (128, 0, 1024, 1 << 15, 1, 0),
-    (256, 0, 0, 0, 16, 2), (256, 0, 0, 0, 64, 4), (512, 0, 0, 0, 64, 4), (256, 0, 1024, 1 << 15, 64, 4),
+    (128, 0, 0, 0, 1, 0), (256, 0, 0, 0, 1, 0), (512, 0, 0, 0, 1, 0),
+    (256, 0, 1024, 1 << 15, 1, 0), (128, 0, 1024, 1 << 15, 1, 0),
+    (128, 0, 0, 0, 16, 1), (256, 0, 0, 0, 16, 1), (256, 0, 0, 0, 64, 2), (512, 0, 0, 0, 64, 1),
+    (256, 0, 1024, 1 << 15, 64, 1),
 )
 KEYS = ("threads", "ctas_per_sm", "wide_threads", "wide_min_states", "splitters", "split_budget")
 

@@ -29,6 +29,7 @@ BISIM_ENOTSUP = -6
 ENGINE_AUTO = 0
 ENGINE_DENSE = 1
 ENGINE_FRONTIER = 2
+ENGINE_PAIR = 3
 
 
 class bisim_opts(ctypes.Structure):

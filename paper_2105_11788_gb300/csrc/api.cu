@@ -19,7 +19,7 @@ using namespace bisim;
 
 static int choose_engine(const bisim_plan_s* p) {
     int e = p->opts.engine;
-    if (e == BISIM_ENGINE_DENSE || e == BISIM_ENGINE_FRONTIER) return e;
+    if (e == BISIM_ENGINE_DENSE || e == BISIM_ENGINE_FRONTIER || e == BISIM_ENGINE_PAIR) return e;
     return BISIM_ENGINE_FRONTIER;
 }
 
@@ -71,6 +71,10 @@ int bisim_plan(int32_t n, int64_t m, int32_t num_act, const int32_t* src, const 
     }
     if (opts && (opts->threads < 0 || opts->threads > 1024 || (opts->threads & 31))) {
         set_last_error("opts.threads must be a multiple of 32 in [32, 1024] (or 0)");
+        return BISIM_EINVAL;
+    }
+    if (opts && (opts->engine < BISIM_ENGINE_AUTO || opts->engine > BISIM_ENGINE_PAIR)) {
+        set_last_error("opts.engine must be one of BISIM_ENGINE_*");
         return BISIM_EINVAL;
     }
     bisim_plan_s* p = new (std::nothrow) bisim_plan_s();
@@ -140,7 +144,9 @@ int bisim_refine(bisim_plan_t p, int32_t* out_block, bisim_stats* stats) {
     BISIM_CUDA_TRY(cudaEventRecord(p->ev0, p->st));
     int engine = choose_engine(p);
     g_launches = 0;
-    int rc = engine == BISIM_ENGINE_DENSE ? refine_dense(p, &s) : refine_frontier(p, &s);
+    int rc = engine == BISIM_ENGINE_DENSE  ? refine_dense(p, &s)
+             : engine == BISIM_ENGINE_PAIR ? refine_pair(p, &s)
+                                           : refine_frontier(p, &s);
     if (rc == BISIM_OK) rc = write_output(p, out_block, &s.num_blocks);
     s.launches = p->plan_launches + g_launches;
     if (rc == BISIM_OK) {

@@ -161,6 +161,10 @@ int bisim_batch_plan(int32_t k, const int64_t* state_off_h, const int64_t* trans
         set_last_error("opts.threads / wide_threads must be multiples of 32 in [32, 1024] (or 0)");
         return BISIM_EINVAL;
     }
+    if (opts && opts->engine == BISIM_ENGINE_PAIR) {
+        set_last_error("bisim_batch_plan: the batch path runs frontier rounds; the pair engine is for single LTSs");
+        return BISIM_ENOTSUP;
+    }
     if (k < 1 || !state_off_h || !trans_off_h || !num_act_h) {
         set_last_error("bisim_batch_plan: need k >= 1 and the offset / label-count arrays");
         return BISIM_EINVAL;

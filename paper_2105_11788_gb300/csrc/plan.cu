@@ -454,7 +454,9 @@ int plan_build(bisim_plan_s* p, const int32_t* src, const int32_t* act, const in
     std::vector<int32_t> labels_h;
     for (int32_t a = 0; a < A; a++)
         if (used_h[a]) labels_h.push_back(a);
-    p->pre_rounds = (int64_t)labels_h.size();
+    p->n_labels = (int64_t)labels_h.size();
+    // the pair engine splits by one label per round and needs no preprocessing
+    p->pre_rounds = p->opts.engine == BISIM_ENGINE_PAIR ? 0 : p->n_labels;
 
     // a2: sort by (source, label); slots, off, nr
     const uint64_t keyspace = (uint64_t)n * (uint64_t)A;

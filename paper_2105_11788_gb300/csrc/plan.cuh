@@ -61,7 +61,7 @@ struct bisim_plan_s {
     bisim::DevMem in_edge;   // uint64 [m]: (source << 32) | mark slot of the transition
     bisim::DevMem slot_src;  // int32 [L]: state owning each mark slot
     bisim::DevMem slot_act;  // int32 [L]: label of each mark slot
-    bisim::DevMem labels;    // int32 [pre_rounds]: labels that occur, increasing
+    bisim::DevMem labels;    // int32 [n_labels]: labels that occur, increasing
     bisim::DevMem block0;    // int32 [n]: leader labels after preprocessing
 
     // refinement state
@@ -105,7 +105,8 @@ struct bisim_plan_s {
     cudaEvent_t aux_event = nullptr;
 
     uint32_t stamp = 0;      // last round stamp used (marks are never cleared)
-    int64_t pre_rounds = 0;
+    int64_t pre_rounds = 0;  // action-set preprocessing rounds run (0 for the pair engine)
+    int64_t n_labels = 0;    // labels that occur
     int64_t initial_blocks = 0;
     double t_plan_ms = 0;
     double t_pre_ms = 0;
@@ -123,6 +124,7 @@ int plan_build(bisim_plan_s* p, const int32_t* src, const int32_t* act, const in
                const int32_t* init);
 int refine_dense(bisim_plan_s* p, bisim_stats* st);
 int refine_frontier(bisim_plan_s* p, bisim_stats* st);
+int refine_pair(bisim_plan_s* p, bisim_stats* st);
 // CTA-per-LTS frontier rounds over a batch plan; rounds[i] = iterations of LTS i
 int refine_frontier_batch(bisim_plan_s* p, bisim_stats* st, std::vector<long long>& rounds);
 int write_output(bisim_plan_s* p, int32_t* out_block, int64_t* num_blocks);

@@ -1300,13 +1300,11 @@ __global__ void __launch_bounds__(1024) k_frontier_batch(FrontierArgs a, BatchAr
                 split_step(a, wl, sh, s_defer, &s_ndefer, stamp, C, s_ns, a.tlist + s0, s_nm, a.tlist + a.n + s0,
                            0, 1, states);
             } else {
-                claim_step(a, s_selC, s_selP, K, s_lost, stamp, gw, nwarps);
-                __syncthreads();
-                mark_many(a, wl, s_selC, s_selP, K, s_lost, stamp, gw, nwarps, &s_ns, &s_nm, a.tlist + s0,
-                          a.tlist + a.n + s0, edges, commits);
-                __syncthreads();
-                split_step(a, wl, sh, s_defer, &s_ndefer, stamp, MULTI, s_ns, a.tlist + s0, s_nm,
-                           a.tlist + a.n + s0, 0, 1, states);
+                multi_round(a, wl, sh, s_defer, &s_ndefer, s_selC, s_selP, K, s_lost, stamp, gw, nwarps, &s_ns, &s_nm,
+                            a.tlist + s0, a.tlist + a.n + s0, 0, 1, edges, states, commits, [] {
+                                __syncthreads();
+                                return true;
+                            });
             }
             __syncthreads();
         }
