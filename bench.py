@@ -43,6 +43,26 @@ WORKLOADS = {
                    lambda: lts_gen.powerlaw(seed=3, n=2_000_000)),
 }
 
+# Fan_out_n (Section 5.1): the paper's Par-BCRP run times in ms (Titan RTX)
+PAPER_FANOUT_MS = {10: 1, 100: 5, 200: 9, 300: 13, 400: 18, 500: 22, 600: 26, 700: 30}
+
+
+def workload(args):
+    """(description, generator) of the chosen single-LTS workload."""
+    if args.workload == "fanout":
+        n = args.fanout_n
+        return (f"Fan_out_n of Section 5.1 (n={n}, 3n-3 transitions, labels a/b, single initial block)",
+                lambda: lts_gen.fan_out(n))
+    return WORKLOADS[args.workload]
+
+
+def vs_paper(args, value):
+    """value / the paper's number for this exact workload and metric (LTS/s), else None."""
+    if args.workload == "fanout" and args.fanout_n in PAPER_FANOUT_MS:
+        return value / (1000.0 / PAPER_FANOUT_MS[args.fanout_n])
+    return None
+
+
 L2_BYTES = 129 * 1024 * 1024
 
 
@@ -190,7 +210,7 @@ def run_reference(args, world, rank):
 
     if world > 1 and rank != 0:
         return
-    desc, make = WORKLOADS[args.workload]
+    desc, make = workload(args)
     lts = make()
     for _ in range(args.warmup):
         oracle.ks_lts(lts)
@@ -207,7 +227,7 @@ def run_reference(args, world, rank):
     line = {
         "impl": "reference", "metric": "LTS reduction throughput", "value": value,
         "unit": "LTS/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": vs_paper(args, value),
         "dtype": "int32", "data": "synthetic",
         "config": {"workload": desc, "n": lts.n, "m": lts.m, "num_act": lts.num_act,
                    "l2": "CPU run"},
@@ -389,13 +409,14 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="qexp", choices=sorted(WORKLOADS) + ["stream"])
+    ap.add_argument("--workload", default="qexp", choices=sorted(WORKLOADS) + ["fanout", "stream"])
+    ap.add_argument("--fanout-n", type=int, default=700, help="fanout: states of Fan_out_n")
     ap.add_argument("--stream-k", type=int, default=4096, help="LTSs in the stream workload")
     ap.add_argument("--plain-sample", type=int, default=128,
                     help="stream: LTSs reduced one at a time to estimate the plain rate")
     ap.add_argument("--serve-requests", type=int, default=256,
                     help="stream: requests per arrival rate in the serving run")
-    ap.add_argument("--engine", default="auto", choices=["auto", "dense", "frontier"])
+    ap.add_argument("--engine", default="auto", choices=["auto", "dense", "frontier", "pair"])
     ap.add_argument("--threads", type=int, default=0, help="threads per CTA (0 = library default)")
     ap.add_argument("--max-ctas", type=int, default=0, help="cap on persistent-kernel CTAs")
     ap.add_argument("--light-edges", type=int, default=0,
@@ -420,10 +441,10 @@ def main():
     dev = torch.device("cuda", local)
     bisim.load(build_if_missing=True)
     engine = {"auto": bisim.ENGINE_AUTO, "dense": bisim.ENGINE_DENSE,
-              "frontier": bisim.ENGINE_FRONTIER}[args.engine]
+              "frontier": bisim.ENGINE_FRONTIER, "pair": bisim.ENGINE_PAIR}[args.engine]
     opts = bisim.make_opts(engine=engine, threads=args.threads, max_ctas=args.max_ctas,
                            light_edges=args.light_edges)
-    desc, make = WORKLOADS[args.workload]
+    desc, make = workload(args)
     lts = make()
     src = torch.from_numpy(lts.src).to(dev)
     act = torch.from_numpy(lts.act).to(dev)
@@ -517,8 +538,8 @@ def main():
         line = {
             "metric": "LTS reduction throughput", "value": value, "unit": "LTS/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
-            "data": "synthetic",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": vs_paper(args, value),
+            "dtype": "int32", "data": "synthetic",
             "config": {"workload": desc, "n": lts.n, "m": lts.m, "num_act": lts.num_act,
                        "engine": args.engine, "threads": args.threads, "max_ctas": args.max_ctas,
                        "l2": "flushed between steps (256 MiB write)" if flush is not None

@@ -2,6 +2,8 @@
 
     python -m paper_2105_11788_gb300.diag barrier        # ns per grid barrier
     python -m paper_2105_11788_gb300.diag shapes         # main-loop time per launch shape
+    python -m paper_2105_11788_gb300.diag splitters      # splitters per round / state budget sweep
+    python -m paper_2105_11788_gb300.diag fanout         # Fan_out_n scaling, closed form checked
 
 Each prints JSON lines.
 """
@@ -9,6 +11,8 @@ from __future__ import annotations
 
 import json
 import sys
+
+import numpy as np
 
 from . import bisim, lts_gen
 
@@ -65,6 +69,25 @@ def splitters(workloads=("qexp", "powerlaw2m"), repeats: int = 2):
                                       "main_ms": best, "rounds": st.rounds, "steps": st.steps}), flush=True)
 
 
+def fanout(sizes=(10, 100, 200, 300, 400, 500, 600, 700, 10_000, 100_000, 1_000_000), repeats: int = 3):
+    """Fan_out_n (Section 5.1): reduction time (plan + refinement, device) per
+    engine against n, with the closed form checked (states 0 and 1 together,
+    every other state alone)."""
+    for n in sizes:
+        lts = lts_gen.fan_out(n)
+        want = np.concatenate([[0, 0], np.arange(1, n - 1)]).astype(np.int32)
+        for eng in (bisim.ENGINE_FRONTIER, bisim.ENGINE_DENSE, bisim.ENGINE_PAIR):
+            if eng != bisim.ENGINE_FRONTIER and n > 100_000:
+                continue
+            best, st = None, None
+            for _ in range(repeats):
+                got, st = bisim.reduce(lts, bisim.make_opts(engine=eng), return_stats=True)
+                t = st.t_plan_ms + st.t_refine_ms
+                best = t if best is None else min(best, t)
+            print(json.dumps({"workload": "fanout", "n": n, "engine": eng, "ms": best, "rounds": st.rounds,
+                              "steps": st.steps, "closed_form": bool(np.array_equal(got, want))}), flush=True)
+
+
 def main(argv):
     import torch
 
@@ -75,6 +98,8 @@ def main(argv):
         barrier()
     elif what == "shapes":
         shapes(tuple(argv[2:]) or ("kripke", "qexp", "chain"))
+    elif what == "fanout":
+        fanout()
     elif what == "splitters":
         splitters(tuple(argv[2:]) or ("qexp", "powerlaw2m"))
     else:

@@ -209,12 +209,11 @@ def batch_stream(seed: int = 4, k: int = 4096, rate_per_s: float = 1000.0, **kw)
 def fan_out(n: int) -> LTS:
     """Fan_out_n of Section 5.1: states 0..n-1, i -a-> i+1 for 1 < i < n-1,
     and 0 -b-> i, 1 -b-> i for every state i (a = 0, b = 1)."""
-    s, a, d = [], [], []
-    for i in range(2, n - 1):
-        s.append(i); a.append(0); d.append(i + 1)
-    for i in range(n):
-        s.append(0); a.append(1); d.append(i)
-        s.append(1); a.append(1); d.append(i)
+    chain = np.arange(2, max(n - 1, 2), dtype=np.int64)
+    every = np.arange(n, dtype=np.int64)
+    s = np.concatenate([chain, np.stack([np.zeros(n, np.int64), np.ones(n, np.int64)], axis=1).ravel()])
+    a = np.concatenate([np.zeros(chain.size, np.int64), np.ones(2 * n, np.int64)])
+    d = np.concatenate([chain + 1, np.repeat(every, 2)])
     return LTS(f"fan_out_{n}", n, 2, _i32(s), _i32(a), _i32(d), None)
 
 

@@ -274,3 +274,12 @@ def test_several_splitters_large_worklist():
     got, st = run(lts, bisim.ENGINE_FRONTIER)
     assert got.tolist() == oracle.ks_lts(lts).tolist()
     assert st.steps * 4 < st.rounds  # many splitters per barrier round
+
+
+@pytest.mark.parametrize("n", [10_000, 200_000])
+def test_fan_out_large_closed_form(n):
+    """Fan_out_n far beyond the paper's sizes: states 0 and 1 together, every
+    other state alone (n - 1 blocks)."""
+    got, st = run(lts_gen.fan_out(n), bisim.ENGINE_FRONTIER)
+    assert np.array_equal(got, np.concatenate([[0, 0], np.arange(1, n - 1)]).astype(np.int32))
+    assert st.num_blocks == n - 1
