@@ -64,6 +64,7 @@ def vs_paper(args, value):
 
 
 L2_BYTES = 129 * 1024 * 1024
+SERVE_BIG_STATES = 20000  # serving: LTSs with at least this many states are reduced alone
 
 
 def read_peaks():
@@ -326,16 +327,19 @@ def run_stream(args, world, rank, local):
         bisim.reduce(ltss[i], device=dev)
     plain_s = time.perf_counter() - t0
     plain_rate = len(sample) / plain_s
-    # serving loop at 0.5x, 1x and 2x the one-at-a-time rate
+    # serving loop at 0.5x to 20x the one-at-a-time rate; LTSs of at least
+    # SERVE_BIG_STATES states take the large-request lane (the single-LTS path)
     serving = {}
     if args.serve_requests > 0:
         sub = [ltss[i] for i in rng.choice(k, size=min(args.serve_requests, k), replace=False)]
-        for mult in (0.5, 1.0, 2.0):
+        for mult in (0.5, 1.0, 2.0, 5.0, 20.0):
             reqs = serve.poisson_requests(sub, rate_per_s=mult * plain_rate, seed=int(mult * 10))
             srv = serve.BatchServer(serve.gpu_executor(device=str(dev)), mem_budget=64 << 30, workers=3,
-                                    max_batch=256)
+                                    max_batch=256, big_executor=serve.gpu_single_executor(device=str(dev)),
+                                    big_states=SERVE_BIG_STATES)
             res = srv.serve(reqs)
-            serving[f"{mult}x"] = dict(serve.latency_summary(res), rate_per_s=mult * plain_rate)
+            serving[f"{mult}x"] = dict(serve.latency_summary(res), rate_per_s=mult * plain_rate,
+                                       large_lane=srv.big_served)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
@@ -414,7 +418,7 @@ def main():
     ap.add_argument("--stream-k", type=int, default=4096, help="LTSs in the stream workload")
     ap.add_argument("--plain-sample", type=int, default=128,
                     help="stream: LTSs reduced one at a time to estimate the plain rate")
-    ap.add_argument("--serve-requests", type=int, default=256,
+    ap.add_argument("--serve-requests", type=int, default=512,
                     help="stream: requests per arrival rate in the serving run")
     ap.add_argument("--engine", default="auto", choices=["auto", "dense", "frontier", "pair"])
     ap.add_argument("--threads", type=int, default=0, help="threads per CTA (0 = library default)")

@@ -269,7 +269,7 @@ class Plan:
             pass
 
 
-def reduce(lts, opts=None, device="cuda", return_stats=False):
+def reduce(lts, opts=None, device="cuda", return_stats=False, stream=None):
     """Coarsest bisimulation partition of an `lts_gen.LTS` on the GPU;
     returns a numpy int32 array of canonical block ids."""
     import torch
@@ -278,7 +278,7 @@ def reduce(lts, opts=None, device="cuda", return_stats=False):
         return None if a is None else torch.from_numpy(a).to(device)
 
     src, act, dst, init = dev(lts.src), dev(lts.act), dev(lts.dst), dev(lts.init)
-    with Plan(lts.n, lts.num_act, src, act, dst, init, opts) as p:
+    with Plan(lts.n, lts.num_act, src, act, dst, init, opts, stream=stream) as p:
         out, st = p.refine()
         res = out.cpu().numpy()
     return (res, st) if return_stats else res

@@ -10,6 +10,14 @@ running ones on the device (the batch kernel is an ordinary, non-cooperative
 launch). A request whose footprint alone exceeds the budget is admitted only
 when nothing else is in flight.
 
+With a large-request lane (`big_executor`, `big_states`), an LTS of at least
+`big_states` states that arrives while the lane holds fewer than `big_backlog`
+requests skips the batches and is reduced alone on its own stream by the
+single-LTS path, which spreads one LTS over the whole GPU, one such request
+at a time; inside a batch a large LTS runs on a single CTA and holds its
+batch back. When the lane is backed up, large requests join the batches, so
+that under heavy load they are reduced side by side instead of in a line.
+
 Results are canonical block ids, identical to what the one-at-a-time path
 returns for the same LTS. Latency is measured from a request's arrival to the
 moment its batch's results are on the host.
@@ -72,11 +80,35 @@ def gpu_executor(opts=None, device: str = "cuda"):
     return run
 
 
+def gpu_single_executor(opts=None, device: str = "cuda"):
+    """Executor reducing one LTS with the single-LTS path on the calling
+    thread's own CUDA stream."""
+    import torch
+
+    from . import bisim
+
+    local = threading.local()
+
+    def run(lts) -> np.ndarray:
+        if not hasattr(local, "stream"):
+            local.stream = torch.cuda.Stream(device=device)
+        with torch.cuda.stream(local.stream):
+            return bisim.reduce(lts, opts, device=device, stream=local.stream)
+
+    return run
+
+
 class BatchServer:
     def __init__(self, executor: Callable[[Sequence], List[np.ndarray]], mem_budget: int,
                  workers: int = 2, max_batch: int = 1024,
-                 footprint: Callable[[object], int] = lambda l: footprint_bytes(l.n, l.m)):
+                 footprint: Callable[[object], int] = lambda l: footprint_bytes(l.n, l.m),
+                 big_executor: Optional[Callable[[object], np.ndarray]] = None, big_states: int = 0,
+                 big_backlog: int = 2):
         self.executor = executor
+        self.big_executor = big_executor
+        self.big_states = int(big_states)
+        self.big_backlog = int(big_backlog)
+        self.big_served = 0
         self.mem_budget = int(mem_budget)
         self.workers = int(workers)
         self.max_batch = int(max_batch)
@@ -85,19 +117,27 @@ class BatchServer:
         self.batches = 0
         self.max_concurrent = 0
 
+    def _big(self, req: Request) -> bool:
+        return self.big_executor is not None and req.lts.n >= self.big_states
+
     def serve(self, requests: Sequence[Request], clock=time.perf_counter) -> List[Result]:
         pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
         queue: collections.deque = collections.deque()
+        big_queue: collections.deque = collections.deque()
         inflight = {}  # future -> (batch id, [requests], bytes, dispatch time)
+        big = None  # (future, request, bytes, dispatch time, batch id) of the large-request lane
         inflight_bytes = 0
         results: List[Result] = []
         t0 = clock()
-        with cf.ThreadPoolExecutor(max_workers=self.workers) as pool:
-            while pending or queue or inflight:
+        with cf.ThreadPoolExecutor(max_workers=self.workers) as pool, \
+                cf.ThreadPoolExecutor(max_workers=1) as big_pool:
+            while pending or queue or big_queue or inflight or big:
                 now = clock() - t0
                 while pending and pending[0].arrival <= now:
-                    queue.append(pending.popleft())
-                # retire finished batches
+                    r = pending.popleft()
+                    lane = self._big(r) and len(big_queue) + (big is not None) < self.big_backlog
+                    (big_queue if lane else queue).append(r)
+                # retire finished batches and the finished large request
                 for fut in [f for f in inflight if f.done()]:
                     bid, reqs, nbytes, tdisp = inflight.pop(fut)
                     parts = fut.result()
@@ -105,13 +145,28 @@ class BatchServer:
                     for r, lab in zip(reqs, parts):
                         results.append(Result(r.rid, lab, r.arrival, tdisp, tdone, bid))
                     inflight_bytes -= nbytes
+                if big is not None and big[0].done():
+                    fut, r, nbytes, tdisp, bid = big
+                    results.append(Result(r.rid, fut.result(), r.arrival, tdisp, clock() - t0, bid))
+                    inflight_bytes -= nbytes
+                    big = None
+                # the large-request lane: one at a time, within the memory budget
+                if big is None and big_queue:
+                    fp = self.footprint(big_queue[0].lts)
+                    if inflight_bytes + fp <= self.mem_budget or not inflight:
+                        r = big_queue.popleft()
+                        big = (big_pool.submit(self.big_executor, r.lts), r, fp, clock() - t0, self.batches)
+                        self.batches += 1
+                        self.big_served += 1
+                        inflight_bytes += fp
+                        self.max_inflight_bytes = max(self.max_inflight_bytes, inflight_bytes)
                 # admit: every arrived request that fits, while a worker is free
                 while queue and len(inflight) < self.workers:
                     batch, nbytes = [], 0
                     while queue and len(batch) < self.max_batch:
                         fp = self.footprint(queue[0].lts)
                         fits = inflight_bytes + nbytes + fp <= self.mem_budget
-                        alone = not batch and not inflight
+                        alone = not batch and not inflight and big is None
                         if not (fits or alone):
                             break
                         batch.append(queue.popleft())
@@ -124,13 +179,14 @@ class BatchServer:
                     self.batches += 1
                     inflight_bytes += nbytes
                     self.max_inflight_bytes = max(self.max_inflight_bytes, inflight_bytes)
-                    self.max_concurrent = max(self.max_concurrent, len(inflight))
+                    self.max_concurrent = max(self.max_concurrent, len(inflight) + (big is not None))
                 # sleep until the next arrival or a completion
                 timeout = 0.002
                 if pending:
                     timeout = max(0.0, min(timeout, pending[0].arrival - (clock() - t0)))
-                if inflight:
-                    cf.wait(list(inflight), timeout=timeout, return_when=cf.FIRST_COMPLETED)
+                waiting = list(inflight) + ([big[0]] if big is not None else [])
+                if waiting:
+                    cf.wait(waiting, timeout=timeout, return_when=cf.FIRST_COMPLETED)
                 elif timeout > 0:
                     time.sleep(timeout)
         results.sort(key=lambda r: r.rid)

@@ -66,3 +66,43 @@ def test_max_batch_is_respected():
     srv = serve.BatchServer(_fake_executor(calls), mem_budget=1 << 40, workers=1, max_batch=7)
     srv.serve(reqs)
     assert max(calls) <= 7 and sum(calls) == 25
+
+
+def test_large_requests_take_their_own_lane():
+    ltss = _stream(30, seed=9)
+    thr = sorted(l.n for l in ltss)[20]  # the ten largest (ties included) go to the lane
+    big_calls, calls = [], []
+
+    def big(lts):
+        big_calls.append(lts.n)
+        time.sleep(0.001)
+        return oracle.ks_lts(lts)
+
+    srv = serve.BatchServer(_fake_executor(calls), mem_budget=1 << 40, workers=2, big_executor=big,
+                            big_states=thr, big_backlog=1 << 30)
+    res = srv.serve(serve.poisson_requests(ltss, rate_per_s=1000.0, seed=2))
+    assert [r.rid for r in res] == list(range(30))
+    for r, l in zip(res, ltss):
+        assert r.labels.tolist() == oracle.ks_lts(l).tolist()
+    assert sorted(big_calls) == sorted(l.n for l in ltss if l.n >= thr)
+    assert sum(calls) == sum(1 for l in ltss if l.n < thr)
+    assert srv.big_served == len(big_calls)
+
+
+def test_backed_up_lane_sends_large_requests_to_the_batches():
+    ltss = _stream(30, seed=9)
+    thr = sorted(l.n for l in ltss)[20]
+    big_calls, calls = [], []
+
+    def big(lts):
+        big_calls.append(lts.n)
+        time.sleep(0.05)  # slow lane: arrivals back it up
+        return oracle.ks_lts(lts)
+
+    srv = serve.BatchServer(_fake_executor(calls), mem_budget=1 << 40, workers=2, big_executor=big,
+                            big_states=thr, big_backlog=1)
+    res = srv.serve([serve.Request(i, l, 0.0) for i, l in enumerate(ltss)])
+    assert [r.rid for r in res] == list(range(30))
+    for r, l in zip(res, ltss):
+        assert r.labels.tolist() == oracle.ks_lts(l).tolist()
+    assert len(big_calls) == 1 and sum(calls) == 29  # one lane slot, the rest batched
