@@ -244,6 +244,25 @@ int bisim_batch_refine(bisim_plan_t plan, int32_t* out_block, bisim_stats* stats
 int bisim_barrier_cost(int32_t ctas, int32_t threads, int32_t iters, void* stream,
                        double* ns_per_barrier);
 
+/*
+ * bisim_phase_times / bisim_phase_reset - diagnostic: per-phase device time of
+ * the frontier engine's hybrid rounds, accumulated over launches since the
+ * last reset by thread 0 of CTA 0 with the global timer. Only a library built
+ * with -DBISIM_PHASE_TIMERS records them; the default build returns
+ * BISIM_ENOTSUP (the paper has no counterpart; this is a profiling aid).
+ * out16: host array of 16 uint64 entries, nanoseconds unless noted:
+ *   0 selection, 1 publish to parked CTAs, 2 claim pass, 3 barrier after it,
+ *   4 mark pass, 5 barrier after it, 6 split pass, 7 barrier after it,
+ *   8 one-splitter grid rounds (whole round), 9 multi-splitter rounds (count),
+ *   10 one-splitter rounds (count), 11 rounds run by CTA 0 alone (count),
+ *   12 splitters selected by grid rounds (count), 13 their states (count),
+ *   14 touched blocks (count), 15 time between rounds.
+ * Both synchronise the device. Errors: BISIM_EINVAL (out16 NULL), BISIM_ECUDA,
+ * BISIM_ENOTSUP.
+ */
+int bisim_phase_times(uint64_t* out16);
+int bisim_phase_reset(void);
+
 /* Largest n accepted by bisim_canonical_ids_noalloc. */
 #define BISIM_NOALLOC_MAX_N (1 << 20)
 

@@ -103,16 +103,21 @@ def lib_path() -> str:
     return _build.LIB
 
 
-def load(build_if_missing: bool = False):
-    """Load libbisim.so (raises if it is missing and build_if_missing is False)."""
+def load(build_if_missing: bool = False, path: Optional[str] = None):
+    """Load libbisim.so (raises if it is missing and build_if_missing is False).
+    `path` selects another build of the same library (the phase-timer build)."""
     global _lib
     if _lib is not None:
+        if path is not None and getattr(_lib, "_path", None) != path:
+            raise RuntimeError("another build of libbisim is already loaded in this process")
         return _lib
-    if not os.path.exists(_build.LIB):
-        if not build_if_missing:
-            raise RuntimeError(f"libbisim.so not built ({_build.LIB}); run __graft_entry__.build()")
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing or path != _build.LIB:
+            raise RuntimeError(f"libbisim not built ({path}); run __graft_entry__.build()")
         _build.build()
-    lib = ctypes.CDLL(_build.LIB)
+    lib = ctypes.CDLL(path)
+    lib._path = path
     P, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
     lib.bisim_plan.argtypes = [i32, i64, i32, P, P, P, P, ctypes.POINTER(bisim_opts), P,
                                ctypes.POINTER(P)]
@@ -282,6 +287,28 @@ def reduce(lts, opts=None, device="cuda", return_stats=False, stream=None):
         out, st = p.refine()
         res = out.cpu().numpy()
     return (res, st) if return_stats else res
+
+
+PHASE_NAMES = ("select", "publish", "claim", "barrier_claim", "mark", "barrier_mark", "split",
+               "barrier_split", "single_rounds_ns", "multi_rounds", "single_rounds", "cta0_rounds",
+               "splitters", "splitter_states", "touched_blocks", "between_rounds")
+
+
+def bisim_phase_reset():
+    f = load().bisim_phase_reset
+    f.argtypes = []
+    f.restype = ctypes.c_int
+    _check(f(), "bisim_phase_reset")
+
+
+def bisim_phase_times() -> dict:
+    """Accumulated phase slots of a phase-timer build (see include/bisim.h)."""
+    f = load().bisim_phase_times
+    f.argtypes = [ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    buf = (ctypes.c_uint64 * 16)()
+    _check(f(ctypes.addressof(buf)), "bisim_phase_times")
+    return {k: int(v) for k, v in zip(PHASE_NAMES, buf)}
 
 
 def bisim_canonical_ids_noalloc(labels: int, n: int, out_ids: int, stream: int = 0) -> int:

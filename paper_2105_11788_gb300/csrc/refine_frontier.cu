@@ -28,6 +28,51 @@
 
 using namespace bisim;
 
+// Phase timers of the hybrid kernel (diagnostic build only, -DBISIM_PHASE_TIMERS):
+// thread 0 of CTA 0 adds the global-timer time of each phase of a round, and
+// a few counts, to slots of a shared array that the kernel adds to
+// g_phase_acc at exit. Slots: 0 selection, 1 publish, 2 claim, 3 barrier
+// after claim, 4 mark, 5 barrier after mark, 6 split, 7 barrier after split,
+// 8 one-splitter rounds (whole round), 9 multi-splitter rounds, 10
+// one-splitter rounds, 11 rounds on CTA 0 alone, 12 splitters selected, 13
+// their states, 14 touched blocks, 15 time between rounds.
+#ifdef BISIM_PHASE_TIMERS
+__device__ unsigned long long g_phase_acc[16];
+__device__ __forceinline__ unsigned long long* phase_slots() {
+    __shared__ unsigned long long s[17];  // [16] holds the time of the last mark
+    return s;
+}
+#define PHASE_RESET()                                                         \
+    do {                                                                      \
+        if (threadIdx.x == 0) {                                               \
+            for (int i_ = 0; i_ < 16; i_++) phase_slots()[i_] = 0;            \
+            phase_slots()[16] = globaltimer_ns();                             \
+        }                                                                     \
+    } while (0)
+#define PHASE(i)                                                              \
+    do {                                                                      \
+        if (blockIdx.x == 0 && threadIdx.x == 0) {                            \
+            const unsigned long long t_ = globaltimer_ns();                   \
+            phase_slots()[i] += t_ - phase_slots()[16];                       \
+            phase_slots()[16] = t_;                                           \
+        }                                                                     \
+    } while (0)
+#define PHASE_ADD(i, v)                                                       \
+    do {                                                                      \
+        if (blockIdx.x == 0 && threadIdx.x == 0) phase_slots()[i] += (v);     \
+    } while (0)
+#define PHASE_FLUSH()                                                         \
+    do {                                                                      \
+        if (blockIdx.x == 0 && threadIdx.x == 0)                              \
+            for (int i_ = 0; i_ < 16; i_++) atomicAdd(&g_phase_acc[i_], phase_slots()[i_]); \
+    } while (0)
+#else
+#define PHASE_RESET() do {} while (0)
+#define PHASE(i) do {} while (0)
+#define PHASE_ADD(i, v) do {} while (0)
+#define PHASE_FLUSH() do {} while (0)
+#endif
+
 namespace {
 
 constexpr int WARP_MAX = 64;  // blocks up to this size are split by one warp
@@ -972,18 +1017,28 @@ __device__ __forceinline__ bool multi_round(const FrontierArgs& a, const Worklis
     if (selP[K] <= nwarps) {
         ItemCarry ic;
         claim_item(a, selC, selP, K, lost, stamp, gw, ic);
+        PHASE(2);
         if (!sync()) return false;
+        PHASE(3);
         mark_item(a, wl, selP, lost, stamp, gw, ic, n_small, n_mid, small_list, mid_list, edges, commits);
     } else {
         claim_step(a, selC, selP, K, lost, stamp, gw, nwarps);
+        PHASE(2);
         if (!sync()) return false;
+        PHASE(3);
         mark_many(a, wl, selC, selP, K, lost, stamp, gw, nwarps, n_small, n_mid, small_list, mid_list, edges,
                   commits);
     }
+    PHASE(4);
     if (!sync()) return false;
-    split_step(a, wl, sh, defer, ndefer, stamp, MULTI, ld_volatile_i32(n_small), small_list, ld_volatile_i32(n_mid),
-               mid_list, cta, ncta, states);
-    return sync();
+    PHASE(5);
+    const int ns = ld_volatile_i32(n_small), nm = ld_volatile_i32(n_mid);
+    PHASE_ADD(14, (unsigned long long)(ns + nm));
+    split_step(a, wl, sh, defer, ndefer, stamp, MULTI, ns, small_list, nm, mid_list, cta, ncta, states);
+    PHASE(6);
+    const bool ok = sync();
+    PHASE(7);
+    return ok;
 }
 
 // Hybrid schedule for one LTS. A round of one light splitter (at most 32
@@ -1043,6 +1098,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_frontier_hybrid(FrontierArgs a, Hyb
     };
     if (threadIdx.x < BISIM_BUCKETS) sh.head[threadIdx.x] = 0;
     if (threadIdx.x < 32) s_lost[threadIdx.x] = 0u;
+    PHASE_RESET();
     __syncthreads();
     bool in_step = true;  // the other CTAs follow the selection (CTA 0: they are not parked)
     unsigned long long seen = 0;
@@ -1106,6 +1162,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_frontier_hybrid(FrontierArgs a, Hyb
             in_step = true;
             continue;
         }
+        PHASE(15);
         r++;
         const uint32_t stamp = a.stamp0 + (uint32_t)r;
         const int par = (int)(r & 1);
@@ -1118,6 +1175,8 @@ __global__ void __launch_bounds__(MAXT, 1) k_frontier_hybrid(FrontierArgs a, Hyb
             C = select_splitter(wl, sh.head, sh);
             K = C >= 0 ? 1 : 0;
         }
+        PHASE(0);
+        PHASE_ADD(K > 1 ? 9 : 10, K > 0 ? 1ull : 0ull);
         if (K > 0 && r > a.round_cap) {
             if (lead && threadIdx.x == 0) atomicOr(&c->status, ST_ROUNDS);
             K = 0;
@@ -1171,6 +1230,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_frontier_hybrid(FrontierArgs a, Hyb
                 s_ns = 0;
                 s_nm = 0;
             }
+            PHASE_ADD(11, 1ull);
             __syncthreads();
             if (K > 1) {
                 multi_round(a, wl, sh, s_defer, &s_ndefer, s_selC, s_selP, K, s_lost, stamp, wid, nw, &s_ns, &s_nm,
@@ -1204,8 +1264,15 @@ __global__ void __launch_bounds__(MAXT, 1) k_frontier_hybrid(FrontierArgs a, Hyb
             }
         }
         in_step = true;
+        PHASE(1);
+        if (K > 1) {
+            PHASE_ADD(12, (unsigned long long)K);
+            PHASE_ADD(13, (unsigned long long)s_selP[K]);
+        }
         if (!grid_round(K, C, stamp, par)) return;
+        if (K == 1) PHASE(8);
     }
+    PHASE_FLUSH();
     if (edges) atomicAdd((unsigned long long*)&c->edges, (unsigned long long)edges);
     if (states) atomicAdd((unsigned long long*)&c->states, (unsigned long long)states);
     if (commits) atomicAdd((unsigned long long*)&c->commits, (unsigned long long)commits);
@@ -1612,3 +1679,32 @@ int refine_frontier_batch(bisim_plan_s* p, bisim_stats* stats, std::vector<long 
 }
 
 }  // namespace bisim
+
+extern "C" {
+
+int bisim_phase_times(uint64_t* out16) {
+#ifdef BISIM_PHASE_TIMERS
+    if (!out16) return BISIM_EINVAL;
+    BISIM_CUDA_TRY(cudaDeviceSynchronize());
+    BISIM_CUDA_TRY(cudaMemcpyFromSymbol(out16, g_phase_acc, sizeof(g_phase_acc)));
+    return BISIM_OK;
+#else
+    (void)out16;
+    set_last_error("built without BISIM_PHASE_TIMERS");
+    return BISIM_ENOTSUP;
+#endif
+}
+
+int bisim_phase_reset(void) {
+#ifdef BISIM_PHASE_TIMERS
+    unsigned long long z[16] = {0};
+    BISIM_CUDA_TRY(cudaDeviceSynchronize());
+    BISIM_CUDA_TRY(cudaMemcpyToSymbol(g_phase_acc, z, sizeof(z)));
+    return BISIM_OK;
+#else
+    set_last_error("built without BISIM_PHASE_TIMERS");
+    return BISIM_ENOTSUP;
+#endif
+}
+
+}  // extern "C"

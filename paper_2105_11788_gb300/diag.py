@@ -4,6 +4,8 @@
     python -m paper_2105_11788_gb300.diag shapes         # main-loop time per launch shape
     python -m paper_2105_11788_gb300.diag splitters      # splitters per round / state budget sweep
     python -m paper_2105_11788_gb300.diag fanout         # Fan_out_n scaling, closed form checked
+    python -m paper_2105_11788_gb300.diag phases         # per-phase time of the hybrid rounds
+                                                         # (builds the phase-timer library)
 
 Each prints JSON lines.
 """
@@ -88,12 +90,39 @@ def fanout(sizes=(10, 100, 200, 300, 400, 500, 600, 700, 10_000, 100_000, 1_000_
                               "steps": st.steps, "closed_form": bool(np.array_equal(got, want))}), flush=True)
 
 
+def phases(workloads=("qexp", "powerlaw2m", "kripke"), repeats: int = 2):
+    """Per-phase time of the hybrid rounds (phase-timer build of the library):
+    microseconds per multi-splitter round for each phase, and the counts."""
+    for wl in workloads:
+        lts = WORKLOADS[wl]()
+        bisim.reduce(lts)  # warm-up
+        bisim.bisim_phase_reset()
+        best = None
+        for _ in range(repeats):
+            _, st = bisim.reduce(lts, return_stats=True)
+            best = st.t_main_ms if best is None else min(best, st.t_main_ms)
+        ph = bisim.bisim_phase_times()
+        rounds = max(ph["multi_rounds"], 1)
+        per_round = {k: ph[k] / 1e3 / rounds for k in ("select", "publish", "claim", "barrier_claim", "mark",
+                                                        "barrier_mark", "split", "barrier_split")}
+        print(json.dumps({"workload": wl, "main_ms": best, "rounds": st.rounds, "steps": st.steps,
+                          "us_per_multi_round": per_round, "counts_over_runs": {
+                              k: ph[k] for k in ("multi_rounds", "single_rounds", "cta0_rounds", "splitters",
+                                                 "splitter_states", "touched_blocks")}}), flush=True)
+
+
 def main(argv):
     import torch
 
     torch.cuda.init()
-    bisim.load(build_if_missing=True)
     what = argv[1] if len(argv) > 1 else "barrier"
+    if what == "phases":
+        from . import _build
+
+        bisim.load(path=_build.build_phase())
+        phases(tuple(argv[2:]) or ("qexp", "powerlaw2m", "kripke"))
+        return
+    bisim.load(build_if_missing=True)
     if what == "barrier":
         barrier()
     elif what == "shapes":
