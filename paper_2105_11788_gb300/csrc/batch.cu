@@ -31,43 +31,89 @@ __device__ __forceinline__ int find_range(const int64_t* __restrict__ off, int k
     return lo;
 }
 
+// Element ranges of the LTSs (transitions or states), tile by tile: a tile
+// of TILE consecutive elements looks up the ranges it meets once (thread 0,
+// binary search) and keeps their offsets in shared memory; each element then
+// finds its range there. A tile that meets more than TILE_RANGES ranges (many
+// tiny or empty LTSs) searches the global offsets per element instead.
+constexpr int TILE = 2048;
+constexpr int TILE_RANGES = 64;
+
+struct TileRanges {
+    int l0, cnt;  // ranges l0 .. l0 + cnt - 1; cnt = 0: use the global offsets
+    int64_t off[TILE_RANGES];
+};
+
+__device__ __forceinline__ void tile_ranges(const int64_t* __restrict__ off, int k, int64_t i0, int64_t i1,
+                                            TileRanges& tr) {
+    __syncthreads();  // the previous tile's lookups are done
+    if (threadIdx.x == 0) {
+        const int l0 = find_range(off, k, i0), l1 = find_range(off, k, i1 - 1);
+        tr.l0 = l0;
+        tr.cnt = l1 - l0 + 1 <= TILE_RANGES ? l1 - l0 + 1 : 0;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < tr.cnt; j += blockDim.x) tr.off[j] = off[tr.l0 + j];
+    __syncthreads();
+}
+
+__device__ __forceinline__ int range_of(const int64_t* __restrict__ off, int k, const TileRanges& tr, int64_t i) {
+    if (tr.cnt == 0) return find_range(off, k, i);
+    int lo = 0, hi = tr.cnt - 1;  // largest j with off[l0 + j] <= i
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tr.off[mid] <= i) lo = mid;
+        else hi = mid - 1;
+    }
+    return tr.l0 + lo;
+}
+
 // local (state, label) ids -> union ids, with range checks per LTS
 __global__ void k_batch_union(int k, const int64_t* __restrict__ state_off, const int64_t* __restrict__ trans_off,
                               const int32_t* __restrict__ num_act, const int32_t* __restrict__ src,
                               const int32_t* __restrict__ act, const int32_t* __restrict__ dst,
                               const int32_t* __restrict__ init, int64_t M, int64_t N, int32_t* usrc,
                               int32_t* uact, int32_t* udst, int32_t* uinit, int* status) {
-    const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
+    __shared__ TileRanges tr;
     int bad = 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gsz) {
-        const int li = find_range(trans_off, k, i);
-        const int64_t s0 = state_off[li];
-        const int64_t ni = state_off[li + 1] - s0;
-        const int32_t s = src[i], d = dst[i], a = act ? act[i] : 0;
-        if ((int64_t)(unsigned)s >= ni || (int64_t)(unsigned)d >= ni || (unsigned)a >= (unsigned)num_act[li]) {
-            bad = 1;
-            usrc[i] = 0;
-            udst[i] = 0;
-            uact[i] = 0;
-        } else {
-            usrc[i] = (int32_t)(s0 + s);
-            udst[i] = (int32_t)(s0 + d);
-            uact[i] = a;
+    const int64_t tiles_m = (M + TILE - 1) / TILE, tiles_n = (N + TILE - 1) / TILE;
+    for (int64_t t = blockIdx.x; t < tiles_m + tiles_n; t += gridDim.x) {
+        const bool trans = t < tiles_m;
+        const int64_t i0 = (trans ? t : t - tiles_m) * TILE;
+        const int64_t i1 = min(i0 + TILE, trans ? M : N);
+        tile_ranges(trans ? trans_off : state_off, k, i0, i1, tr);
+        for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+            if (trans) {
+                const int li = range_of(trans_off, k, tr, i);
+                const int64_t s0 = state_off[li];
+                const int64_t ni = state_off[li + 1] - s0;
+                const int32_t s = src[i], d = dst[i], a = act ? act[i] : 0;
+                if ((int64_t)(unsigned)s >= ni || (int64_t)(unsigned)d >= ni ||
+                    (unsigned)a >= (unsigned)num_act[li]) {
+                    bad = 1;
+                    usrc[i] = 0;
+                    udst[i] = 0;
+                    uact[i] = 0;
+                } else {
+                    usrc[i] = (int32_t)(s0 + s);
+                    udst[i] = (int32_t)(s0 + d);
+                    uact[i] = a;
+                }
+            } else {
+                const int li = range_of(state_off, k, tr, i);
+                const int64_t s0 = state_off[li];
+                const int64_t ni = state_off[li + 1] - s0;
+                const int32_t v = init ? init[i] : 0;
+                if ((int64_t)(unsigned)v >= ni) {
+                    bad = 1;
+                    uinit[i] = (int32_t)s0;
+                } else {
+                    uinit[i] = (int32_t)(s0 + v);
+                }
+            }
         }
     }
-    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < N; x += gsz) {
-        const int li = find_range(state_off, k, x);
-        const int64_t s0 = state_off[li];
-        const int64_t ni = state_off[li + 1] - s0;
-        const int32_t v = init ? init[x] : 0;
-        if ((int64_t)(unsigned)v >= ni) {
-            bad = 1;
-            uinit[x] = (int32_t)s0;
-        } else {
-            uinit[x] = (int32_t)(s0 + v);
-        }
-    }
-    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, ST_INVALID);
+    if (bad) atomicOr(status, ST_INVALID);
 }
 
 // union canonical ids -> ids local to each LTS (the first state of every LTS
@@ -78,14 +124,34 @@ __global__ void k_batch_base(int k, const int64_t* __restrict__ state_off, const
         base[i] = state_off[i + 1] > state_off[i] ? out[state_off[i]] : 0;
 }
 
+// local ids and the block count of every LTS (largest local id + 1; one
+// atomicMax per group of lanes of a warp that hold states of the same LTS)
 __global__ void k_batch_local(int k, const int64_t* __restrict__ state_off, const int32_t* __restrict__ base,
                               int64_t N, int32_t* out, int32_t* nblocks) {
-    const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < N; x += gsz) {
-        const int li = find_range(state_off, k, x);
-        const int32_t v = out[x] - base[li];
-        out[x] = v;
-        atomicMax(&nblocks[li], v + 1);
+    __shared__ TileRanges tr;
+    const unsigned lane = threadIdx.x & 31u;
+    for (int64_t t = blockIdx.x; t * TILE < N; t += gridDim.x) {
+        const int64_t i0 = t * TILE, i1 = min(i0 + TILE, N);
+        tile_ranges(state_off, k, i0, i1, tr);
+        // trip count rounded up to whole warps so that every lane reaches the match
+        for (int64_t i = i0 + threadIdx.x; i - lane < i1; i += blockDim.x) {
+            int li = -1 - (int)lane, v = 0;
+            if (i < i1) {
+                li = range_of(state_off, k, tr, i);
+                v = out[i] - base[li];
+                out[i] = v;
+            }
+            // lanes hold consecutive states, so the lanes of one LTS are a
+            // contiguous run: a suffix max leaves the run's max at its lowest lane
+            const unsigned peers = __match_any_sync(0xffffffffu, li);
+            int mx = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_down_sync(0xffffffffu, mx, o);
+                if (lane + o < 32u && ((peers >> (lane + o)) & 1u)) mx = max(mx, y);
+            }
+            if (li >= 0 && (peers & lanemask_lt()) == 0u) atomicMax(&nblocks[li], mx + 1);
+        }
     }
 }
 
@@ -133,7 +199,8 @@ int batch_plan_build(bisim_plan_s* p, int32_t k, const int64_t* state_off_h, con
     BISIM_TRY(uinit.alloc(4 * (size_t)N, st));
     BISIM_TRY(p->ctrl.alloc(sizeof(bisim_ctrl), st));
     BISIM_CUDA_TRY(cudaMemsetAsync(p->ctrl.p, 0, sizeof(bisim_ctrl), st));
-    k_batch_union<<<grid_for(std::max(M, N), T), T, 0, st>>>(
+    k_batch_union<<<(unsigned)std::min<int64_t>((M + TILE - 1) / TILE + (N + TILE - 1) / TILE, 1 << 20), T, 0,
+                    st>>>(
         k, p->state_off.as<int64_t>(), toff.as<int64_t>(), p->batch_act.as<int32_t>(), src, act, dst, init, M, N,
         usrc.as<int32_t>(), uact.as<int32_t>(), udst.as<int32_t>(), uinit.as<int32_t>(),
         &p->ctrl.as<bisim_ctrl>()->status);
@@ -244,8 +311,8 @@ int bisim_batch_refine(bisim_plan_t p, int32_t* out_block, bisim_stats* stats, b
         BISIM_CUDA_TRY(cudaMemsetAsync(nbd.p, 0, 4 * (size_t)k, st));
         k_batch_base<<<grid_for(k, T), T, 0, st>>>(k, p->state_off.as<int64_t>(), out_block, base.as<int32_t>());
         BISIM_LAUNCHED();
-        k_batch_local<<<grid_for(p->n, T), T, 0, st>>>(k, p->state_off.as<int64_t>(), base.as<int32_t>(), p->n,
-                                                       out_block, nbd.as<int32_t>());
+        k_batch_local<<<(unsigned)std::min<int64_t>(((int64_t)p->n + TILE - 1) / TILE, 1 << 20), T, 0, st>>>(
+            k, p->state_off.as<int64_t>(), base.as<int32_t>(), p->n, out_block, nbd.as<int32_t>());
         BISIM_LAUNCHED();
         BISIM_CUDA_TRY(cudaGetLastError());
         BISIM_CUDA_TRY(cudaMemcpyAsync(nb.data(), nbd.p, 4 * (size_t)k, cudaMemcpyDeviceToHost, st));

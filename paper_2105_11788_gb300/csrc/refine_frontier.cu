@@ -1414,17 +1414,24 @@ __global__ void k_front_ranges(const uint32_t* __restrict__ skeys, const int32_t
     }
 }
 
-// initial worklist: every label, in the bucket of its block size
+// initial worklist: every label, in the bucket of its block size (one
+// atomicAdd per bucket and warp; the lanes of a bucket take consecutive slots)
 __global__ void k_front_queue(const uint32_t* __restrict__ flags, const int32_t* __restrict__ bbeg,
                               const int32_t* __restrict__ bend, int32_t n, bisim_ctrl* ctrl,
                               int32_t* queue) {
     const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gsz)
-        if (flags[i]) {
-            const int bk = size_bucket(bend[i] - bbeg[i]);
-            const unsigned long long pos = atomicAdd(&ctrl->bq_tail[bk], 1ull);
-            queue[(size_t)bk * n + pos] = (int32_t)i;
-        }
+    const int lane = (int)(threadIdx.x & 31);
+    // trip count rounded up to whole warps so that every lane reaches the match
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i - lane < n; i += gsz) {
+        const bool has = i < n && flags[i];
+        const int bk = has ? size_bucket(bend[i] - bbeg[i]) : 32 + lane;
+        const unsigned peers = __match_any_sync(0xffffffffu, bk);
+        const int first = __ffs(peers) - 1;
+        unsigned long long base = 0;
+        if (has && lane == first) base = atomicAdd(&ctrl->bq_tail[bk], (unsigned long long)__popc(peers));
+        base = __shfl_sync(0xffffffffu, base, first);
+        if (has) queue[(size_t)bk * n + base + __popc(peers & lanemask_lt())] = (int32_t)i;
+    }
 }
 
 int ensure_frontier(bisim_plan_s* p) {
