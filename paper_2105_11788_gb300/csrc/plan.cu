@@ -155,7 +155,7 @@ struct LabelArgs {
 // round of label a is "s has an a-transition": read from the state's label
 // bitmask when there is one (two grid barriers per round), else written by
 // one thread per mark slot (three).
-__global__ void k_label_rounds(LabelArgs a) {
+__global__ void __launch_bounds__(512, 4) k_label_rounds(LabelArgs a) {  // launched with 512 threads
     const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
     unsigned long long tgt = 0;
@@ -202,12 +202,35 @@ __global__ void k_label_rounds(LabelArgs a) {
                 // lanes hold consecutive states: the lowest lane of each group of
                 // splitting states with the same block holds the group's minimum
                 const unsigned peers = __match_any_sync(0xffffffffu, sp ? b[u] : -1);
-                if (sp && (peers & lanemask_lt()) == 0u) atomicMin(&a.nl64[b[u]], elect_key(stamp, (int32_t)s));
+                if (sp && (peers & lanemask_lt()) == 0u) {
+                    // early rounds split a few huge blocks: skip the atomic when
+                    // the election word already holds a smaller key
+                    // (a cached, possibly stale read is enough: election words
+                    // only drop within a round, and older rounds' keys are larger)
+                    const unsigned long long key = elect_key(stamp, (int32_t)s);
+                    if (a.nl64[b[u]] > key) atomicMin(&a.nl64[b[u]], key);
+                }
             }
         }
         if (!grid_sync(a.gb, tgt)) return;
-        for (int64_t s = gtid; s < a.n; s += gsz)
-            if (a.split[s]) a.block[s] = (int32_t)(uint32_t)ldcg(&a.nl64[a.block[s]]);
+        // relabel: each level of loads (flags, blocks, election words) of the
+        // thread's four states is issued together
+        for (int64_t s0 = gtid; s0 < a.n; s0 += 4 * gsz) {
+            uint8_t f[4];
+            int32_t bb[4];
+            uint32_t v[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) f[u] = s0 + u * gsz < a.n ? ldcg(&a.split[s0 + u * gsz]) : (uint8_t)0;
+#pragma unroll
+            for (int u = 0; u < 4; u++) bb[u] = f[u] ? a.block[s0 + u * gsz] : 0;
+            // after the barrier's acquire, cached loads of the election words see
+            // their final values; they keep the few words of big blocks in L1
+#pragma unroll
+            for (int u = 0; u < 4; u++) v[u] = f[u] ? (uint32_t)a.nl64[bb[u]] : 0u;
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+                if (f[u]) a.block[s0 + u * gsz] = (int32_t)v[u];
+        }
         if (!grid_sync(a.gb, tgt)) return;
     }
 }

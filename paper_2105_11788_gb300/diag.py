@@ -4,6 +4,7 @@
     python -m paper_2105_11788_gb300.diag shapes         # main-loop time per launch shape
     python -m paper_2105_11788_gb300.diag splitters      # splitters per round / state budget sweep
     python -m paper_2105_11788_gb300.diag fanout         # Fan_out_n scaling, closed form checked
+    python -m paper_2105_11788_gb300.diag hbm [n]        # HBM-bound rounds (label, dense) vs peak
     python -m paper_2105_11788_gb300.diag phases         # per-phase time of the hybrid rounds
                                                          # (builds the phase-timer library)
 
@@ -111,6 +112,56 @@ def phases(workloads=("qexp", "powerlaw2m", "kripke"), repeats: int = 2):
                                                  "splitter_states", "touched_blocks")}}), flush=True)
 
 
+def _hbm_peak():
+    import os
+
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
+def hbm(window: int = 200, repeats: int = 3, n: int = 10_000_000):
+    """The bandwidth-bound rounds of the paper's method on the 10^7-state
+    power-law LTS: the literal action-set preprocessing rounds (one pass over
+    the states per label) and a window of `window` dense main rounds (every
+    round scans all states and mark slots; the window ends with the round cap,
+    BISIM_EROUNDS, since the whole dense run takes ~10^7 rounds). Achieved
+    GB/s of algorithmic bytes against the HBM peak:
+      label round: 14 B per state (block, own and leader's label-set word,
+                   split flag written and read);
+      dense round: 30 B per state + 8 B per mark slot, plus 12 B per walked
+                   incoming transition."""
+    import ctypes
+
+    import torch
+
+    peak, kind = _hbm_peak()
+    lts = lts_gen.powerlaw(seed=3, n=n)
+    d = lambda a: torch.from_numpy(a).cuda()  # noqa: E731
+    src, act, dst, init = d(lts.src), d(lts.act), d(lts.dst), d(lts.init)
+    out = torch.empty(lts.n, dtype=torch.int32, device="cuda")
+    lib = bisim.load()
+    for rep in range(repeats):
+        opts = bisim.make_opts(engine=bisim.ENGINE_DENSE, preprocess=1, round_cap=window)
+        with bisim.Plan(lts.n, lts.num_act, src, act, dst, init, opts) as p:
+            st = bisim.bisim_stats()
+            rc = lib.bisim_refine(p.handle, out.data_ptr(), ctypes.byref(st))
+        label_bytes = 14.0 * st.n * st.pre_rounds
+        dense_bytes = st.rounds * (30.0 * st.n + 8.0 * st.mark_length) + 12.0 * st.edges_visited
+        print(json.dumps({
+            "workload": f"powerlaw n={n}", "rep": rep, "peak_gbs": peak, "peak_kind": kind,
+            "label_rounds": {"rounds": st.pre_rounds, "ms": st.t_pre_ms, "bytes": label_bytes,
+                             "gbs": label_bytes / (st.t_pre_ms * 1e6), "frac": label_bytes / (st.t_pre_ms * 1e6) / peak},
+            "dense_window": {"rounds": st.rounds, "ms": st.t_main_ms, "bytes": dense_bytes,
+                             "gbs": dense_bytes / (st.t_main_ms * 1e6),
+                             "frac": dense_bytes / (st.t_main_ms * 1e6) / peak,
+                             "us_per_round": 1e3 * st.t_main_ms / max(st.rounds, 1),
+                             "ended_by_round_cap": rc == bisim.BISIM_EROUNDS}}), flush=True)
+
+
 def main(argv):
     import torch
 
@@ -129,6 +180,8 @@ def main(argv):
         shapes(tuple(argv[2:]) or ("kripke", "qexp", "chain"))
     elif what == "fanout":
         fanout()
+    elif what == "hbm":
+        hbm(n=int(argv[2]) if len(argv) > 2 else 10_000_000)
     elif what == "splitters":
         splitters(tuple(argv[2:]) or ("qexp", "powerlaw2m"))
     else:
