@@ -368,6 +368,7 @@ def run_stream(args, world, rank, local):
                        "threads": opts.threads, "ctas_per_sm": opts.ctas_per_sm,
                        "wide_threads": opts.wide_threads, "wide_min_states": opts.wide_min_states,
                        "splitters": opts.splitters, "split_budget": opts.split_budget,
+                       "multi_min_states": opts.multi_min_states,
                        "autotune": tuned,
                        "l2": "inputs larger than L2",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},

@@ -101,7 +101,8 @@ typedef struct bisim_opts {
     int32_t split_budget;    /* frontier engine, rounds with several splitters: at most
                                 this many splitter states per warp (0 = 1 on the grid,
                                 8 per CTA of a batch) */
-    int32_t reserved;
+    int32_t multi_min_states; /* batch: only LTSs with at least this many states take
+                                 several splitters per round (0 = every LTS) */
 } bisim_opts;
 
 typedef struct bisim_stats {

@@ -26,18 +26,19 @@ import numpy as np
 
 from . import bisim
 
-# (threads, ctas_per_sm, wide_threads, wide_min_states, splitters, split_budget)
-CANDIDATES: Tuple[Tuple[int, int, int, int, int, int], ...] = (
-    (128, 0, 0, 0, 1, 0), (256, 0, 0, 0, 1, 0), (512, 0, 0, 0, 1, 0),
-    (256, 0, 1024, 1 << 15, 1, 0), (128, 0, 1024, 1 << 15, 1, 0),
-    (128, 0, 0, 0, 16, 1), (256, 0, 0, 0, 16, 1), (256, 0, 0, 0, 64, 2), (512, 0, 0, 0, 64, 1),
-    (256, 0, 1024, 1 << 15, 64, 1),
+# (threads, ctas_per_sm, wide_threads, wide_min_states, splitters, split_budget, multi_min_states)
+CANDIDATES: Tuple[Tuple[int, int, int, int, int, int, int], ...] = (
+    (128, 0, 0, 0, 1, 0, 0), (256, 0, 0, 0, 1, 0, 0), (512, 0, 0, 0, 1, 0, 0),
+    (256, 0, 1024, 1 << 15, 1, 0, 0),
+    (256, 0, 0, 0, 16, 1, 0), (256, 0, 0, 0, 64, 2, 0),
+    (512, 0, 0, 0, 16, 8, 50000), (256, 0, 0, 0, 16, 4, 20000),
 )
-KEYS = ("threads", "ctas_per_sm", "wide_threads", "wide_min_states", "splitters", "split_budget")
+KEYS = ("threads", "ctas_per_sm", "wide_threads", "wide_min_states", "splitters", "split_budget",
+        "multi_min_states")
 
 
 def _name(c) -> str:
-    return "t{}x{}+w{}@{}+s{}b{}".format(*c)
+    return "t{}x{}+w{}@{}+s{}b{}m{}".format(*c)
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "bisim_gb300_autotune.json")
 
 

@@ -1294,6 +1294,7 @@ struct BatchArgs {
     int32_t* block0;
     int kmax;                               // most splitters per round (1: one per round)
     int budget_per_warp;                    // states of a round's splitters per warp at most
+    int multi_min_states;                   // smaller LTSs take one splitter per round
 };
 
 __global__ void __launch_bounds__(1024) k_frontier_batch(FrontierArgs a, BatchArgs bt) {
@@ -1333,6 +1334,7 @@ __global__ void __launch_bounds__(1024) k_frontier_batch(FrontierArgs a, BatchAr
             if (bt.block0[l] == l) push(a, wl, l);
         __syncthreads();
         const int64_t cap = 3ll * ni + bt.num_act[li] + 2;
+        const int kmax_i = ni >= bt.multi_min_states ? kmax : 1;
         int64_t r = 0;
         long long commits = 0;
         for (;;) {
@@ -1340,8 +1342,8 @@ __global__ void __launch_bounds__(1024) k_frontier_batch(FrontierArgs a, BatchAr
             const uint32_t stamp = a.stamp0 + (uint32_t)r;
             int K;
             int32_t C;
-            if (kmax > 1) {
-                K = select_many(a, wl, sh.head, sh, s_selC, s_selP, kmax, budget);
+            if (kmax_i > 1) {
+                K = select_many(a, wl, sh.head, sh, s_selC, s_selP, kmax_i, budget);
                 C = K > 0 ? s_selC[0] : -1;
             } else {
                 C = select_splitter(wl, sh.head, sh);
@@ -1617,6 +1619,7 @@ int refine_frontier_batch(bisim_plan_s* p, bisim_stats* stats, std::vector<long 
     bt.block0 = p->block0.as<int32_t>();
     bt.kmax = p->opts.splitters > 0 ? std::min(p->opts.splitters, BISIM_KMAX_CTA) : 1;
     bt.budget_per_warp = p->opts.split_budget > 0 ? std::min(p->opts.split_budget, 1 << 20) : 8;
+    bt.multi_min_states = std::max(p->opts.multi_min_states, 0);
     const int threads = p->opts.threads > 0 ? p->opts.threads : 256;
     // optional split schedule: the LTSs with at least wide_min_states states
     // (a prefix of the largest-first order) run in a second launch of wide

@@ -118,14 +118,16 @@ def test_split_schedule_matches_single_launch():
         assert g.tolist() == oracle.ks_lts(l).tolist()
 
 
-@pytest.mark.parametrize("splitters", [1, 4, 0], ids=["one", "four", "default"])
-def test_batch_several_splitters_per_round(splitters):
+@pytest.mark.parametrize("splitters,multi_min", [(1, 0), (4, 0), (0, 0), (16, 3000)],
+                         ids=["one", "four", "default", "large-only"])
+def test_batch_several_splitters_per_round(splitters, multi_min):
     """CTA rounds with several splitters: oracle partitions, identical to one
     splitter per round, and the per-LTS iteration bounds hold."""
     rng = np.random.default_rng(77)
     ltss = [lts_gen.stream_instance(rng, n_lo=100, n_hi=8000, idx=i) for i in range(40)]
     ltss += _random_batch(12, 60)
-    parts, st, inst = bisim.reduce_batch(ltss, bisim.make_opts(splitters=splitters), return_stats=True)
+    parts, st, inst = bisim.reduce_batch(ltss, bisim.make_opts(splitters=splitters, split_budget=8 if multi_min else 0,
+                                                               multi_min_states=multi_min), return_stats=True)
     for i, (l, got) in enumerate(zip(ltss, parts)):
         want = oracle.ks_lts(l)
         assert got.tolist() == want.tolist(), i
