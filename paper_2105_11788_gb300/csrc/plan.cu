@@ -24,20 +24,34 @@ namespace {
 
 constexpr int T = 256;
 
+// The transition arrays are read as int4 (four transitions per load) when
+// all of them start on a 16-byte boundary; `vec` says so (checked on the
+// host), and the last m % 4 transitions, or all of them otherwise, are read
+// one by one.
+__device__ __forceinline__ int4 ld4(const int32_t* p, int64_t q) { return reinterpret_cast<const int4*>(p)[q]; }
+
+__device__ __forceinline__ int check_transition(int32_t s, int32_t a, int32_t d, int32_t n, int32_t A,
+                                                uint32_t* used) {
+    if ((unsigned)s >= (unsigned)n || (unsigned)d >= (unsigned)n || (unsigned)a >= (unsigned)A) return 1;
+    if (used[a] == 0) used[a] = 1;  // benign same-value store
+    return 0;
+}
+
 __global__ void k_validate(const int32_t* __restrict__ src, const int32_t* __restrict__ act,
                            const int32_t* __restrict__ dst, const int32_t* __restrict__ init,
-                           int32_t n, int64_t m, int32_t A, int* status, uint32_t* used) {
+                           int32_t n, int64_t m, int32_t A, int* status, uint32_t* used, int vec) {
     const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
+    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int bad = 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gsz) {
-        int32_t s = src[i], d = dst[i];
-        int32_t a = act ? act[i] : 0;
-        if ((unsigned)s >= (unsigned)n || (unsigned)d >= (unsigned)n || (unsigned)a >= (unsigned)A) {
-            bad = 1;
-        } else if (used[a] == 0) {
-            used[a] = 1;  // benign same-value store
-        }
+    const int64_t m4 = vec ? m / 4 : 0;
+    for (int64_t q = gtid; q < m4; q += gsz) {
+        const int4 s = ld4(src, q), d = ld4(dst, q);
+        const int4 a = act ? ld4(act, q) : make_int4(0, 0, 0, 0);
+        bad |= check_transition(s.x, a.x, d.x, n, A, used) | check_transition(s.y, a.y, d.y, n, A, used) |
+               check_transition(s.z, a.z, d.z, n, A, used) | check_transition(s.w, a.w, d.w, n, A, used);
     }
+    for (int64_t i = 4 * m4 + gtid; i < m; i += gsz)
+        bad |= check_transition(src[i], act ? act[i] : 0, dst[i], n, A, used);
     if (init)
         for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gsz)
             if ((unsigned)init[i] >= (unsigned)n) bad = 1;
@@ -47,9 +61,20 @@ __global__ void k_validate(const int32_t* __restrict__ src, const int32_t* __res
 template <typename K>
 __global__ void k_make_keys(const int32_t* __restrict__ src, const int32_t* __restrict__ act,
                             const int32_t* __restrict__ dst, int64_t m, int32_t A, K* keys,
-                            uint32_t* vals) {
+                            uint32_t* vals, int vec) {
     const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gsz) {
+    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t m4 = vec ? m / 4 : 0;  // keys and vals are fresh allocations: 16-byte aligned
+    for (int64_t q = gtid; q < m4; q += gsz) {
+        const int4 s = ld4(src, q), d = ld4(dst, q);
+        const int4 a = act ? ld4(act, q) : make_int4(0, 0, 0, 0);
+        keys[4 * q + 0] = (K)s.x * (K)A + (K)a.x;
+        keys[4 * q + 1] = (K)s.y * (K)A + (K)a.y;
+        keys[4 * q + 2] = (K)s.z * (K)A + (K)a.z;
+        keys[4 * q + 3] = (K)s.w * (K)A + (K)a.w;
+        reinterpret_cast<uint4*>(vals)[q] = make_uint4((uint32_t)d.x, (uint32_t)d.y, (uint32_t)d.z, (uint32_t)d.w);
+    }
+    for (int64_t i = 4 * m4 + gtid; i < m; i += gsz) {
         keys[i] = (K)src[i] * (K)A + (K)(act ? act[i] : 0);
         vals[i] = (uint32_t)dst[i];
     }
@@ -462,8 +487,9 @@ int plan_build(bisim_plan_s* p, const int32_t* src, const int32_t* act, const in
     DevMem used;
     BISIM_TRY(used.alloc(sizeof(uint32_t) * (size_t)A, st));
     BISIM_CUDA_TRY(cudaMemsetAsync(used.p, 0, sizeof(uint32_t) * (size_t)A, st));
+    const int vec = (((uintptr_t)src | (uintptr_t)dst | (uintptr_t)act) & 15u) == 0 ? 1 : 0;
     k_validate<<<grid_for(std::max<int64_t>(m, n), T), T, 0, st>>>(src, act, dst, init, n, m, A,
-                                                                   status, used.as<uint32_t>());
+                                                                   status, used.as<uint32_t>(), vec);
     BISIM_LAUNCHED();
     BISIM_CUDA_TRY(cudaGetLastError());
     std::vector<uint32_t> used_h((size_t)A);
@@ -495,7 +521,7 @@ int plan_build(bisim_plan_s* p, const int32_t* src, const int32_t* act, const in
     bool alt = false;
     if (wide) {
         k_make_keys<uint64_t><<<gm, T, 0, st>>>(src, act, dst, m, A, keys.as<uint64_t>(),
-                                                vals.as<uint32_t>());
+                                                vals.as<uint32_t>(), vec);
         BISIM_LAUNCHED();
         BISIM_CUDA_TRY(cudaGetLastError());
         BISIM_TRY(radix_sort_pairs<uint64_t, uint32_t>(keys.as<uint64_t>(), vals.as<uint32_t>(),
@@ -503,7 +529,7 @@ int plan_build(bisim_plan_s* p, const int32_t* src, const int32_t* act, const in
                                                        vals_alt.as<uint32_t>(), m, kbits, st, &alt));
     } else {
         k_make_keys<uint32_t><<<gm, T, 0, st>>>(src, act, dst, m, A, keys.as<uint32_t>(),
-                                                vals.as<uint32_t>());
+                                                vals.as<uint32_t>(), vec);
         BISIM_LAUNCHED();
         BISIM_CUDA_TRY(cudaGetLastError());
         BISIM_TRY(radix_sort_pairs<uint32_t, uint32_t>(keys.as<uint32_t>(), vals.as<uint32_t>(),

@@ -283,3 +283,28 @@ def test_fan_out_large_closed_form(n):
     got, st = run(lts_gen.fan_out(n), bisim.ENGINE_FRONTIER)
     assert np.array_equal(got, np.concatenate([[0, 0], np.arange(1, n - 1)]).astype(np.int32))
     assert st.num_blocks == n - 1
+
+
+def test_vector_and_unaligned_input_paths():
+    """Transition arrays are read four at a time when they start on a 16-byte
+    boundary: a bad entry inside that part is caught, and arrays that start
+    4 bytes past a boundary (read one by one) give the same partition."""
+    import torch
+
+    lts = lts_gen.random_small(61, 300, 3, 1000, blocks=2)
+    bad = lts_gen.LTS("bad", lts.n, lts.num_act, lts.src.copy(), lts.act.copy(), lts.dst.copy(), lts.init)
+    bad.dst[501] = lts.n  # out of range, inside the int4 part
+    with pytest.raises(bisim.BisimError) as ei:
+        run(bad)
+    assert ei.value.code == bisim.BISIM_EINVAL
+    bad = lts_gen.LTS("bad", lts.n, lts.num_act, lts.src.copy(), lts.act.copy(), lts.dst.copy(), lts.init)
+    bad.act[502] = lts.num_act
+    with pytest.raises(bisim.BisimError) as ei:
+        run(bad)
+    assert ei.value.code == bisim.BISIM_EINVAL
+    pad = lambda a: torch.from_numpy(np.concatenate([[0], a]).astype(np.int32)).cuda()[1:]  # noqa: E731
+    src, act, dst = pad(lts.src), pad(lts.act), pad(lts.dst)
+    assert src.data_ptr() % 16 != 0
+    with bisim.Plan(lts.n, lts.num_act, src, act, dst, torch.from_numpy(lts.init).cuda()) as p:
+        got, _ = p.refine()
+    assert got.cpu().numpy().tolist() == oracle.ks_lts(lts).tolist()
