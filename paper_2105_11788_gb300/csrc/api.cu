@@ -89,6 +89,7 @@ int bisim_plan(int32_t n, int64_t m, int32_t num_act, const int32_t* src, const 
     do {
         cudaError_t e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess && retain_pool_memory() != BISIM_OK) e = cudaErrorUnknown;
         if (e == cudaSuccess) e = cudaMallocHost(&p->ctrl_h, sizeof(bisim_ctrl));
         if (e == cudaSuccess) e = cudaEventCreate(&p->ev0);
         if (e == cudaSuccess) e = cudaEventCreate(&p->ev1);

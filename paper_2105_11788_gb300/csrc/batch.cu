@@ -159,6 +159,7 @@ int device_setup(bisim_plan_s* p) {
     int dev = 0;
     BISIM_CUDA_TRY(cudaGetDevice(&dev));
     BISIM_CUDA_TRY(cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, dev));
+    BISIM_TRY(retain_pool_memory());
     BISIM_CUDA_TRY(cudaMallocHost(&p->ctrl_h, sizeof(bisim_ctrl)));
     BISIM_CUDA_TRY(cudaEventCreate(&p->ev0));
     BISIM_CUDA_TRY(cudaEventCreate(&p->ev1));

@@ -2,9 +2,26 @@
 // tile sums) and a stable LSD radix sort (8-bit digits; per pass a tile
 // histogram, a scan of the digit-major histogram, and a stable scatter whose
 // in-tile ranks come from warp match/ballot).
+#include <mutex>
+
 #include "prim.cuh"
 
 namespace bisim {
+
+int retain_pool_memory() {
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    BISIM_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev < 0 || dev >= 64 || done[dev]) return BISIM_OK;
+    cudaMemPool_t pool;
+    BISIM_CUDA_TRY(cudaDeviceGetDefaultMemPool(&pool, dev));
+    uint64_t threshold = UINT64_MAX;
+    BISIM_CUDA_TRY(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &threshold));
+    done[dev] = true;
+    return BISIM_OK;
+}
 
 namespace {
 

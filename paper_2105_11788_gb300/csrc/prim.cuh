@@ -10,6 +10,12 @@
 
 namespace bisim {
 
+// Keep the memory that plans free in the device's default pool (release
+// threshold: unlimited) instead of returning it to the driver at every
+// synchronisation, so the next plan's allocations need no new mappings.
+// Done once per device; other users of the default pool see the same pool.
+int retain_pool_memory();
+
 // Stream-ordered device allocation (cudaMallocAsync / cudaFreeAsync).
 struct DevMem {
     void* p = nullptr;
