@@ -164,12 +164,24 @@ def max_over_ranks(x, world, device=None):
     return float(t.item())
 
 
+def source_digest(path):
+    """sha256 of a CUDA source with comments removed and whitespace runs
+    collapsed: it changes when the code changes, not when a comment does."""
+    import hashlib
+    import re
+
+    with open(path) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    text = re.sub(r"\s+", " ", text).strip()
+    return hashlib.sha256(text.encode()).hexdigest()
+
+
 def recorded_traffic(kernel, workload):
     """DRAM bytes per launch of `kernel` on `workload` from the committed ncu
     record (profiles/ncu_traffic.json), or None when there is none or the
-    kernel's source has changed since the counters were taken."""
-    import hashlib
-
+    kernel's source code has changed since the counters were taken."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(path):
         return None
@@ -178,11 +190,8 @@ def recorded_traffic(kernel, workload):
     if not rec:
         return None
     src = os.path.join(ROOT, rec["source"])
-    if not os.path.exists(src):
+    if not os.path.exists(src) or source_digest(src) != rec.get("source_digest"):
         return None
-    with open(src, "rb") as f:
-        if hashlib.sha256(f.read()).hexdigest() != rec["source_sha256"]:
-            return None
     return rec["dram_bytes_per_launch"]
 
 

@@ -1,21 +1,22 @@
 // Frontier refinement engine: the while-loop of Algorithm 3 (Algorithm 2 with
-// rcpp_alg2) where a round touches only the splitter C, the transitions into
-// C, the states that reach C and - when a block's leader reaches C - the part
-// of that block that moves out.
+// rcpp_alg2) where a splitter iteration touches only the splitter C, the
+// transitions into C, the states that reach C and - when a block's leader
+// reaches C - the part of that block that moves out.
 //
 // Layout (refinable partition): the members of block b occupy
 // elems[bbeg[b] .. bend[b]) and loc[s] is the position of state s. Splits
 // rearrange a block's range in place by swapping members.
 //
-// Round r (stamp = stamp0 + r), two grid barriers:
-//   select  C := next label of the FIFO worklist; unstable_C := false
+// A splitter iteration (stamp = stamp0 + round):
+//   select  C := next label of the size-bucketed worklist; unstable_C := false
 //   mark    one warp per member t of C, lanes over the transitions s -a-> t:
 //           mark[off(s) + order] := stamp. The first time s is marked in the
 //           round (smark stamp) it gets a rank r_s in its block b (atomicAdd)
 //           and is written to mscr[bend[b] - 1 - r_s], so after the step the
 //           marked members of b sit in the tail of b's range of mscr; the
-//           first one appends b to a list (warp list for blocks of at most 64
-//           states, CTA list otherwise). Blocks of one state cannot split.
+//           first one appends b (with its range) to a list (warp list for
+//           blocks of at most 64 states, CTA list otherwise). Blocks of one
+//           state cannot split.
 //   split   Algorithm 3's rule: s splits off iff its marks differ from the
 //           leader's. If the leader is unmarked the split part is exactly the
 //           marked members (k of them) and moves to the last k positions; if
@@ -24,6 +25,12 @@
 //           positions, the rest is relabelled. The new label is the smallest
 //           state of the split part; the old label, the new label and
 //           (Algorithm 3) C are pushed if they were stable.
+//
+// A round carries out one iteration (mark, barrier, split, barrier), or
+// several whose touched blocks do not overlap: claim, barrier, mark,
+// barrier, split, barrier (see the section on rounds with several splitters
+// below). Rounds run on the whole grid, on CTA 0 alone (light rounds of the
+// hybrid schedule) or on the CTA that owns an LTS of a batch.
 #include "plan.cuh"
 
 using namespace bisim;
