@@ -433,6 +433,8 @@ def main():
     ap.add_argument("--engine", default="auto", choices=["auto", "dense", "frontier", "pair"])
     ap.add_argument("--threads", type=int, default=0, help="threads per CTA (0 = library default)")
     ap.add_argument("--max-ctas", type=int, default=0, help="cap on persistent-kernel CTAs")
+    ap.add_argument("--local-states", type=int, default=0,
+                    help="frontier: LTSs up to this many states on one CTA (0 = library rule, -1 = never)")
     ap.add_argument("--light-edges", type=int, default=0,
                     help="frontier: light-round threshold (0 = library default, <0 = grid only)")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
@@ -457,7 +459,7 @@ def main():
     engine = {"auto": bisim.ENGINE_AUTO, "dense": bisim.ENGINE_DENSE,
               "frontier": bisim.ENGINE_FRONTIER, "pair": bisim.ENGINE_PAIR}[args.engine]
     opts = bisim.make_opts(engine=engine, threads=args.threads, max_ctas=args.max_ctas,
-                           light_edges=args.light_edges)
+                           light_edges=args.light_edges, local_states=args.local_states)
     desc, make = workload(args)
     lts = make()
     src = torch.from_numpy(lts.src).to(dev)
@@ -520,9 +522,15 @@ def main():
     hbm, peak_kind = read_peaks()
     achieved = (sum(kernel_bytes) / len(kernel_bytes)) / (sum(kernel_ms) / len(kernel_ms) * 1e-3) / 1e9
     if st.engine == bisim.ENGINE_DENSE:
-        kname = "k_dense_main"
+        kname, schedule = "k_dense_main", "dense rounds on the whole grid"
+    elif st.engine == bisim.ENGINE_PAIR:
+        kname, schedule = "k_pair_main", "pair rounds on the whole grid"
+    elif st.grid_ctas == 1:
+        kname, schedule = "k_frontier_batch", "one CTA (small sparse LTS)"
+    elif args.light_edges < 0:
+        kname, schedule = "k_frontier_main", "every round on the whole grid"
     else:
-        kname = "k_frontier_main" if args.light_edges < 0 else "k_frontier_hybrid"
+        kname, schedule = "k_frontier_hybrid", "hybrid (light rounds on one CTA)"
     roof = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm, "peak_kind": peak_kind,
             "traffic": recorded_traffic(kname, args.workload),
@@ -555,7 +563,8 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": vs_paper(args, value),
             "dtype": "int32", "data": "synthetic",
             "config": {"workload": desc, "n": lts.n, "m": lts.m, "num_act": lts.num_act,
-                       "engine": args.engine, "threads": args.threads, "max_ctas": args.max_ctas,
+                       "engine": args.engine, "schedule": schedule, "threads": args.threads,
+                       "max_ctas": args.max_ctas,
                        "l2": "flushed between steps (256 MiB write)" if flush is not None
                              else "inputs larger than L2",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},

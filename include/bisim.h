@@ -103,6 +103,16 @@ typedef struct bisim_opts {
                                 8 per CTA of a batch) */
     int32_t multi_min_states; /* batch: only LTSs with at least this many states take
                                  several splitters per round (0 = every LTS) */
+    int32_t local_states;     /* frontier engine, one LTS: start on a single CTA with CTA
+                                 barriers (the batch schedule on one LTS; threads 0 =
+                                 1024, splitters 0 = 32, split_budget 0 = 4) and hand
+                                 the rest to the hybrid schedule before a round whose
+                                 splitters hold more than this many states.
+                                 0 = sparse LTSs only (m <= 4n), 16384 states, and also
+                                 hand off after 3 rounds in a row in which at least
+                                 half of the splitters won or that took more than
+                                 25 us each; negative = never (hybrid or grid
+                                 schedule from the start) */
 } bisim_opts;
 
 typedef struct bisim_stats {

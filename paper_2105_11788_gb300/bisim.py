@@ -50,6 +50,7 @@ class bisim_opts(ctypes.Structure):
         ("splitters", ctypes.c_int32),
         ("split_budget", ctypes.c_int32),
         ("multi_min_states", ctypes.c_int32),
+        ("local_states", ctypes.c_int32),
     ]
 
 
@@ -155,10 +156,11 @@ def make_opts(engine: int = ENGINE_AUTO, rcpp_alg2: bool = False, raw_labels: bo
               threads: int = 0, ctas_per_sm: int = 0, round_cap: int = 0, timeout_ms: int = 0,
               test_hook: int = 0, max_ctas: int = 0, light_edges: int = 0,
               preprocess: int = 0, wide_threads: int = 0, wide_min_states: int = 0,
-              splitters: int = 0, split_budget: int = 0, multi_min_states: int = 0) -> bisim_opts:
+              splitters: int = 0, split_budget: int = 0, multi_min_states: int = 0,
+              local_states: int = 0) -> bisim_opts:
     return bisim_opts(engine, int(rcpp_alg2), int(raw_labels), threads, ctas_per_sm, test_hook,
                       round_cap, timeout_ms, max_ctas, light_edges, preprocess, wide_threads,
-                      wide_min_states, splitters, split_budget, multi_min_states)
+                      wide_min_states, splitters, split_budget, multi_min_states, local_states)
 
 
 # ----------------------------------------------------------- C-ABI mirrors

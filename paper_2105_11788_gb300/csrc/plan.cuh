@@ -33,12 +33,23 @@ struct bisim_ctrl {
     int pad3;
     long long commits;               // splitter iterations carried out (multi-splitter schedules)
     unsigned long long cmd_heads[32];  // worklist heads after the published round's selection
+    long long local_rounds;            // one LTS on one CTA: splitter iterations + 1
+    int handoff;                       // one LTS on one CTA: 1 = the grid takes over
+    int pad4;
+    unsigned long long start_heads[32];  // worklist heads at the hand-off to the grid
 };
 
 // Most splitters one multi-splitter round takes: grid rounds of the hybrid
 // schedule, and CTA rounds of the batch schedule.
 constexpr int BISIM_KMAX_GRID = 8192;
 constexpr int BISIM_KMAX_CTA = 128;
+// A sparse single LTS starting on one CTA moves to the grid before a round
+// whose splitters hold more than BISIM_HANDOFF_STATES states, or after
+// BISIM_HANDOFF_BUSY rounds in a row in which half the splitters won, or
+// that took longer than BISIM_HANDOFF_ROUND_NS each (about a grid round)
+constexpr int BISIM_HANDOFF_STATES = 16384;
+constexpr int BISIM_HANDOFF_BUSY = 3;
+constexpr unsigned long long BISIM_HANDOFF_ROUND_NS = 25000;
 
 // Frontier worklist: one FIFO ring of n entries per size bucket
 // floor(log2(block size)); the splitter is taken from the lowest non-empty

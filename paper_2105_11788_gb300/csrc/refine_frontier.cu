@@ -251,6 +251,7 @@ struct CtaShared {
     int mn;
     unsigned lmask;
     int C;
+    int bk;                 // select_splitter: size bucket of the popped label (-1: none)
     int bx[BISIM_BUCKETS];  // select_many: entries before each bucket
     int bn[BISIM_BUCKETS];  // select_many: entries taken from each bucket at most
     int hp[BISIM_BUCKETS];  // select_many: ring position of each bucket's head
@@ -849,9 +850,13 @@ __device__ __forceinline__ int32_t select_splitter(const Worklist& wl, unsigned 
         const bool ne = h < *(volatile const unsigned long long*)&wl.tail[lane];
         const unsigned bal = __ballot_sync(0xffffffffu, ne);
         if (bal == 0u) {
-            if (lane == 0) sh.C = -1;
+            if (lane == 0) {
+                sh.C = -1;
+                sh.bk = -1;
+            }
         } else if ((int)lane == __ffs(bal) - 1) {
             sh.C = ldcg(&wl.queue[(size_t)lane * wl.stride + wl.base + h % (unsigned long long)wl.cap]);
+            sh.bk = (int)lane;
             head[lane] = h + 1;
         }
     }
@@ -1103,7 +1108,9 @@ __global__ void __launch_bounds__(MAXT, 1) k_frontier_hybrid(FrontierArgs a, Hyb
                    a.tlist + n, (int)blockIdx.x, (int)gridDim.x, states);
         return gsync();
     };
-    if (threadIdx.x < BISIM_BUCKETS) sh.head[threadIdx.x] = 0;
+    // zero, or where a one-CTA start handed the refinement over (a field that
+    // CTA 0's commands never overwrite, so a late-starting CTA reads it too)
+    if (threadIdx.x < BISIM_BUCKETS) sh.head[threadIdx.x] = ldcg(&c->start_heads[threadIdx.x]);
     if (threadIdx.x < 32) s_lost[threadIdx.x] = 0u;
     PHASE_RESET();
     __syncthreads();
@@ -1290,7 +1297,9 @@ __global__ void __launch_bounds__(MAXT, 1) k_frontier_hybrid(FrontierArgs a, Hyb
 // shared memory. LTS i owns states, labels and member positions
 // [state_off[i], state_off[i+1]) of the batch arrays; CTAs take LTSs from a
 // counter in `order` (largest first). Nothing waits on another CTA, so the
-// launch is an ordinary one and may overlap other work.
+// launch is an ordinary one and may overlap other work. With state_off,
+// order and num_act null the batch is the plan's single LTS (states 0..n-1,
+// round cap a.round_cap), refined by one CTA.
 struct BatchArgs {
     int32_t k;
     const int64_t* __restrict__ state_off;  // [k+1]
@@ -1302,6 +1311,14 @@ struct BatchArgs {
     int kmax;                               // most splitters per round (1: one per round)
     int budget_per_warp;                    // states of a round's splitters per warp at most
     int multi_min_states;                   // smaller LTSs take one splitter per round
+    // single LTS only: hand the refinement to the grid before a round whose
+    // splitters hold more than handoff_states states (0 = never), or after
+    // handoff_busy rounds in a row with at least kmax / 2 winners, or
+    // handoff_busy rounds in a row of more than handoff_round_ns each
+    // (handoff_busy 0 = neither)
+    int handoff_states;
+    int handoff_busy;
+    unsigned long long handoff_round_ns;
 };
 
 __global__ void __launch_bounds__(1024) k_frontier_batch(FrontierArgs a, BatchArgs bt) {
@@ -1314,6 +1331,7 @@ __global__ void __launch_bounds__(1024) k_frontier_batch(FrontierArgs a, BatchAr
     __shared__ int32_t s_selP[BISIM_KMAX_CTA + 1];
     __shared__ uint32_t s_lost[BISIM_KMAX_CTA];
     __shared__ unsigned long long s_commits;
+    __shared__ int s_slow;  // rounds in a row longer than handoff_round_ns
     const int64_t gw = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int kmax = min(max(bt.kmax, 1), BISIM_KMAX_CTA);
     const int32_t budget = bt.budget_per_warp * (int32_t)nwarps;
@@ -1324,32 +1342,49 @@ __global__ void __launch_bounds__(1024) k_frontier_batch(FrontierArgs a, BatchAr
         const int inst = s_inst;
         __syncthreads();
         if (inst >= bt.k) break;
-        const int32_t li = bt.order[inst];
-        const int32_t s0 = (int32_t)bt.state_off[li];
-        const int32_t ni = (int32_t)(bt.state_off[li + 1] - s0);
+        const int32_t li = bt.order ? bt.order[inst] : 0;
+        const int32_t s0 = bt.state_off ? (int32_t)bt.state_off[li] : 0;
+        const int32_t ni = bt.state_off ? (int32_t)(bt.state_off[li + 1] - s0) : a.n;
         if (threadIdx.x < BISIM_BUCKETS) {
-            s_tail[threadIdx.x] = 0;
+            // a single LTS finds its worklist filled by the whole grid (k_front_queue)
+            s_tail[threadIdx.x] = bt.order ? 0ull : ldcg(&a.ctrl->bq_tail[threadIdx.x]);
             sh.head[threadIdx.x] = 0;
         }
         // the round stamps restart with every LTS: forget this CTA's last losses
         for (int i = threadIdx.x; i < BISIM_KMAX_CTA; i += blockDim.x) s_lost[i] = 0u;
-        if (threadIdx.x == 0) s_commits = 0;
+        if (threadIdx.x == 0) {
+            s_commits = 0;
+            s_slow = 0;
+        }
         __syncthreads();
         const Worklist wl{s_tail, a.queue, (size_t)a.n, s0, max(ni, 1)};
         // Algorithm 3, lines 1-3: every label of this LTS is unstable
-        for (int32_t l = s0 + threadIdx.x; l < s0 + ni; l += blockDim.x)
-            if (bt.block0[l] == l) push(a, wl, l);
+        if (bt.order)
+            for (int32_t l = s0 + threadIdx.x; l < s0 + ni; l += blockDim.x)
+                if (bt.block0[l] == l) push(a, wl, l);
         __syncthreads();
-        const int64_t cap = 3ll * ni + bt.num_act[li] + 2;
+        const int64_t cap = bt.num_act ? min((long long)a.round_cap, 3ll * ni + bt.num_act[li] + 2) : a.round_cap;
         const int kmax_i = ni >= bt.multi_min_states ? kmax : 1;
         int64_t r = 0;
         long long commits = 0;
+        // A round of several splitters costs about as much as two rounds of
+        // one (claim phase, one more barrier). After a round with at most two
+        // winners (the others touch the same blocks, as in Fan_out_n, or only
+        // two splitters were ready, as in a chain) the next `skip` rounds take
+        // one splitter; each further such round doubles the stretch (to 64),
+        // a round with three or more winners ends it.
+        int skip = 0, backoff = 0, busy = 0;
+        bool handoff = false;
         for (;;) {
             r++;
             const uint32_t stamp = a.stamp0 + (uint32_t)r;
+            const unsigned long long head0 = threadIdx.x < BISIM_BUCKETS ? sh.head[threadIdx.x] : 0ull;
+            const unsigned long long t0 = threadIdx.x == 0 && bt.handoff_busy > 0 ? globaltimer_ns() : 0ull;
             int K;
             int32_t C;
-            if (kmax_i > 1) {
+            const bool many = kmax_i > 1 && skip == 0;
+            if (skip > 0) skip--;
+            if (many) {
                 K = select_many(a, wl, sh.head, sh, s_selC, s_selP, kmax_i, budget);
                 C = K > 0 ? s_selC[0] : -1;
             } else {
@@ -1357,6 +1392,28 @@ __global__ void __launch_bounds__(1024) k_frontier_batch(FrontierArgs a, BatchAr
                 K = C >= 0 ? 1 : 0;
             }
             if (K == 0) break;
+            if (bt.handoff_states > 0 || bt.handoff_busy > 0) {
+                int32_t rs = many ? s_selP[K] : 0;
+                // a popped label of size bucket k had at least 2^k states when it was
+                // pushed; it may have shrunk since, so only then is its size looked up
+                if (!many && bt.handoff_states > 0 && (1ll << sh.bk) > bt.handoff_states) {
+                    if (threadIdx.x == 0) s_ns = ldcg(&a.bend[C]) - ldcg(&a.bbeg[C]);
+                    __syncthreads();
+                    rs = s_ns;
+                    __syncthreads();
+                }
+                if ((bt.handoff_states > 0 && rs > bt.handoff_states) ||
+                    (bt.handoff_busy > 0 && (busy >= bt.handoff_busy || s_slow >= bt.handoff_busy))) {
+                    // leave this round's labels in the worklist for the grid
+                    if (threadIdx.x < BISIM_BUCKETS) {
+                        a.ctrl->start_heads[threadIdx.x] = head0;
+                        a.ctrl->bq_tail[threadIdx.x] = s_tail[threadIdx.x];
+                    }
+                    if (threadIdx.x == 0) a.ctrl->handoff = 1;
+                    handoff = true;
+                    break;
+                }
+            }
             if (r > cap) {
                 if (threadIdx.x == 0) atomicOr(&a.ctrl->status, ST_ROUNDS);
                 break;
@@ -1381,13 +1438,28 @@ __global__ void __launch_bounds__(1024) k_frontier_batch(FrontierArgs a, BatchAr
                                 __syncthreads();
                                 return true;
                             });
+                // winners of this round: every warp counts the same losers
+                int nlost = 0;
+                for (int j0 = 0; j0 < K; j0 += 32) {
+                    const int j = j0 + (int)(threadIdx.x & 31);
+                    nlost += __popc(__ballot_sync(0xffffffffu, j < K && s_lost[j] == stamp));
+                }
+                if (K - nlost <= 2) {
+                    backoff = min(max(2 * backoff, 2), 64);
+                    skip = backoff;
+                } else {
+                    backoff = 0;
+                }
+                busy = 2 * (K - nlost) >= kmax_i ? busy + 1 : 0;
             }
+            if (threadIdx.x == 0 && bt.handoff_busy > 0)
+                s_slow = globaltimer_ns() - t0 > bt.handoff_round_ns ? s_slow + 1 : 0;
             __syncthreads();
         }
         if (commits) atomicAdd(&s_commits, (unsigned long long)commits);
         __syncthreads();
         if (threadIdx.x == 0) bt.inst_rounds[li] = (long long)s_commits + 1;
-        steps += r;
+        steps += handoff ? r - 1 : r;  // the round that found the hand-off did not run
         __syncthreads();
     }
     if (edges) atomicAdd((unsigned long long*)&a.ctrl->edges, (unsigned long long)edges);
@@ -1552,6 +1624,39 @@ int report(bisim_plan_s* p) {
     return code;
 }
 
+// One LTS on one CTA: the batch kernel with the plan's LTS as its only
+// instance, every round between CTA barriers. With a hand-off rule it stops
+// before a round that the whole grid would do faster and leaves the worklist
+// (tails, and the heads before that round) in ctrl for the hybrid kernel.
+int refine_frontier_local(bisim_plan_s* p, int64_t cap, uint32_t base, int handoff_states, int handoff_busy,
+                          double* ms) {
+    cudaStream_t st = p->st;
+    FrontierArgs a = make_args(p, base, cap);
+    bisim_ctrl* c = p->ctrl.as<bisim_ctrl>();
+    BatchArgs bt;
+    bt.k = 1;
+    bt.state_off = nullptr;
+    bt.order = nullptr;
+    bt.num_act = nullptr;
+    bt.next = &c->next_inst;
+    bt.inst_rounds = &c->local_rounds;
+    bt.block0 = p->block0.as<int32_t>();
+    bt.kmax = p->opts.splitters > 0 ? std::min(p->opts.splitters, BISIM_KMAX_CTA) : 32;
+    bt.budget_per_warp = p->opts.split_budget > 0 ? std::min(p->opts.split_budget, 1 << 20) : 4;
+    bt.multi_min_states = 0;
+    bt.handoff_states = handoff_states;
+    bt.handoff_busy = handoff_busy;
+    bt.handoff_round_ns = BISIM_HANDOFF_ROUND_NS;
+    const int threads = p->opts.threads > 0 ? p->opts.threads : 1024;
+    BISIM_CUDA_TRY(cudaEventRecord(p->evk0, st));
+    k_frontier_batch<<<1, threads, 0, st>>>(a, bt);
+    BISIM_LAUNCHED();
+    BISIM_CUDA_TRY(cudaGetLastError());
+    BISIM_CUDA_TRY(cudaEventRecord(p->evk1, st));
+    BISIM_TRY(read_ctrl(p));
+    return persistent_ms(p, ms);
+}
+
 }  // namespace
 
 namespace bisim {
@@ -1561,8 +1666,36 @@ int refine_frontier(bisim_plan_s* p, bisim_stats* stats) {
     const int64_t cap = p->opts.round_cap > 0 ? p->opts.round_cap : 3ll * n + p->A + 2;
     uint32_t base;
     BISIM_TRY(reserve_stamps(p, cap + 1, &base));
+    // A sparse LTS (m <= 4n) starts on one CTA, whose rounds cost a few
+    // CTA barriers instead of grid barriers, and moves to the grid before a
+    // round of a large splitter or once many splitters win every round.
+    const int32_t lo = p->opts.local_states;
+    const bool start_local = p->opts.light_edges >= 0 && (lo > 0 || (lo == 0 && p->m <= 4ll * n));
+    int64_t done = 0;            // rounds carried out on one CTA
+    long long done_commits = 0;  // splitter iterations among them
+    double local_ms = 0;
     BISIM_TRY(frontier_setup(p, true));
-    FrontierArgs a = make_args(p, base, cap);
+    if (start_local) {
+        BISIM_TRY(refine_frontier_local(p, cap, base, lo > 0 ? lo : BISIM_HANDOFF_STATES,
+                                        lo > 0 ? 0 : BISIM_HANDOFF_BUSY, &local_ms));
+        BISIM_TRY(report(p));
+        if (!p->ctrl_h->handoff) {
+            p->stamp = base + (uint32_t)std::min<long long>(p->ctrl_h->rounds + 1, cap + 1);
+            if (stats) {
+                stats->t_main_ms = local_ms;
+                stats->rounds = p->ctrl_h->local_rounds;
+                stats->steps = p->ctrl_h->rounds;
+                stats->edges_visited = p->ctrl_h->edges;
+                stats->states_visited = p->ctrl_h->states;
+                stats->engine = BISIM_ENGINE_FRONTIER;
+                stats->grid_ctas = 1;
+            }
+            return BISIM_OK;
+        }
+        done = p->ctrl_h->rounds;
+        done_commits = p->ctrl_h->local_rounds - 1;
+    }
+    FrontierArgs a = make_args(p, base + (uint32_t)done, cap - done);
     const int threads = p->opts.threads > 0 ? p->opts.threads : 512;
     const int light = p->opts.light_edges == 0 ? 256 : p->opts.light_edges;
     int grid = 0;
@@ -1593,11 +1726,12 @@ int refine_frontier(bisim_plan_s* p, bisim_stats* stats) {
                                     sizeof(int32_t) * (2 * (size_t)h.kmax + 1)));
     }
     BISIM_TRY(read_ctrl(p));
-    p->stamp = base + (uint32_t)std::min<long long>(p->ctrl_h->rounds + 1, cap + 1);
+    p->stamp = base + (uint32_t)std::min<long long>(done + p->ctrl_h->rounds + 1, cap + 1);
     if (stats) {
         BISIM_TRY(persistent_ms(p, &stats->t_main_ms));
-        stats->rounds = p->ctrl_h->commits + 1;
-        stats->steps = p->ctrl_h->rounds;
+        stats->t_main_ms += local_ms;
+        stats->rounds = done_commits + p->ctrl_h->commits + 1;
+        stats->steps = done + p->ctrl_h->rounds;
         stats->edges_visited = p->ctrl_h->edges;
         stats->states_visited = p->ctrl_h->states;
         stats->engine = BISIM_ENGINE_FRONTIER;
@@ -1627,6 +1761,9 @@ int refine_frontier_batch(bisim_plan_s* p, bisim_stats* stats, std::vector<long 
     bt.kmax = p->opts.splitters > 0 ? std::min(p->opts.splitters, BISIM_KMAX_CTA) : 1;
     bt.budget_per_warp = p->opts.split_budget > 0 ? std::min(p->opts.split_budget, 1 << 20) : 8;
     bt.multi_min_states = std::max(p->opts.multi_min_states, 0);
+    bt.handoff_states = 0;
+    bt.handoff_busy = 0;
+    bt.handoff_round_ns = 0;
     const int threads = p->opts.threads > 0 ? p->opts.threads : 256;
     // optional split schedule: the LTSs with at least wide_min_states states
     // (a prefix of the largest-first order) run in a second launch of wide

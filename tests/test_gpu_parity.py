@@ -14,8 +14,11 @@ from paper_2105_11788_gb300 import bisim, lts_gen
 pytestmark = pytest.mark.gpu
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
-ENGINES = [bisim.ENGINE_DENSE, bisim.ENGINE_FRONTIER]
-ENGINE_IDS = ["dense", "frontier"]
+# the frontier engine twice: the hybrid/grid schedule, and one CTA for the whole LTS
+FRONTIER_GRID = dict(engine=bisim.ENGINE_FRONTIER, local_states=-1)
+FRONTIER_LOCAL = dict(engine=bisim.ENGINE_FRONTIER, local_states=1 << 30)
+ENGINES = [dict(engine=bisim.ENGINE_DENSE), FRONTIER_GRID, FRONTIER_LOCAL]
+ENGINE_IDS = ["dense", "frontier", "frontier-local"]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -27,7 +30,8 @@ def _cuda():
 
 
 def run(lts, engine=bisim.ENGINE_AUTO, **kw):
-    return bisim.reduce(lts, bisim.make_opts(engine=engine, **kw), return_stats=True)
+    kw = {**engine, **kw} if isinstance(engine, dict) else {"engine": engine, **kw}
+    return bisim.reduce(lts, bisim.make_opts(**kw), return_stats=True)
 
 
 def _golden(name):
@@ -171,7 +175,7 @@ def test_round_cap_reports_error(engine):
     assert np.array_equal(got, np.arange(200))
 
 
-@pytest.mark.parametrize("engine", ENGINES, ids=ENGINE_IDS)
+@pytest.mark.parametrize("engine", ENGINES[:2], ids=ENGINE_IDS[:2])
 def test_barrier_wait_times_out_and_context_survives(engine):
     """CTA 0 never arrives at its first barrier (a flag nothing sets); the
     other CTAs give up after the time limit and the call reports it."""
@@ -190,7 +194,7 @@ def test_refine_twice_same_plan(engine):
     lts = lts_gen.quotient_expansion(seed=9, classes=300, trans=3000, copies_hi=20)
     d = lambda a: torch.from_numpy(a).cuda()  # noqa: E731
     with bisim.Plan(lts.n, lts.num_act, d(lts.src), d(lts.act), d(lts.dst), None,
-                    bisim.make_opts(engine=engine)) as p:
+                    bisim.make_opts(**engine)) as p:
         a, s1 = p.refine()
         a = a.cpu().numpy()
         b, s2 = p.refine()
@@ -218,16 +222,72 @@ def test_launch_shapes(engine):
         assert got.tolist() == want.tolist(), (threads, per_sm)
 
 
-@pytest.mark.parametrize("light_edges", [-1, 0, 1 << 30], ids=["grid", "hybrid", "all-light"])
-def test_frontier_schedules(light_edges):
+@pytest.mark.parametrize("light_edges,local", [(-1, 0), (0, -1), (1 << 30, -1), (0, 1 << 30)],
+                         ids=["grid", "hybrid", "all-light", "one-cta"])
+def test_frontier_schedules(light_edges, local):
     """Frontier rounds on the whole grid, hybrid (light rounds on one CTA),
-    and every eligible round light: same partitions."""
+    every eligible round light, and the whole LTS on one CTA: same
+    partitions."""
     cases = [lts_gen.random_small(100 + s, 40, 1 + s % 3, 120, blocks=2) for s in range(30)]
     cases += [lts_gen.kripke_uniform(), lts_gen.chain(n=2000), lts_gen.fan_out(200),
               lts_gen.quotient_expansion(seed=6, classes=500, trans=5000, copies_hi=40)]
     for lts in cases:
-        got, st = run(lts, bisim.ENGINE_FRONTIER, light_edges=light_edges)
+        got, st = run(lts, bisim.ENGINE_FRONTIER, light_edges=light_edges, local_states=local)
         assert got.tolist() == oracle.ks_lts(lts).tolist(), lts.name
+        assert (st.grid_ctas == 1) == (local > 0), lts.name
+
+
+def test_one_cta_start_and_hand_off():
+    """A sparse LTS (m <= 4n) starts on one CTA; a denser one takes the hybrid
+    schedule. A round whose splitter holds more than local_states states, or
+    (by default) a run of rounds in which most splitters win, hands the rest
+    of the refinement to the grid: same partition."""
+    n = 8192
+    got, st = run(lts_gen.fan_out(n), bisim.ENGINE_FRONTIER)
+    assert st.grid_ctas == 1 and got.tolist() == [0, 0] + list(range(1, n - 1))
+    dense = lts_gen.quotient_expansion(seed=4, classes=400, trans=4000, copies_hi=30)
+    assert dense.m > 4 * dense.n
+    got, st = run(dense, bisim.ENGINE_FRONTIER)
+    assert st.grid_ctas > 1 and got.tolist() == oracle.ks_lts(dense).tolist()
+    # 100 singleton blocks on a chain, then a 1,900-state cycle that no
+    # singleton splits: its round (1,900 > 512 states) goes to the grid
+    big, small = 1900, 100
+    trip = [(i, 0, (i + 1) % big) for i in range(big)]
+    trip += [(big + i, 0, big + i + 1) for i in range(small - 1)]
+    init = [0] * big + list(range(1, small + 1))
+    lts = lts_gen.from_triples(big + small, 1, trip, init)
+    got, st = run(lts, bisim.ENGINE_FRONTIER, local_states=512)
+    assert got.tolist() == defs.canonical(np.array(init, dtype=np.int32)).tolist()
+    assert st.grid_ctas > 1 and st.rounds >= small + 1
+    got, st = run(lts, bisim.ENGINE_FRONTIER, local_states=4096)
+    assert st.grid_ctas == 1 and got.tolist() == defs.canonical(np.array(init, dtype=np.int32)).tolist()
+    # a sparse power-law LTS: thousands of independent small splitters
+    lts = lts_gen.powerlaw(seed=3, n=20000, mean_deg=3.0)
+    assert lts.m <= 4 * lts.n
+    got, st = run(lts, bisim.ENGINE_FRONTIER)
+    assert st.grid_ctas > 1 and got.tolist() == oracle.ks_lts(lts).tolist()
+    # one splitter per round on one CTA
+    lts = lts_gen.kripke_uniform()
+    got, st = run(lts, bisim.ENGINE_FRONTIER, splitters=1, threads=256)
+    assert got.tolist() == oracle.ks_lts(lts).tolist()
+    assert st.grid_ctas == 1 and st.steps == st.rounds
+
+
+@pytest.mark.parametrize("local", [16, 64, 300])
+def test_hand_off_at_random_points(local):
+    """Hand-offs from one CTA to the grid wherever a splitter first exceeds
+    the threshold: every partition equals the oracle's, and the splitter
+    iterations obey the bounds."""
+    cases = [lts_gen.random_small(700 + s, 200, 1 + s % 3, 500, blocks=1 + s % 4) for s in range(20)]
+    cases += [lts_gen.kripke_uniform(seed=5), lts_gen.chain(n=3000), lts_gen.fan_out(500),
+              lts_gen.quotient_expansion(seed=6, classes=500, trans=5000, copies_hi=40)]
+    for lts in cases:
+        want = oracle.ks_lts(lts)
+        got, st = run(lts, bisim.ENGINE_FRONTIER, local_states=local)
+        assert got.tolist() == want.tolist(), lts.name
+        B = defs.num_blocks(want)
+        assert B + 1 <= st.rounds <= 3 * B - st.initial_blocks + 1, lts.name
+        assert st.steps <= st.rounds
 
 
 @pytest.mark.parametrize("engine", ENGINES, ids=ENGINE_IDS)
@@ -246,8 +306,9 @@ def test_preprocessing_rounds_and_direct_grouping_agree(engine):
         assert st1.pre_rounds == st2.pre_rounds
 
 
+@pytest.mark.parametrize("local", [-1, 1 << 30], ids=["grid", "one-cta"])
 @pytest.mark.parametrize("splitters", [1, 2, 7, 0], ids=["one", "two", "seven", "default"])
-def test_several_splitters_per_round(splitters):
+def test_several_splitters_per_round(splitters, local):
     """Rounds that take several splitters at once (deferring those whose
     touched blocks overlap) give the oracle's partition; the splitter
     iterations still obey B + 1 <= rounds <= 3B - |pi_0'| + 1, and there are
@@ -257,7 +318,7 @@ def test_several_splitters_per_round(splitters):
               lts_gen.quotient_expansion(seed=6, classes=500, trans=5000, copies_hi=40),
               lts_gen.powerlaw(seed=3, n=20000)]
     for lts in cases:
-        got, st = run(lts, bisim.ENGINE_FRONTIER, splitters=splitters)
+        got, st = run(lts, bisim.ENGINE_FRONTIER, splitters=splitters, local_states=local)
         want = oracle.ks_lts(lts)
         assert got.tolist() == want.tolist(), lts.name
         B = defs.num_blocks(want)
@@ -276,11 +337,11 @@ def test_several_splitters_large_worklist():
     assert st.steps * 4 < st.rounds  # many splitters per barrier round
 
 
-@pytest.mark.parametrize("n", [10_000, 200_000])
-def test_fan_out_large_closed_form(n):
+@pytest.mark.parametrize("n,local", [(10_000, 0), (10_000, 1 << 30), (200_000, 0)])
+def test_fan_out_large_closed_form(n, local):
     """Fan_out_n far beyond the paper's sizes: states 0 and 1 together, every
     other state alone (n - 1 blocks)."""
-    got, st = run(lts_gen.fan_out(n), bisim.ENGINE_FRONTIER)
+    got, st = run(lts_gen.fan_out(n), bisim.ENGINE_FRONTIER, local_states=local)
     assert np.array_equal(got, np.concatenate([[0, 0], np.arange(1, n - 1)]).astype(np.int32))
     assert st.num_blocks == n - 1
 

@@ -10,9 +10,12 @@ from paper_2105_11788_gb300 import bisim, lts_gen
 
 pytestmark = pytest.mark.gpu
 
-SETTINGS = [dict(threads=t, splitters=k, light_edges=le, split_budget=bud)
+SETTINGS = [dict(threads=t, splitters=k, light_edges=le, split_budget=bud, local_states=-1)
             for t in (128, 512, 1024) for k in (2, 16, 0) for le in (0, -1, 1 << 30) for bud in (0, 3)
             if not (le == -1 and k != 0)]
+# the whole LTS on one CTA, or one CTA until a splitter exceeds 8 / 100 states
+SETTINGS += [dict(threads=t, splitters=k, split_budget=bud, local_states=lo)
+             for t in (128, 1024) for k in (1, 16, 0) for bud in (0, 3) for lo in (1 << 30, 8, 100)]
 
 
 @pytest.fixture(scope="module", autouse=True)
