@@ -526,7 +526,11 @@ def main():
     elif st.engine == bisim.ENGINE_PAIR:
         kname, schedule = "k_pair_main", "pair rounds on the whole grid"
     elif st.grid_ctas == 1:
-        kname, schedule = "k_frontier_batch", "one CTA (small sparse LTS)"
+        kname, schedule = "k_frontier_batch", "one CTA (sparse LTS)"
+    elif st.local_steps > 0:
+        # started on one CTA, handed to the hybrid: name the kernel that ran more rounds
+        kname = "k_frontier_batch" if 2 * st.local_steps >= st.steps else "k_frontier_hybrid"
+        schedule = f"one CTA for {st.local_steps} of {st.steps} rounds, then hybrid"
     elif args.light_edges < 0:
         kname, schedule = "k_frontier_main", "every round on the whole grid"
     else:
@@ -575,7 +579,8 @@ def main():
             "cpu_baseline": cpu,
             "gpu_launches": int(sum(s.launches for s in stats)),
             "clocks": clk,
-            "detail": {"rounds": st.rounds, "steps": st.steps, "pre_rounds": st.pre_rounds,
+            "detail": {"rounds": st.rounds, "steps": st.steps, "local_steps": st.local_steps,
+                       "pre_rounds": st.pre_rounds,
                        "initial_blocks": st.initial_blocks, "num_blocks": st.num_blocks,
                        "mark_length": st.mark_length, "t_plan_ms": st.t_plan_ms,
                        "t_refine_ms": st.t_refine_ms, "t_pre_ms": st.t_pre_ms,

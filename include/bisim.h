@@ -133,6 +133,8 @@ typedef struct bisim_stats {
     int32_t grid_ctas;      /* CTAs of the persistent launch */
     int64_t steps;          /* barrier-separated rounds incl. the final empty one; equals
                                rounds when every round takes one splitter */
+    int64_t local_steps;    /* frontier engine, one LTS: of those, the rounds run on one CTA
+                               before the grid took over (= steps when it never did) */
 } bisim_stats;
 
 typedef struct bisim_plan_s* bisim_plan_t;

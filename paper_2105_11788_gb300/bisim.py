@@ -74,6 +74,7 @@ class bisim_stats(ctypes.Structure):
         ("engine", ctypes.c_int32),
         ("grid_ctas", ctypes.c_int32),
         ("steps", ctypes.c_int64),
+        ("local_steps", ctypes.c_int64),
     ]
 
     def as_dict(self) -> dict:

@@ -1685,6 +1685,7 @@ int refine_frontier(bisim_plan_s* p, bisim_stats* stats) {
                 stats->t_main_ms = local_ms;
                 stats->rounds = p->ctrl_h->local_rounds;
                 stats->steps = p->ctrl_h->rounds;
+                stats->local_steps = p->ctrl_h->rounds;
                 stats->edges_visited = p->ctrl_h->edges;
                 stats->states_visited = p->ctrl_h->states;
                 stats->engine = BISIM_ENGINE_FRONTIER;
@@ -1732,6 +1733,7 @@ int refine_frontier(bisim_plan_s* p, bisim_stats* stats) {
         stats->t_main_ms += local_ms;
         stats->rounds = done_commits + p->ctrl_h->commits + 1;
         stats->steps = done + p->ctrl_h->rounds;
+        stats->local_steps = done;
         stats->edges_visited = p->ctrl_h->edges;
         stats->states_visited = p->ctrl_h->states;
         stats->engine = BISIM_ENGINE_FRONTIER;

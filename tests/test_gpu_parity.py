@@ -245,10 +245,12 @@ def test_one_cta_start_and_hand_off():
     n = 8192
     got, st = run(lts_gen.fan_out(n), bisim.ENGINE_FRONTIER)
     assert st.grid_ctas == 1 and got.tolist() == [0, 0] + list(range(1, n - 1))
+    assert st.local_steps == st.steps
     dense = lts_gen.quotient_expansion(seed=4, classes=400, trans=4000, copies_hi=30)
     assert dense.m > 4 * dense.n
     got, st = run(dense, bisim.ENGINE_FRONTIER)
     assert st.grid_ctas > 1 and got.tolist() == oracle.ks_lts(dense).tolist()
+    assert st.local_steps == 0
     # 100 singleton blocks on a chain, then a 1,900-state cycle that no
     # singleton splits: its round (1,900 > 512 states) goes to the grid
     big, small = 1900, 100
@@ -259,6 +261,7 @@ def test_one_cta_start_and_hand_off():
     got, st = run(lts, bisim.ENGINE_FRONTIER, local_states=512)
     assert got.tolist() == defs.canonical(np.array(init, dtype=np.int32)).tolist()
     assert st.grid_ctas > 1 and st.rounds >= small + 1
+    assert 0 < st.local_steps < st.steps  # the singletons' rounds ran on one CTA
     got, st = run(lts, bisim.ENGINE_FRONTIER, local_states=4096)
     assert st.grid_ctas == 1 and got.tolist() == defs.canonical(np.array(init, dtype=np.int32)).tolist()
     # a sparse power-law LTS: thousands of independent small splitters
