@@ -114,23 +114,16 @@ struct FrontierArgs {
     int test_hook;
 };
 
-// The arguments as seen by one kind of kernel. Own = true: every array entry
-// the kernel touches belongs to one CTA (the CTA-per-LTS kernel), so a load
-// after __syncthreads may come from L1; Own = false: other CTAs write the
-// same arrays between grid barriers, so loads go to L2 (ld.global.cg).
-template <bool Own>
-struct FrontierArgsOf : FrontierArgs {
-    static constexpr bool own = Own;
-};
-using GridArgs = FrontierArgsOf<false>;
-using CtaArgs = FrontierArgsOf<true>;
-
-template <class A, typename T>
-__device__ __forceinline__ T ld(const A&, const T* p) {
-    if constexpr (A::own)
-        return *p;
-    else
-        return ldcg(p);
+// Loads of the round functions. Each one follows the barrier that orders it
+// after the stores it must observe: __syncthreads within a CTA, and between
+// CTAs the grid barrier (release arrive, acquire wait) or the release/acquire
+// pair of a published command. By the memory model such a load sees those
+// stores even when served from L1, so it takes the default caching. Waits on
+// words that other CTAs change while this one spins (the heartbeat, the
+// status word) read them with ld.global.cg instead.
+template <typename T>
+__device__ __forceinline__ T ld(const T* p) {
+    return *p;
 }
 
 __device__ __forceinline__ int size_bucket(int32_t sz) { return 31 - __clz(max(sz, 1)); }
@@ -154,17 +147,15 @@ __device__ __forceinline__ void push_sized(const Worklist& wl, int32_t label, in
     wl.queue[(size_t)bk * wl.stride + wl.base + pos % (unsigned long long)wl.cap] = label;
 }
 
-template <class A>
-__device__ __forceinline__ void push(const A& a, const Worklist& wl, int32_t label) {
-    push_sized(wl, label, ld(a, &a.bend[label]) - ld(a, &a.bbeg[label]));
+__device__ __forceinline__ void push(const FrontierArgs& a, const Worklist& wl, int32_t label) {
+    push_sized(wl, label, ld(&a.bend[label]) - ld(&a.bbeg[label]));
 }
 
 // unstable_label := true; enqueue it if it was stable (size < 0: look it up)
-template <class A>
-__device__ __forceinline__ void set_unstable(const A& a, const Worklist& wl, int32_t label,
+__device__ __forceinline__ void set_unstable(const FrontierArgs& a, const Worklist& wl, int32_t label,
                                              int32_t size = -1) {
     if (atomicExch(&a.unstable[label], 1u) == 0u) {
-        if (size < 0) size = ld(a, &a.bend[label]) - ld(a, &a.bbeg[label]);
+        if (size < 0) size = ld(&a.bend[label]) - ld(&a.bbeg[label]);
         push_sized(wl, label, size);
     }
 }
@@ -172,20 +163,18 @@ __device__ __forceinline__ void set_unstable(const A& a, const Worklist& wl, int
 // finish_split by a whole warp: the (up to) three labels are pushed by three
 // lanes at once; the kept part b has szb states and the split part szl. The
 // caller's stores of the new ranges precede a __syncwarp.
-template <class A>
-__device__ __forceinline__ void finish_split_warp(const A& a, const Worklist& wl, int32_t b,
+__device__ __forceinline__ void finish_split_warp(const FrontierArgs& a, const Worklist& wl, int32_t b,
                                                   int32_t szb, int32_t leader, int32_t szl, int32_t C) {
     const unsigned lane = threadIdx.x & 31u;
     int32_t lab = lane == 0 ? b : lane == 1 ? leader : (lane == 2 && !a.alg2) ? C : -1;
-    if (lab == MULTI) lab = ld(a, &a.bspl[b]);  // the splitter that touched b this round
+    if (lab == MULTI) lab = ld(&a.bspl[b]);  // the splitter that touched b this round
     if (lab >= 0) set_unstable(a, wl, lab, lane == 0 ? szb : lane == 1 ? szl : -1);
 }
 
 // Does a member with mark slots [os, os + ks) have the same marks as the
 // leader (slots [lo, lo + k); for k <= 32 their marks are the bits of
 // lmask)? Loads go out eight at a time.
-template <class A>
-__device__ __forceinline__ bool same_marks_at(const A& a, int32_t os, int32_t ks, int32_t lo, int32_t k,
+__device__ __forceinline__ bool same_marks_at(const FrontierArgs& a, int32_t os, int32_t ks, int32_t lo, int32_t k,
                                               unsigned lmask, uint32_t stamp) {
     if (ks != k) {  // members must share the leader's label set (preprocessing invariant)
         atomicOr(&a.ctrl->status, ST_INTERNAL);
@@ -196,8 +185,8 @@ __device__ __forceinline__ bool same_marks_at(const A& a, int32_t os, int32_t ks
         uint32_t v[8], w[8];
 #pragma unroll
         for (int u = 0; u < 8; u++) {
-            v[u] = q0 + u < ks ? ld(a, &a.mark[os + q0 + u]) : 0u;
-            w[u] = k > 32 && q0 + u < ks ? ld(a, &a.mark[lo + q0 + u]) : 0u;
+            v[u] = q0 + u < ks ? ld(&a.mark[os + q0 + u]) : 0u;
+            w[u] = k > 32 && q0 + u < ks ? ld(&a.mark[lo + q0 + u]) : 0u;
         }
 #pragma unroll
         for (int u = 0; u < 8; u++)
@@ -207,8 +196,7 @@ __device__ __forceinline__ bool same_marks_at(const A& a, int32_t os, int32_t ks
     return !diff;
 }
 
-template <class A>
-__device__ __forceinline__ bool same_marks(const A& a, int32_t s, int32_t lo, int32_t k,
+__device__ __forceinline__ bool same_marks(const FrontierArgs& a, int32_t s, int32_t lo, int32_t k,
                                            unsigned lmask, uint32_t stamp) {
     const int32_t os = a.off[s];
     return same_marks_at(a, os, a.off[s + 1] - os, lo, k, lmask, stamp);
@@ -217,27 +205,26 @@ __device__ __forceinline__ bool same_marks(const A& a, int32_t s, int32_t lo, in
 // One warp splits block b (range [b0, e0), at most 64 members) from the
 // members themselves. The loads are grouped by what they depend on: b and
 // its range; then the members; then the members' marks.
-template <class A>
-__device__ void warp_split(const A& a, const Worklist& wl, int32_t b, int32_t b0, int32_t e0,
+__device__ void warp_split(const FrontierArgs& a, const Worklist& wl, int32_t b, int32_t b0, int32_t e0,
                            uint32_t stamp, int32_t C, long long& states) {
     const unsigned lane = threadIdx.x & 31u;
     const unsigned lt = lanemask_lt();
     const int32_t sz = e0 - b0;
     const int32_t lo = a.off[b];
     const int32_t k = a.off[b + 1] - lo;
-    const bool lead_marked = ld(a, &a.smark[b]) == stamp;
-    const int32_t s0 = (int)lane < sz ? ld(a, &a.elems[b0 + lane]) : -1;
-    const int32_t s1 = (int)lane + 32 < sz ? ld(a, &a.elems[b0 + 32 + lane]) : -1;
+    const bool lead_marked = ld(&a.smark[b]) == stamp;
+    const int32_t s0 = (int)lane < sz ? ld(&a.elems[b0 + lane]) : -1;
+    const int32_t s1 = (int)lane + 32 < sz ? ld(&a.elems[b0 + 32 + lane]) : -1;
     if (lane == 0) a.mcnt[b] = 0;
-    const bool mk0 = s0 >= 0 && ld(a, &a.smark[s0]) == stamp;
-    const bool mk1 = s1 >= 0 && ld(a, &a.smark[s1]) == stamp;
+    const bool mk0 = s0 >= 0 && ld(&a.smark[s0]) == stamp;
+    const bool mk1 = s1 >= 0 && ld(&a.smark[s1]) == stamp;
     bool p0 = mk0, p1 = mk1;  // splits off (leader unmarked: exactly the marked members)
     if (lead_marked) {
         // slot ranges of the members, issued with the leader's marks
         const int32_t o0 = s0 >= 0 ? a.off[s0] : 0, q0 = s0 >= 0 ? a.off[s0 + 1] : 0;
         const int32_t o1 = s1 >= 0 ? a.off[s1] : 0, q1 = s1 >= 0 ? a.off[s1 + 1] : 0;
         unsigned lmask = 0;
-        if (k <= 32) lmask = __ballot_sync(0xffffffffu, (int)lane < k && ld(a, &a.mark[lo + lane]) == stamp);
+        if (k <= 32) lmask = __ballot_sync(0xffffffffu, (int)lane < k && ld(&a.mark[lo + lane]) == stamp);
         p0 = s0 >= 0 && !(mk0 && same_marks_at(a, o0, q0 - o0, lo, k, lmask, stamp));
         p1 = s1 >= 0 && !(mk1 && same_marks_at(a, o1, q1 - o1, lo, k, lmask, stamp));
     }
@@ -360,8 +347,8 @@ __device__ __forceinline__ int cta_min(int v, CtaShared& sh) {
 // position range [r0, r0+cnt) by swapping with the states there that are not
 // in the set. in_set(u) tells membership of the state u currently at a
 // position of the range.
-template <class A, typename InSet>
-__device__ void cta_gather_range(const A& a, CtaShared& sh, int32_t t0, int32_t cnt,
+template <typename InSet>
+__device__ void cta_gather_range(const FrontierArgs& a, CtaShared& sh, int32_t t0, int32_t cnt,
                                  int32_t r0, InSet in_set) {
     // outsiders of the set: X = members of the set outside [r0, r0+cnt),
     // compacted in place at mscr[t0 ..); Y = positions inside the range held
@@ -369,8 +356,8 @@ __device__ void cta_gather_range(const A& a, CtaShared& sh, int32_t t0, int32_t 
     int nx = 0;
     for (int32_t base = 0; base < cnt; base += blockDim.x) {
         const int32_t i = base + threadIdx.x;
-        const int32_t s = i < cnt ? ld(a, &a.mscr[t0 + i]) : -1;
-        const bool out = s >= 0 && (ld(a, &a.loc[s]) < r0 || ld(a, &a.loc[s]) >= r0 + cnt);
+        const int32_t s = i < cnt ? ld(&a.mscr[t0 + i]) : -1;
+        const bool out = s >= 0 && (ld(&a.loc[s]) < r0 || ld(&a.loc[s]) >= r0 + cnt);
         int tot;
         const int rk = cta_rank(out, sh, tot);
         if (out) a.mscr[t0 + nx + rk] = s;  // stable in-place compaction (target <= source)
@@ -381,7 +368,7 @@ __device__ void cta_gather_range(const A& a, CtaShared& sh, int32_t t0, int32_t 
     for (int32_t base = 0; base < cnt; base += blockDim.x) {
         const int32_t i = base + threadIdx.x;
         const int32_t q = r0 + i;
-        const bool foreign = i < cnt && !in_set(ld(a, &a.elems[q]));
+        const bool foreign = i < cnt && !in_set(ld(&a.elems[q]));
         int tot;
         const int rk = cta_rank(foreign, sh, tot);
         if (foreign) a.yscr[t0 + ny + rk] = q;
@@ -393,10 +380,10 @@ __device__ void cta_gather_range(const A& a, CtaShared& sh, int32_t t0, int32_t 
         return;
     }
     for (int32_t j = threadIdx.x; j < nx; j += blockDim.x) {
-        const int32_t s = ld(a, &a.mscr[t0 + j]);
-        const int32_t q = ld(a, &a.yscr[t0 + j]);
-        const int32_t p = ld(a, &a.loc[s]);
-        const int32_t u = ld(a, &a.elems[q]);
+        const int32_t s = ld(&a.mscr[t0 + j]);
+        const int32_t q = ld(&a.yscr[t0 + j]);
+        const int32_t p = ld(&a.loc[s]);
+        const int32_t u = ld(&a.elems[q]);
         a.elems[p] = u;
         a.loc[u] = p;
         a.elems[q] = s;
@@ -407,26 +394,25 @@ __device__ void cta_gather_range(const A& a, CtaShared& sh, int32_t t0, int32_t 
 
 // One CTA splits block b (more than WARP_MAX members), touching only the
 // marked members, plus the moved-out part when the leader is marked.
-template <class A>
-__device__ void cta_split(const A& a, const Worklist& wl, CtaShared& sh, int32_t b, uint32_t stamp,
+__device__ void cta_split(const FrontierArgs& a, const Worklist& wl, CtaShared& sh, int32_t b, uint32_t stamp,
                           int32_t C, long long& states) {
     const unsigned lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
-    const int32_t b0 = ld(a, &a.bbeg[b]), e0 = ld(a, &a.bend[b]);
-    const int32_t km = ld(a, &a.mcnt[b]);
+    const int32_t b0 = ld(&a.bbeg[b]), e0 = ld(&a.bend[b]);
+    const int32_t km = ld(&a.mcnt[b]);
     const int32_t t0 = e0 - km;  // marked members are listed in mscr[t0 .. e0)
     const int32_t lo = a.off[b];
     const int32_t k = a.off[b + 1] - lo;
-    const bool lead_marked = ld(a, &a.smark[b]) == stamp;
+    const bool lead_marked = ld(&a.smark[b]) == stamp;
     __syncthreads();
     if (threadIdx.x == 0) a.mcnt[b] = 0;
     if (!lead_marked) {
         // split part = the km marked members; it moves to [t0, e0)
         int mn = NONE;
-        for (int32_t i = threadIdx.x; i < km; i += blockDim.x) mn = min(mn, ld(a, &a.mscr[t0 + i]));
+        for (int32_t i = threadIdx.x; i < km; i += blockDim.x) mn = min(mn, ld(&a.mscr[t0 + i]));
         const int32_t leader = cta_min(mn, sh);
-        for (int32_t i = threadIdx.x; i < km; i += blockDim.x) a.block[ld(a, &a.mscr[t0 + i])] = leader;
+        for (int32_t i = threadIdx.x; i < km; i += blockDim.x) a.block[ld(&a.mscr[t0 + i])] = leader;
         __syncthreads();
-        cta_gather_range(a, sh, t0, km, t0, [&](int32_t u) { return ld(a, &a.smark[u]) == stamp; });
+        cta_gather_range(a, sh, t0, km, t0, [&](int32_t u) { return ld(&a.smark[u]) == stamp; });
         if (threadIdx.x < 32) {
             if (threadIdx.x == 0) {
                 states += km;
@@ -443,7 +429,7 @@ __device__ void cta_split(const A& a, const Worklist& wl, CtaShared& sh, int32_t
     // leader marked: kept part = marked members with the leader's marks
     if (wid == 0) {
         unsigned lm = 0;
-        if (k <= 32) lm = __ballot_sync(0xffffffffu, (int)lane < k && ld(a, &a.mark[lo + lane]) == stamp);
+        if (k <= 32) lm = __ballot_sync(0xffffffffu, (int)lane < k && ld(&a.mark[lo + lane]) == stamp);
         if (lane == 0) sh.lmask = lm;
     }
     __syncthreads();
@@ -451,7 +437,7 @@ __device__ void cta_split(const A& a, const Worklist& wl, CtaShared& sh, int32_t
     int kk = 0;
     for (int32_t base = 0; base < km; base += blockDim.x) {
         const int32_t i = base + threadIdx.x;
-        const int32_t s = i < km ? ld(a, &a.mscr[t0 + i]) : -1;
+        const int32_t s = i < km ? ld(&a.mscr[t0 + i]) : -1;
         const bool keep = s >= 0 && same_marks(a, s, lo, k, lmask, stamp);
         int tot;
         const int rk = cta_rank(keep, sh, tot);
@@ -465,12 +451,12 @@ __device__ void cta_split(const A& a, const Worklist& wl, CtaShared& sh, int32_t
     const int32_t sz = e0 - b0;
     if (threadIdx.x == 0) states += km;
     if (kk == sz) return;  // every member kept: no split
-    cta_gather_range(a, sh, t0, kk, b0, [&](int32_t u) { return ld(a, &a.kmark[u]) == stamp; });
+    cta_gather_range(a, sh, t0, kk, b0, [&](int32_t u) { return ld(&a.kmark[u]) == stamp; });
     // split part = [b0 + kk, e0)
     int mn = NONE;
-    for (int32_t q = b0 + kk + threadIdx.x; q < e0; q += blockDim.x) mn = min(mn, ld(a, &a.elems[q]));
+    for (int32_t q = b0 + kk + threadIdx.x; q < e0; q += blockDim.x) mn = min(mn, ld(&a.elems[q]));
     const int32_t leader = cta_min(mn, sh);
-    for (int32_t q = b0 + kk + threadIdx.x; q < e0; q += blockDim.x) a.block[ld(a, &a.elems[q])] = leader;
+    for (int32_t q = b0 + kk + threadIdx.x; q < e0; q += blockDim.x) a.block[ld(&a.elems[q])] = leader;
     __syncthreads();
     if (threadIdx.x < 32) {
         if (threadIdx.x == 0) {
@@ -488,16 +474,16 @@ __device__ void cta_split(const A& a, const Worklist& wl, CtaShared& sh, int32_t
 // Warp version of the gather: lanes l < cnt hold the members s_l of a set
 // (cnt <= 32) that must end up at positions [r0, r0 + cnt). Members outside
 // the range swap with the non-members inside it, paired by rank.
-template <class A, typename InSet>
-__device__ __forceinline__ void warp_gather(const A& a, int32_t s, int32_t cnt, int32_t r0,
+template <typename InSet>
+__device__ __forceinline__ void warp_gather(const FrontierArgs& a, int32_t s, int32_t cnt, int32_t r0,
                                             InSet in_set) {
     const unsigned lane = threadIdx.x & 31u;
     const unsigned lt = lanemask_lt();
     const bool mine = (int)lane < cnt;
-    const int32_t p = mine ? ld(a, &a.loc[s]) : -1;
+    const int32_t p = mine ? ld(&a.loc[s]) : -1;
     const bool x = mine && (p < r0 || p >= r0 + cnt);
     const int32_t q = r0 + (int32_t)lane;
-    const bool y = mine && !in_set(ld(a, &a.elems[q]));
+    const bool y = mine && !in_set(ld(&a.elems[q]));
     const unsigned xm = __ballot_sync(0xffffffffu, x), ym = __ballot_sync(0xffffffffu, y);
     if (__popc(xm) != __popc(ym)) {
         if (lane == 0) atomicOr(&a.ctrl->status, ST_INTERNAL);
@@ -511,7 +497,7 @@ __device__ __forceinline__ void warp_gather(const A& a, int32_t s, int32_t cnt, 
     }
     const int32_t qq = __shfl_sync(0xffffffffu, q, src);
     if (x) {
-        const int32_t u = ld(a, &a.elems[qq]);
+        const int32_t u = ld(&a.elems[qq]);
         a.elems[p] = u;
         a.loc[u] = p;
         a.elems[qq] = s;
@@ -522,22 +508,21 @@ __device__ __forceinline__ void warp_gather(const A& a, int32_t s, int32_t cnt, 
 
 // One warp splits block b (more than WARP_MAX members) that has at most 32
 // marked members this round.
-template <class A>
-__device__ void warp_split_sparse(const A& a, const Worklist& wl, int32_t b, int32_t b0, int32_t e0,
+__device__ void warp_split_sparse(const FrontierArgs& a, const Worklist& wl, int32_t b, int32_t b0, int32_t e0,
                                   int32_t km, uint32_t stamp, int32_t C, long long& states) {
     const unsigned lane = threadIdx.x & 31u;
     const int32_t t0 = e0 - km;  // marked members listed in mscr[t0 .. e0)
     const int32_t lo = a.off[b];
     const int32_t k = a.off[b + 1] - lo;
-    const bool lead_marked = ld(a, &a.smark[b]) == stamp;
-    const int32_t s = (int)lane < km ? ld(a, &a.mscr[t0 + lane]) : -1;
+    const bool lead_marked = ld(&a.smark[b]) == stamp;
+    const int32_t s = (int)lane < km ? ld(&a.mscr[t0 + lane]) : -1;
     __syncwarp();
     if (lane == 0) a.mcnt[b] = 0;
     if (!lead_marked) {
         // split part = the marked members; they move to [t0, e0)
         const int32_t leader = __reduce_min_sync(0xffffffffu, s >= 0 ? s : NONE);
         if (s >= 0) a.block[s] = leader;
-        warp_gather(a, s, km, t0, [&](int32_t u) { return ld(a, &a.smark[u]) == stamp; });
+        warp_gather(a, s, km, t0, [&](int32_t u) { return ld(&a.smark[u]) == stamp; });
         if (lane == 0) {
             states += km;
             a.bend[b] = t0;
@@ -550,7 +535,7 @@ __device__ void warp_split_sparse(const A& a, const Worklist& wl, int32_t b, int
     }
     // leader marked: kept part = marked members with the leader's marks
     unsigned lmask = 0;
-    if (k <= 32) lmask = __ballot_sync(0xffffffffu, (int)lane < k && ld(a, &a.mark[lo + lane]) == stamp);
+    if (k <= 32) lmask = __ballot_sync(0xffffffffu, (int)lane < k && ld(&a.mark[lo + lane]) == stamp);
     const bool keep = s >= 0 && same_marks(a, s, lo, k, lmask, stamp);
     const unsigned km_mask = __ballot_sync(0xffffffffu, keep);
     const int32_t kk = __popc(km_mask);
@@ -564,12 +549,12 @@ __device__ void warp_split_sparse(const A& a, const Worklist& wl, int32_t b, int
     const int32_t ks = __shfl_sync(0xffffffffu, s, src);
     if ((int)lane < kk) a.kmark[ks] = stamp;
     __syncwarp();
-    warp_gather(a, (int)lane < kk ? ks : -1, kk, b0, [&](int32_t u) { return ld(a, &a.kmark[u]) == stamp; });
+    warp_gather(a, (int)lane < kk ? ks : -1, kk, b0, [&](int32_t u) { return ld(&a.kmark[u]) == stamp; });
     // split part = [b0 + kk, e0): every other member
     int mn = NONE;
-    for (int32_t q = b0 + kk + (int32_t)lane; q < e0; q += 32) mn = min(mn, ld(a, &a.elems[q]));
+    for (int32_t q = b0 + kk + (int32_t)lane; q < e0; q += 32) mn = min(mn, ld(&a.elems[q]));
     const int32_t leader = __reduce_min_sync(0xffffffffu, mn);
-    for (int32_t q = b0 + kk + (int32_t)lane; q < e0; q += 32) a.block[ld(a, &a.elems[q])] = leader;
+    for (int32_t q = b0 + kk + (int32_t)lane; q < e0; q += 32) a.block[ld(&a.elems[q])] = leader;
     __syncwarp();
     if (lane == 0) {
         states += e0 - b0;
@@ -586,8 +571,7 @@ __device__ void warp_split_sparse(const A& a, const Worklist& wl, int32_t b, int
 // when at most 32 members are marked, otherwise one per CTA. CTA `cta` of
 // `ncta` takes its share; `defer` is a CTA-local list of at least
 // blockDim/32 entries.
-template <class A>
-__device__ void split_step(const A& a, const Worklist& wl, CtaShared& sh, int* defer, int* ndefer,
+__device__ void split_step(const FrontierArgs& a, const Worklist& wl, CtaShared& sh, int* defer, int* ndefer,
                            uint32_t stamp, int32_t C, int ns, const int4* small_list, int nm,
                            const int4* mid_list, int cta, int ncta,
                            long long& states) {
@@ -598,8 +582,8 @@ __device__ void split_step(const A& a, const Worklist& wl, CtaShared& sh, int* d
     // warps and CTA-list entries the last, and the first pass over the CTA
     // list runs alongside the warp list
     auto mid_entry = [&](int i) {
-        const int4 t = ld(a, &mid_list[i]);
-        const int32_t km = ld(a, &a.mcnt[t.x]);
+        const int4 t = ld(&mid_list[i]);
+        const int32_t km = ld(&a.mcnt[t.x]);
         if (km <= 32)
             warp_split_sparse(a, wl, t.x, t.y, t.z, km, stamp, C, states);
         else if ((threadIdx.x & 31) == 0)
@@ -612,7 +596,7 @@ __device__ void split_step(const A& a, const Worklist& wl, CtaShared& sh, int* d
         if (i < nm) mid_entry(i);
         if (base == 0)
             for (int64_t q = cta + (int64_t)wid * ncta; q < ns; q += (int64_t)ncta * nw) {
-                const int4 t = ld(a, &small_list[q]);
+                const int4 t = ld(&small_list[q]);
                 warp_split(a, wl, t.x, t.y, t.z, stamp, C, states);
             }
         __syncthreads();
@@ -635,8 +619,7 @@ __device__ void split_step(const A& a, const Worklist& wl, CtaShared& sh, int* d
 // The part of a mark step after the first mark of a source s in its block b
 // (range [bb, be)): rank s among the block's marked members and list b when
 // it is the first. Blocks of one state cannot split and are skipped.
-template <class A>
-__device__ __forceinline__ void rank_marked(const A& a, int32_t s, int32_t b, int32_t bb, int32_t be,
+__device__ __forceinline__ void rank_marked(const FrontierArgs& a, int32_t s, int32_t b, int32_t bb, int32_t be,
                                             int32_t Cw, int* n_small, int* n_mid, int4* small_list,
                                             int4* mid_list) {
     if (be - bb <= 1) return;
@@ -651,8 +634,7 @@ __device__ __forceinline__ void rank_marked(const A& a, int32_t s, int32_t b, in
     }
 }
 
-template <class A>
-__device__ __forceinline__ void mark_member(const A& a, int32_t t, uint32_t stamp, int32_t Cw,
+__device__ __forceinline__ void mark_member(const FrontierArgs& a, int32_t t, uint32_t stamp, int32_t Cw,
                                             int* n_small, int* n_mid, int4* small_list, int4* mid_list,
                                             long long& edges) {
     const int lane = threadIdx.x & 31;
@@ -662,19 +644,18 @@ __device__ __forceinline__ void mark_member(const A& a, int32_t t, uint32_t stam
         const unsigned long long e = a.in_edge[j];
         const int32_t s = (int32_t)(e >> 32);
         a.mark[(uint32_t)e] = stamp;
-        const int32_t b = ld(a, &a.block[s]);  // issued before the atomic: both depend on s only
+        const int32_t b = ld(&a.block[s]);  // issued before the atomic: both depend on s only
         if (atomicExch(&a.smark[s], stamp) == stamp) continue;
-        rank_marked(a, s, b, ld(a, &a.bbeg[b]), ld(a, &a.bend[b]), Cw, n_small, n_mid, small_list, mid_list);
+        rank_marked(a, s, b, ld(&a.bbeg[b]), ld(&a.bend[b]), Cw, n_small, n_mid, small_list, mid_list);
     }
 }
 
-template <class A>
-__device__ __forceinline__ void mark_step(const A& a, int32_t C, uint32_t stamp, int64_t gw,
+__device__ __forceinline__ void mark_step(const FrontierArgs& a, int32_t C, uint32_t stamp, int64_t gw,
                                           int64_t nwarps, int* n_small, int* n_mid, int4* small_list,
                                           int4* mid_list, long long& edges) {
-    const int32_t b0 = ld(a, &a.bbeg[C]), e0 = ld(a, &a.bend[C]);
+    const int32_t b0 = ld(&a.bbeg[C]), e0 = ld(&a.bend[C]);
     for (int64_t idx = b0 + gw; idx < e0; idx += nwarps)
-        mark_member(a, ld(a, &a.elems[idx]), stamp, -1, n_small, n_mid, small_list, mid_list, edges);
+        mark_member(a, ld(&a.elems[idx]), stamp, -1, n_small, n_mid, small_list, mid_list, edges);
 }
 
 // ------------------------------------------- rounds with several splitters
@@ -707,8 +688,7 @@ constexpr int SEL_E = 8;
 // consecutive threads on consecutive ring entries; the sizes of bucket-0
 // entries are known without a load (blocks only shrink and are never empty,
 // so a label pushed with one state still has one).
-template <class A>
-__device__ int select_many(const A& a, const Worklist& wl, unsigned long long* head, CtaShared& sh,
+__device__ int select_many(const FrontierArgs& a, const Worklist& wl, unsigned long long* head, CtaShared& sh,
                            int32_t* selC, int32_t* selP, int kmax, int32_t budget) {
     const unsigned lane = threadIdx.x & 31u;
     kmax = min(kmax, SEL_E * (int)blockDim.x);
@@ -741,7 +721,7 @@ __device__ int select_many(const A& a, const Worklist& wl, unsigned long long* h
                 while (j >= sh.bx[bk] + sh.bn[bk]) bk++;
                 int pos = sh.hp[bk] + (j - sh.bx[bk]);  // < 2 cap: the bucket holds at most cap entries
                 if (pos >= wl.cap) pos -= wl.cap;
-                lv[e] = ld(a, &wl.queue[(size_t)bk * wl.stride + wl.base + pos]);
+                lv[e] = ld(&wl.queue[(size_t)bk * wl.stride + wl.base + pos]);
             }
         }
 #pragma unroll
@@ -772,7 +752,7 @@ __device__ int select_many(const A& a, const Worklist& wl, unsigned long long* h
     int mine = 0;
 #pragma unroll
     for (int e = 0; e < SEL_E; e++) {
-        sz[e] = cs[e] < 0 ? 0 : j0 + e < n0 ? 1 : ld(a, &a.bend[cs[e]]) - ld(a, &a.bbeg[cs[e]]);
+        sz[e] = cs[e] < 0 ? 0 : j0 + e < n0 ? 1 : ld(&a.bend[cs[e]]) - ld(&a.bbeg[cs[e]]);
         mine += sz[e];
     }
     int tot;
@@ -809,8 +789,7 @@ __device__ __forceinline__ int find_sel(const int32_t* selP, int K, int32_t i) {
     return lo;
 }
 
-template <class A>
-__device__ __forceinline__ void claim_label(const A& a, int32_t b, unsigned long long key,
+__device__ __forceinline__ void claim_label(const FrontierArgs& a, int32_t b, unsigned long long key,
                                             uint32_t* lost, uint32_t stamp) {
     const unsigned long long old = atomicMin(&a.claim[b], key);
     if ((old >> 32) == (key >> 32)) {
@@ -825,8 +804,7 @@ __device__ __forceinline__ void claim_label(const A& a, int32_t b, unsigned long
 // Claim phase: splitter j claims its own block and every block of more than
 // one state that holds a predecessor of one of its members. Items (members
 // of the K splitters, in order) go to warps gw, gw + nwarps, ...
-template <class A>
-__device__ void claim_step(const A& a, const int32_t* selC, const int32_t* selP, int K, uint32_t* lost,
+__device__ void claim_step(const FrontierArgs& a, const int32_t* selC, const int32_t* selP, int K, uint32_t* lost,
                            uint32_t stamp, int64_t gw, int64_t nwarps) {
     const int lane = threadIdx.x & 31;
     const int32_t tot = selP[K];
@@ -835,13 +813,13 @@ __device__ void claim_step(const A& a, const int32_t* selC, const int32_t* selP,
         const int j = find_sel(selP, K, (int32_t)i);
         const int32_t C = selC[j];
         const unsigned long long key = hi | (unsigned)j;
-        if (i == selP[j] && lane == 0 && ld(a, &a.bend[C]) - ld(a, &a.bbeg[C]) > 1) claim_label(a, C, key, lost, stamp);
-        const int32_t t = ld(a, &a.elems[ld(a, &a.bbeg[C]) + (int32_t)i - selP[j]]);
+        if (i == selP[j] && lane == 0 && ld(&a.bend[C]) - ld(&a.bbeg[C]) > 1) claim_label(a, C, key, lost, stamp);
+        const int32_t t = ld(&a.elems[ld(&a.bbeg[C]) + (int32_t)i - selP[j]]);
         const int32_t j0 = a.in_ptr[t], j1 = a.in_ptr[t + 1];
         for (int32_t q = j0 + lane; q < j1; q += 32) {
             const int32_t s = (int32_t)(a.in_edge[q] >> 32);
-            const int32_t b = ld(a, &a.block[s]);
-            if (ld(a, &a.bend[b]) - ld(a, &a.bbeg[b]) > 1) claim_label(a, b, key, lost, stamp);
+            const int32_t b = ld(&a.block[s]);
+            if (ld(&a.bend[b]) - ld(&a.bbeg[b]) > 1) claim_label(a, b, key, lost, stamp);
         }
     }
 }
@@ -849,8 +827,7 @@ __device__ void claim_step(const A& a, const int32_t* selC, const int32_t* selP,
 // Mark phase of a round with several splitters: a splitter that lost a claim
 // goes back to the worklist (its unstable flag is still set); a winner
 // clears its unstable flag (Algorithm 3, line 23) and marks as mark_step.
-template <class A>
-__device__ void mark_many(const A& a, const Worklist& wl, const int32_t* selC, const int32_t* selP,
+__device__ void mark_many(const FrontierArgs& a, const Worklist& wl, const int32_t* selC, const int32_t* selP,
                           int K, const uint32_t* lost, uint32_t stamp, int64_t gw, int64_t nwarps, int* n_small,
                           int* n_mid, int4* small_list, int4* mid_list, long long& edges,
                           long long& commits) {
@@ -869,16 +846,14 @@ __device__ void mark_many(const A& a, const Worklist& wl, const int32_t* selC, c
             }
         }
         if (lose) continue;
-        const int32_t t = ld(a, &a.elems[ld(a, &a.bbeg[C]) + (int32_t)i - selP[j]]);
+        const int32_t t = ld(&a.elems[ld(&a.bbeg[C]) + (int32_t)i - selP[j]]);
         mark_member(a, t, stamp, C, n_small, n_mid, small_list, mid_list, edges);
     }
 }
 
 // Pop the next splitter (lowest non-empty size bucket) with warp 0 of the CTA;
 // returns it to every thread, or -1 when the worklist is empty.
-template <class A>
-__device__ __forceinline__ int32_t select_splitter(const A& a, const Worklist& wl, unsigned long long* head,
-                                                   CtaShared& sh) {
+__device__ __forceinline__ int32_t select_splitter(const Worklist& wl, unsigned long long* head, CtaShared& sh) {
     const unsigned lane = threadIdx.x & 31u;
     if (threadIdx.x < 32) {
         const unsigned long long h = head[lane];
@@ -892,7 +867,7 @@ __device__ __forceinline__ int32_t select_splitter(const A& a, const Worklist& w
                 sh.bk = -1;
             }
         } else if ((int)lane == __ffs(bal) - 1) {
-            sh.C = ld(a, &wl.queue[(size_t)lane * wl.stride + wl.base + h % (unsigned long long)wl.cap]);
+            sh.C = ld(&wl.queue[(size_t)lane * wl.stride + wl.base + h % (unsigned long long)wl.cap]);
             sh.bk = (int)lane;
             head[lane] = h + 1;
         }
@@ -903,7 +878,7 @@ __device__ __forceinline__ int32_t select_splitter(const A& a, const Worklist& w
     return C;
 }
 
-__global__ void __launch_bounds__(1024) k_frontier_main(GridArgs a) {
+__global__ void __launch_bounds__(1024) k_frontier_main(FrontierArgs a) {
     __shared__ CtaShared sh;
     __shared__ int s_defer[32];
     __shared__ int s_ndefer;
@@ -922,7 +897,7 @@ __global__ void __launch_bounds__(1024) k_frontier_main(GridArgs a) {
         const uint32_t stamp = a.stamp0 + (uint32_t)r;
         const int par = (int)(r & 1);
         // every CTA pops the same label
-        const int32_t C = select_splitter(a, wl, sh.head, sh);
+        const int32_t C = select_splitter(wl, sh.head, sh);
         if (C < 0) break;  // no unstable label: C = bottom
         if (r > a.round_cap) {
             if (gtid == 0) atomicOr(&a.ctrl->status, ST_ROUNDS);
@@ -936,8 +911,8 @@ __global__ void __launch_bounds__(1024) k_frontier_main(GridArgs a) {
         mark_step(a, C, stamp, gw, nwarps, &a.ctrl->n_touched[par], &a.ctrl->n_mid[par], a.tlist,
                   a.tlist + n, edges);
         if (!grid_sync(a.gb, tgt)) return;
-        split_step(a, wl, sh, s_defer, &s_ndefer, stamp, C, ld(a, &a.ctrl->n_touched[par]), a.tlist,
-                   ld(a, &a.ctrl->n_mid[par]), a.tlist + n, (int)blockIdx.x, (int)gridDim.x, states);
+        split_step(a, wl, sh, s_defer, &s_ndefer, stamp, C, ldcg(&a.ctrl->n_touched[par]), a.tlist,
+                   ldcg(&a.ctrl->n_mid[par]), a.tlist + n, (int)blockIdx.x, (int)gridDim.x, states);
         if (!grid_sync(a.gb, tgt)) return;
     }
     if (edges) atomicAdd((unsigned long long*)&a.ctrl->edges, (unsigned long long)edges);
@@ -974,8 +949,7 @@ struct ItemCarry {
     int32_t b, bb, be;     // its source's block and block range
 };
 
-template <class A>
-__device__ __forceinline__ void claim_item(const A& a, const int32_t* selC, const int32_t* selP, int K,
+__device__ __forceinline__ void claim_item(const FrontierArgs& a, const int32_t* selC, const int32_t* selP, int K,
                                            uint32_t* lost, uint32_t stamp, int64_t i, ItemCarry& ic) {
     const int lane = threadIdx.x & 31;
     ic.j = -1;
@@ -987,31 +961,30 @@ __device__ __forceinline__ void claim_item(const A& a, const int32_t* selC, cons
     const unsigned long long key = ((unsigned long long)(~stamp) << 32) | (unsigned)j;
     int32_t t = C;  // a block of one state holds its label only
     if (selP[j + 1] - selP[j] > 1) {
-        const int32_t cb = ld(a, &a.bbeg[C]);
+        const int32_t cb = ld(&a.bbeg[C]);
         if (i == selP[j] && lane == 0) claim_label(a, C, key, lost, stamp);
-        t = ld(a, &a.elems[cb + (int32_t)i - selP[j]]);
+        t = ld(&a.elems[cb + (int32_t)i - selP[j]]);
     }
     ic.j0 = a.in_ptr[t];
     ic.j1 = a.in_ptr[t + 1];
     const bool has = ic.j0 + lane < ic.j1;
     if (has) {
         ic.e = a.in_edge[ic.j0 + lane];
-        ic.b = ld(a, &a.block[(int32_t)(ic.e >> 32)]);
-        ic.bb = ld(a, &a.bbeg[ic.b]);
-        ic.be = ld(a, &a.bend[ic.b]);
+        ic.b = ld(&a.block[(int32_t)(ic.e >> 32)]);
+        ic.bb = ld(&a.bbeg[ic.b]);
+        ic.be = ld(&a.bend[ic.b]);
     }
     // one claim per distinct block of the warp (sources often share a block)
     const bool cl = has && ic.be - ic.bb > 1;
     const unsigned peers = __match_any_sync(0xffffffffu, cl ? ic.b : -1 - lane);  // every lane gets here
     if (cl && (peers & lanemask_lt()) == 0u) claim_label(a, ic.b, key, lost, stamp);
     for (int32_t q = ic.j0 + 32 + lane; q < ic.j1; q += 32) {
-        const int32_t b = ld(a, &a.block[(int32_t)(a.in_edge[q] >> 32)]);
-        if (ld(a, &a.bend[b]) - ld(a, &a.bbeg[b]) > 1) claim_label(a, b, key, lost, stamp);
+        const int32_t b = ld(&a.block[(int32_t)(a.in_edge[q] >> 32)]);
+        if (ld(&a.bend[b]) - ld(&a.bbeg[b]) > 1) claim_label(a, b, key, lost, stamp);
     }
 }
 
-template <class A>
-__device__ __forceinline__ void mark_item(const A& a, const Worklist& wl, const int32_t* selP,
+__device__ __forceinline__ void mark_item(const FrontierArgs& a, const Worklist& wl, const int32_t* selP,
                                           const uint32_t* lost, uint32_t stamp, int64_t i, const ItemCarry& ic,
                                           int* n_small, int* n_mid, int4* small_list, int4* mid_list,
                                           long long& edges, long long& commits) {
@@ -1038,9 +1011,9 @@ __device__ __forceinline__ void mark_item(const A& a, const Worklist& wl, const 
         const unsigned long long e = a.in_edge[q];
         const int32_t s = (int32_t)(e >> 32);
         a.mark[(uint32_t)e] = stamp;
-        const int32_t b = ld(a, &a.block[s]);
+        const int32_t b = ld(&a.block[s]);
         if (atomicExch(&a.smark[s], stamp) == stamp) continue;
-        rank_marked(a, s, b, ld(a, &a.bbeg[b]), ld(a, &a.bend[b]), ic.C, n_small, n_mid, small_list, mid_list);
+        rank_marked(a, s, b, ld(&a.bbeg[b]), ld(&a.bend[b]), ic.C, n_small, n_mid, small_list, mid_list);
     }
 }
 
@@ -1059,8 +1032,8 @@ struct HybridArgs {
 
 // The three phases of a round with several splitters, by the warps gw,
 // gw + nwarps, ... of the grid (sync = grid barrier) or of one CTA.
-template <class A, typename Sync>
-__device__ __forceinline__ bool multi_round(const A& a, const Worklist& wl, CtaShared& sh, int* defer,
+template <typename Sync>
+__device__ __forceinline__ bool multi_round(const FrontierArgs& a, const Worklist& wl, CtaShared& sh, int* defer,
                                             int* ndefer, const int32_t* selC, const int32_t* selP, int K,
                                             uint32_t* lost, uint32_t stamp, int64_t gw, int64_t nwarps, int* n_small,
                                             int* n_mid, int4* small_list, int4* mid_list, int cta, int ncta,
@@ -1107,7 +1080,7 @@ __device__ __forceinline__ bool multi_round(const A& a, const Worklist& wl, CtaS
 // new command or a new heartbeat from CTA 0. The touched-block counters of
 // grid rounds alternate by round parity; CTA 0 clears the next round's pair.
 template <int MAXT>  // most threads per CTA (sets the register budget)
-__global__ void __launch_bounds__(MAXT, 1) k_frontier_hybrid(GridArgs a, HybridArgs h) {
+__global__ void __launch_bounds__(MAXT, 1) k_frontier_hybrid(FrontierArgs a, HybridArgs h) {
     __shared__ CtaShared sh;
     __shared__ int s_defer[32];
     __shared__ int s_ndefer;
@@ -1149,7 +1122,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_frontier_hybrid(GridArgs a, HybridA
     };
     // zero, or where a one-CTA start handed the refinement over (a field that
     // CTA 0's commands never overwrite, so a late-starting CTA reads it too)
-    if (threadIdx.x < BISIM_BUCKETS) sh.head[threadIdx.x] = ld(a, &c->start_heads[threadIdx.x]);
+    if (threadIdx.x < BISIM_BUCKETS) sh.head[threadIdx.x] = ldcg(&c->start_heads[threadIdx.x]);
     if (threadIdx.x < 32) s_lost[threadIdx.x] = 0u;
     PHASE_RESET();
     __syncthreads();
@@ -1167,7 +1140,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_frontier_hybrid(GridArgs a, HybridA
                     __nanosleep(64);
                     if ((++spins & 31u) == 0) {
                         const unsigned long long now = globaltimer_ns();
-                        const unsigned long long hbv = ld(a, &c->heartbeat);
+                        const unsigned long long hbv = ldcg(&c->heartbeat);
                         if (hbv != hb) {
                             hb = hbv;
                             t0 = now;
@@ -1176,31 +1149,31 @@ __global__ void __launch_bounds__(MAXT, 1) k_frontier_hybrid(GridArgs a, HybridA
                             ab = 1;
                             break;
                         }
-                        if (ld(a, &c->status) & ST_ABORT_MASK) {
+                        if (ldcg(&c->status) & ST_ABORT_MASK) {
                             ab = 1;
                             break;
                         }
                     }
                 }
                 seen = v;
-                s_cmd = ab ? -1 : ld(a, &c->cmd_C);
-                s_stamp = ld(a, &c->cmd_stamp);
-                s_K = ld(a, &c->cmd_K);
+                s_cmd = ab ? -1 : ldcg(&c->cmd_C);
+                s_stamp = ldcg(&c->cmd_stamp);
+                s_K = ldcg(&c->cmd_K);
             }
             __syncthreads();
             const int32_t C = s_cmd;
             const uint32_t stamp = s_stamp;
             const int K = s_K;
             if (C == -1) break;
-            if (threadIdx.x < BISIM_BUCKETS) sh.head[threadIdx.x] = ld(a, &c->cmd_heads[threadIdx.x]);
+            if (threadIdx.x < BISIM_BUCKETS) sh.head[threadIdx.x] = ldcg(&c->cmd_heads[threadIdx.x]);
             if (C == MULTI) {
                 // K <= SEL_E * blockDim: every load is issued before the first store
                 int32_t vc[SEL_E], vp[SEL_E + 1];
 #pragma unroll
                 for (int e = 0; e <= SEL_E; e++) {
                     const int i = e * (int)blockDim.x + (int)threadIdx.x;
-                    if (e < SEL_E) vc[e] = i < K ? ld(a, &h.g_selC[i]) : 0;
-                    vp[e] = i <= K ? ld(a, &h.g_selP[i]) : 0;
+                    if (e < SEL_E) vc[e] = i < K ? ldcg(&h.g_selC[i]) : 0;
+                    vp[e] = i <= K ? ldcg(&h.g_selP[i]) : 0;
                 }
 #pragma unroll
                 for (int e = 0; e <= SEL_E; e++) {
@@ -1225,7 +1198,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_frontier_hybrid(GridArgs a, HybridA
             K = select_many(a, wl, sh.head, sh, s_selC, s_selP, kmax, h.budget);
             C = K > 0 ? s_selC[0] : -1;
         } else {
-            C = select_splitter(a, wl, sh.head, sh);
+            C = select_splitter(wl, sh.head, sh);
             K = C >= 0 ? 1 : 0;
         }
         PHASE(0);
@@ -1251,12 +1224,12 @@ __global__ void __launch_bounds__(MAXT, 1) k_frontier_hybrid(GridArgs a, HybridA
             local = s_selP[K] <= h.local_budget;
         } else {
             if (threadIdx.x < 32) {
-                const int32_t b0 = ld(a, &a.bbeg[C]), e0 = ld(a, &a.bend[C]);
+                const int32_t b0 = ld(&a.bbeg[C]), e0 = ld(&a.bend[C]);
                 int heavy = 1;
                 if (e0 - b0 <= 32) {
                     int deg = 0;
                     if ((int)threadIdx.x < e0 - b0) {
-                        const int32_t t = ld(a, &a.elems[b0 + threadIdx.x]);
+                        const int32_t t = ld(&a.elems[b0 + threadIdx.x]);
                         deg = a.in_ptr[t + 1] - a.in_ptr[t];
                     }
                     heavy = __reduce_add_sync(0xffffffffu, deg) > h.light_edges;
@@ -1360,7 +1333,7 @@ struct BatchArgs {
     unsigned long long handoff_round_ns;
 };
 
-__global__ void __launch_bounds__(1024) k_frontier_batch(CtaArgs a, BatchArgs bt) {
+__global__ void __launch_bounds__(1024) k_frontier_batch(FrontierArgs a, BatchArgs bt) {
     __shared__ CtaShared sh;
     __shared__ int s_defer[32];
     __shared__ int s_ndefer;
@@ -1386,7 +1359,7 @@ __global__ void __launch_bounds__(1024) k_frontier_batch(CtaArgs a, BatchArgs bt
         const int32_t ni = bt.state_off ? (int32_t)(bt.state_off[li + 1] - s0) : a.n;
         if (threadIdx.x < BISIM_BUCKETS) {
             // a single LTS finds its worklist filled by the whole grid (k_front_queue)
-            s_tail[threadIdx.x] = bt.order ? 0ull : ld(a, &a.ctrl->bq_tail[threadIdx.x]);
+            s_tail[threadIdx.x] = bt.order ? 0ull : ldcg(&a.ctrl->bq_tail[threadIdx.x]);
             sh.head[threadIdx.x] = 0;
         }
         // the round stamps restart with every LTS: forget this CTA's last losses
@@ -1427,7 +1400,7 @@ __global__ void __launch_bounds__(1024) k_frontier_batch(CtaArgs a, BatchArgs bt
                 K = select_many(a, wl, sh.head, sh, s_selC, s_selP, kmax_i, budget);
                 C = K > 0 ? s_selC[0] : -1;
             } else {
-                C = select_splitter(a, wl, sh.head, sh);
+                C = select_splitter(wl, sh.head, sh);
                 K = C >= 0 ? 1 : 0;
             }
             if (K == 0) break;
@@ -1436,7 +1409,7 @@ __global__ void __launch_bounds__(1024) k_frontier_batch(CtaArgs a, BatchArgs bt
                 // a popped label of size bucket k had at least 2^k states when it was
                 // pushed; it may have shrunk since, so only then is its size looked up
                 if (!many && bt.handoff_states > 0 && (1ll << sh.bk) > bt.handoff_states) {
-                    if (threadIdx.x == 0) s_ns = ld(a, &a.bend[C]) - ld(a, &a.bbeg[C]);
+                    if (threadIdx.x == 0) s_ns = ld(&a.bend[C]) - ld(&a.bbeg[C]);
                     __syncthreads();
                     rs = s_ns;
                     __syncthreads();
@@ -1688,7 +1661,7 @@ int refine_frontier_local(bisim_plan_s* p, int64_t cap, uint32_t base, int hando
     bt.handoff_round_ns = BISIM_HANDOFF_ROUND_NS;
     const int threads = p->opts.threads > 0 ? p->opts.threads : 1024;
     BISIM_CUDA_TRY(cudaEventRecord(p->evk0, st));
-    k_frontier_batch<<<1, threads, 0, st>>>(CtaArgs{a}, bt);
+    k_frontier_batch<<<1, threads, 0, st>>>(a, bt);
     BISIM_LAUNCHED();
     BISIM_CUDA_TRY(cudaGetLastError());
     BISIM_CUDA_TRY(cudaEventRecord(p->evk1, st));
@@ -1735,7 +1708,7 @@ int refine_frontier(bisim_plan_s* p, bisim_stats* stats) {
         done = p->ctrl_h->rounds;
         done_commits = p->ctrl_h->local_rounds - 1;
     }
-    GridArgs a{make_args(p, base + (uint32_t)done, cap - done)};
+    FrontierArgs a = make_args(p, base + (uint32_t)done, cap - done);
     const int threads = p->opts.threads > 0 ? p->opts.threads : 512;
     const int light = p->opts.light_edges == 0 ? 256 : p->opts.light_edges;
     int grid = 0;
@@ -1835,7 +1808,7 @@ int refine_frontier_batch(bisim_plan_s* p, bisim_stats* stats, std::vector<long 
         BatchArgs bw = bt;
         bw.k = kw;
         bw.next = &p->ctrl.as<bisim_ctrl>()->next_inst_wide;
-        k_frontier_batch<<<gridw, p->opts.wide_threads, 0, p->aux_stream>>>(CtaArgs{a}, bw);
+        k_frontier_batch<<<gridw, p->opts.wide_threads, 0, p->aux_stream>>>(a, bw);
         BISIM_LAUNCHED();
         BISIM_CUDA_TRY(cudaGetLastError());
         BISIM_CUDA_TRY(cudaEventRecord(p->aux_event, p->aux_stream));
@@ -1845,7 +1818,7 @@ int refine_frontier_batch(bisim_plan_s* p, bisim_stats* stats, std::vector<long 
         BatchArgs bn = bt;
         bn.k = k - kw;
         bn.order = bt.order + kw;
-        k_frontier_batch<<<grid, threads, 0, st>>>(CtaArgs{a}, bn);
+        k_frontier_batch<<<grid, threads, 0, st>>>(a, bn);
         BISIM_LAUNCHED();
         BISIM_CUDA_TRY(cudaGetLastError());
     }
