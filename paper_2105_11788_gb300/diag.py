@@ -94,13 +94,14 @@ def fanout(sizes=(10, 100, 200, 300, 400, 500, 600, 700, 10_000, 100_000, 1_000_
 def phases(workloads=("qexp", "powerlaw2m", "kripke"), repeats: int = 2):
     """Per-phase time of the hybrid rounds (phase-timer build of the library):
     microseconds per multi-splitter round for each phase, and the counts."""
+    o = bisim.make_opts(local_states=-1)  # the hybrid schedule from the first round
     for wl in workloads:
         lts = WORKLOADS[wl]()
-        bisim.reduce(lts)  # warm-up
+        bisim.reduce(lts, o)  # warm-up
         bisim.bisim_phase_reset()
         best = None
         for _ in range(repeats):
-            _, st = bisim.reduce(lts, return_stats=True)
+            _, st = bisim.reduce(lts, o, return_stats=True)
             best = st.t_main_ms if best is None else min(best, st.t_main_ms)
         ph = bisim.bisim_phase_times()
         rounds = max(ph["multi_rounds"], 1)
