@@ -440,6 +440,9 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="stream: skip the launch-shape tuner")
+    ap.add_argument("--hbm-rounds", type=int, default=-1,
+                    help="also time the paper's bandwidth-bound rounds (literal label rounds and a "
+                         "window of this many dense rounds); -1 = 200 for the power-law workload, else off")
     args = ap.parse_args()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
@@ -556,6 +559,14 @@ def main():
             e2e_ms.append(1000 * (time.perf_counter() - t0))
     e2e_step = max_over_ranks(sum(e2e_ms) / len(e2e_ms), world, dev)
     h2d = lts.nbytes()
+    paper_hbm = None
+    hbm_window = args.hbm_rounds if args.hbm_rounds >= 0 else (200 if args.workload == "powerlaw" else 0)
+    if hbm_window > 0:
+        from paper_2105_11788_gb300 import diag
+
+        diag.paper_rounds(lts, src, act, dst, init, window=min(hbm_window, 20))  # warm-up
+        paper_hbm = diag.paper_rounds(lts, src, act, dst, init, window=hbm_window, peak=hbm,
+                                      peak_kind=peak_kind)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(lts, args.cpu_budget)
@@ -573,6 +584,7 @@ def main():
                              else "inputs larger than L2",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "roofline": roof,
+            "hbm_rounds": paper_hbm,
             "e2e": {"value": world * 1000.0 / e2e_step, "unit": "LTS/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4 * lts.n,
                     "ms_per_step": e2e_step},

@@ -124,12 +124,12 @@ def _hbm_peak():
         return 6800.0, "fallback"
 
 
-def hbm(window: int = 200, repeats: int = 3, n: int = 10_000_000):
-    """The bandwidth-bound rounds of the paper's method on the 10^7-state
-    power-law LTS: the literal action-set preprocessing rounds (one pass over
-    the states per label) and a window of `window` dense main rounds (every
-    round scans all states and mark slots; the window ends with the round cap,
-    BISIM_EROUNDS, since the whole dense run takes ~10^7 rounds). Achieved
+def paper_rounds(lts, src, act, dst, init, window: int = 200, peak: float = None, peak_kind: str = None) -> dict:
+    """The bandwidth-bound rounds of the paper's method on one LTS (device
+    tensors src/act/dst/init): the literal action-set preprocessing rounds
+    (one pass over the states per label) and a window of `window` dense main
+    rounds (every round scans all states and mark slots; the window ends with
+    the round cap, BISIM_EROUNDS, when the whole dense run is longer). Achieved
     GB/s of algorithmic bytes against the HBM peak:
       label round: 14 B per state (block, own and leader's label-set word,
                    split flag written and read);
@@ -139,28 +139,37 @@ def hbm(window: int = 200, repeats: int = 3, n: int = 10_000_000):
 
     import torch
 
-    peak, kind = _hbm_peak()
+    if peak is None:
+        peak, peak_kind = _hbm_peak()
+    out = torch.empty(max(lts.n, 1), dtype=torch.int32, device=src.device)
+    lib = bisim.load()
+    opts = bisim.make_opts(engine=bisim.ENGINE_DENSE, preprocess=1, round_cap=window)
+    with bisim.Plan(lts.n, lts.num_act, src, act, dst, init, opts) as p:
+        st = bisim.bisim_stats()
+        rc = lib.bisim_refine(p.handle, out.data_ptr(), ctypes.byref(st))
+    label_bytes = 14.0 * st.n * st.pre_rounds
+    dense_bytes = st.rounds * (30.0 * st.n + 8.0 * st.mark_length) + 12.0 * st.edges_visited
+    lab_gbs = label_bytes / (st.t_pre_ms * 1e6) if st.t_pre_ms > 0 else 0.0
+    den_gbs = dense_bytes / (st.t_main_ms * 1e6) if st.t_main_ms > 0 else 0.0
+    return {"peak_gbs": peak, "peak_kind": peak_kind,
+            "label_rounds": {"kernel": "k_label_rounds", "rounds": st.pre_rounds, "ms": st.t_pre_ms,
+                             "bytes": label_bytes, "gbs": lab_gbs, "frac": lab_gbs / peak},
+            "dense_window": {"kernel": "k_dense_main", "rounds": st.rounds, "ms": st.t_main_ms,
+                             "bytes": dense_bytes, "gbs": den_gbs, "frac": den_gbs / peak,
+                             "us_per_round": 1e3 * st.t_main_ms / max(st.rounds, 1),
+                             "ended_by_round_cap": rc == bisim.BISIM_EROUNDS}}
+
+
+def hbm(window: int = 200, repeats: int = 3, n: int = 10_000_000):
+    """paper_rounds on the 10^7-state power-law LTS, `repeats` times."""
+    import torch
+
     lts = lts_gen.powerlaw(seed=3, n=n)
     d = lambda a: torch.from_numpy(a).cuda()  # noqa: E731
     src, act, dst, init = d(lts.src), d(lts.act), d(lts.dst), d(lts.init)
-    out = torch.empty(lts.n, dtype=torch.int32, device="cuda")
-    lib = bisim.load()
     for rep in range(repeats):
-        opts = bisim.make_opts(engine=bisim.ENGINE_DENSE, preprocess=1, round_cap=window)
-        with bisim.Plan(lts.n, lts.num_act, src, act, dst, init, opts) as p:
-            st = bisim.bisim_stats()
-            rc = lib.bisim_refine(p.handle, out.data_ptr(), ctypes.byref(st))
-        label_bytes = 14.0 * st.n * st.pre_rounds
-        dense_bytes = st.rounds * (30.0 * st.n + 8.0 * st.mark_length) + 12.0 * st.edges_visited
-        print(json.dumps({
-            "workload": f"powerlaw n={n}", "rep": rep, "peak_gbs": peak, "peak_kind": kind,
-            "label_rounds": {"rounds": st.pre_rounds, "ms": st.t_pre_ms, "bytes": label_bytes,
-                             "gbs": label_bytes / (st.t_pre_ms * 1e6), "frac": label_bytes / (st.t_pre_ms * 1e6) / peak},
-            "dense_window": {"rounds": st.rounds, "ms": st.t_main_ms, "bytes": dense_bytes,
-                             "gbs": dense_bytes / (st.t_main_ms * 1e6),
-                             "frac": dense_bytes / (st.t_main_ms * 1e6) / peak,
-                             "us_per_round": 1e3 * st.t_main_ms / max(st.rounds, 1),
-                             "ended_by_round_cap": rc == bisim.BISIM_EROUNDS}}), flush=True)
+        print(json.dumps({"workload": f"powerlaw n={n}", "rep": rep,
+                          **paper_rounds(lts, src, act, dst, init, window)}), flush=True)
 
 
 def main(argv):
