@@ -70,7 +70,9 @@ typedef struct bisim_opts {
                             not set unstable again after a split); 0: Algorithm 3 */
     int32_t raw_labels;  /* 1: bisim_refine writes leader labels instead of
                             canonical ids (testing the election rule) */
-    int32_t threads;     /* threads per CTA for the persistent kernels (0 = 512) */
+    int32_t threads;     /* threads per CTA for the persistent kernels (0 = 512; the
+                            one-CTA start of the frontier engine: 0 = 1024; a batch:
+                            0 = 256) */
     int32_t ctas_per_sm; /* CTAs per SM for the persistent kernels (0 = 1) */
     int32_t test_hook;   /* testing only: 1 = CTA 0 of the refinement kernel
                             leaves before its first barrier, so the other CTAs'
