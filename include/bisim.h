@@ -95,14 +95,15 @@ typedef struct bisim_opts {
     int32_t wide_min_states; /* batch: LTSs with at least this many states go to the
                                 wide launch */
     int32_t splitters;       /* frontier engine: most splitters per round (0 = 8192 for
-                                one LTS, at most 8 per thread of a CTA; 0 = 1 for a
-                                batch, at most 128 per CTA; 1 = one splitter per round,
-                                as in Algorithm 3).
+                                one LTS on the grid, at most 8 per thread of a CTA;
+                                0 = 32 on the one-CTA start and 1 for a batch, at most
+                                128 per CTA; 1 = one splitter per round, as in
+                                Algorithm 3).
                                 Splitters whose touched blocks overlap are deferred to
                                 a later round */
     int32_t split_budget;    /* frontier engine, rounds with several splitters: at most
                                 this many splitter states per warp (0 = 1 on the grid,
-                                8 per CTA of a batch) */
+                                4 on the one-CTA start, 8 per CTA of a batch) */
     int32_t multi_min_states; /* batch: only LTSs with at least this many states take
                                  several splitters per round (0 = every LTS) */
     int32_t local_states;     /* frontier engine, one LTS: start on a single CTA with CTA
