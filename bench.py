@@ -220,6 +220,9 @@ def run_reference(args, world, rank):
 
     if world > 1 and rank != 0:
         return
+    if args.workload == "stream":
+        run_reference_stream(args, world)
+        return
     desc, make = workload(args)
     lts = make()
     for _ in range(args.warmup):
@@ -250,6 +253,39 @@ def run_reference(args, world, rank):
 
 STREAM_DESC = ("batched stream (seed 4): LTSs with n log-uniform in [100, 200000], m = 5n, |Act| in "
                "[1, 32], quotient expansion with n/20 classes")
+
+
+def run_reference_stream(args, world):
+    """CPU oracle on the stream: every step reduces the same bounded sample
+    (the first `--ref-sample` LTSs of the stream, a random draw of its size
+    mix) one after the other; LTS/s = sample size / step time."""
+    import oracle
+
+    k = max(1, min(args.ref_sample, args.stream_k))
+    ltss, _ = lts_gen.batch_stream(seed=4, k=k)
+    for _ in range(args.warmup):
+        for lts in ltss:
+            oracle.ks_lts(lts)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        for lts in ltss:
+            oracle.ks_lts(lts)
+        times.append(time.perf_counter() - t0)
+    ms = 1000.0 * sum(times) / len(times)
+    value = k * 1000.0 / ms
+    sample = (f"the first {k} LTSs of the {args.stream_k}-LTS stream ({sum(l.n for l in ltss)} states) "
+              f"reduced one after the other by oracle_ks (single-threaded C), {args.steps} times")
+    line = {
+        "impl": "reference", "metric": "batched LTS reduction throughput", "value": value,
+        "unit": "LTS/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int32", "data": "synthetic",
+        "config": {"workload": STREAM_DESC, "k": args.stream_k, "sample": k, "l2": "CPU run"},
+        "cpu_baseline": {"value": value, "unit": "LTS/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "LTS/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
 
 
 def run_stream(args, world, rank, local):
@@ -428,6 +464,8 @@ def main():
     ap.add_argument("--stream-k", type=int, default=4096, help="LTSs in the stream workload")
     ap.add_argument("--plain-sample", type=int, default=128,
                     help="stream: LTSs reduced one at a time to estimate the plain rate")
+    ap.add_argument("--ref-sample", type=int, default=24,
+                    help="stream, --impl reference: LTSs of the stream the oracle reduces per step")
     ap.add_argument("--serve-requests", type=int, default=512,
                     help="stream: requests per arrival rate in the serving run")
     ap.add_argument("--engine", default="auto", choices=["auto", "dense", "frontier", "pair"])

@@ -64,3 +64,20 @@ def test_ratio_to_the_paper_fan_out_time():
     ms = bench.PAPER_FANOUT_MS[700]
     assert abs(bench.vs_paper(args, 1000.0 / ms) - 1.0) < 1e-12
     assert bench.vs_paper(types.SimpleNamespace(workload="qexp", fanout_n=700), 5.0) is None
+
+
+def test_reference_arm_lines():
+    """`bench.py --impl reference` times the oracle on the host and prints the
+    contract's line, for a single-LTS workload and for the stream."""
+    import subprocess
+    import sys
+
+    for extra in (["--workload", "kripke"], ["--workload", "stream", "--ref-sample", "4"]):
+        r = subprocess.run([sys.executable, os.path.join(bench.ROOT, "bench.py"), "--impl", "reference",
+                            "--steps", "1", "--warmup", "0", *extra],
+                           capture_output=True, text=True, timeout=600, cwd=bench.ROOT)
+        assert r.returncode == 0, r.stderr
+        line = json.loads([x for x in r.stdout.splitlines() if x.startswith("{")][-1])
+        assert line["impl"] == "reference" and line["unit"] == "LTS/s" and line["value"] > 0
+        assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+        assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
