@@ -178,6 +178,24 @@ def ks_lts(lts, **kw):
     return ks(lts.n, lts.num_act, lts.src, lts.act, lts.dst, lts.init, **kw)
 
 
+def _ks_job(job):
+    return ks(*job)
+
+
+def ks_many(ltss, processes=None):
+    """oracle_ks on many LTSs, in a pool of worker processes started with
+    'spawn' (safe in a process that has already initialised CUDA). Each job
+    carries plain arrays, so the workers import only this package."""
+    import multiprocessing as mp
+
+    jobs = [(l.n, l.num_act, l.src, l.act, l.dst, l.init) for l in ltss]
+    processes = processes or min(16, os.cpu_count() or 1)
+    if processes <= 1 or len(jobs) < 2:
+        return [_ks_job(j) for j in jobs]
+    with mp.get_context("spawn").Pool(processes) as pool:
+        return pool.map(_ks_job, jobs, chunksize=max(1, len(jobs) // (8 * processes)))
+
+
 def pram_lts(lts, **kw):
     return pram(lts.n, lts.num_act, lts.src, lts.act, lts.dst, lts.init, **kw)
 

@@ -34,12 +34,49 @@ def num_blocks(part) -> int:
     return int(np.unique(np.asarray(part)).shape[0])
 
 
+def _unique_rows(cols, return_counts=False):
+    """np.unique over the rows formed by the non-negative int64 columns
+    `cols`. When the product of the column ranges fits in 63 bits each row is
+    packed into one int64 (mixed radix, first column most significant) and
+    the unique keys are unpacked again; otherwise the rows are compared as
+    rows. Both give the same rows in the same (lexicographic) order."""
+    cols = [np.asarray(c, dtype=np.int64) for c in cols]
+    radix = [int(c.max()) + 1 if c.size else 1 for c in cols]
+    span = 1
+    for r in radix:
+        span *= r
+    if span < (1 << 63) and not packed_disabled:
+        key = np.zeros(cols[0].shape[0], dtype=np.int64)
+        for c, r in zip(cols, radix):
+            key = key * r + c
+        key = np.sort(key)
+        first = np.ones(key.shape[0], dtype=bool)
+        first[1:] = key[1:] != key[:-1]
+        starts = np.flatnonzero(first)
+        uk = key[starts]
+        out = []
+        for r in reversed(radix):
+            out.append(uk % r)
+            uk = uk // r
+        rows = np.stack(out[::-1], axis=1)
+        if return_counts:
+            return rows, np.diff(np.append(starts, key.shape[0]))
+        return rows
+    return np.unique(np.stack(cols, axis=1), axis=0, return_counts=return_counts)
+
+
+# tests set this to check that the packed and the row-wise paths agree
+packed_disabled = False
+
+
 def refines(fine, coarse) -> bool:
     """True iff every block of `fine` lies inside one block of `coarse`."""
-    fine = np.asarray(fine)
-    coarse = np.asarray(coarse)
-    pairs = np.unique(np.stack([fine, coarse], axis=1), axis=0)
-    return pairs.shape[0] == np.unique(fine).shape[0]
+    fine = np.asarray(fine, dtype=np.int64)
+    coarse = np.asarray(coarse, dtype=np.int64)
+    if fine.size == 0:
+        return True
+    pairs = _unique_rows([fine, coarse])
+    return pairs.shape[0] == _unique_rows([fine]).shape[0]
 
 
 def is_stable(n, src, act, dst, part) -> bool:
@@ -51,9 +88,8 @@ def is_stable(n, src, act, dst, part) -> bool:
     src = np.asarray(src, dtype=np.int64)
     act = np.asarray(act, dtype=np.int64)
     dst = np.asarray(dst, dtype=np.int64)
-    reach = np.unique(np.stack([src, act, part[dst]], axis=1), axis=0)  # s reaches U with a
-    keys = np.stack([part[reach[:, 0]], reach[:, 1], reach[:, 2]], axis=1)
-    ukeys, counts = np.unique(keys, axis=0, return_counts=True)
+    reach = _unique_rows([src, act, part[dst]])  # s reaches U with a
+    ukeys, counts = _unique_rows([part[reach[:, 0]], reach[:, 1], reach[:, 2]], return_counts=True)
     size = np.bincount(part, minlength=int(part.max()) + 1)
     return bool(np.all(counts == size[ukeys[:, 0]]))
 

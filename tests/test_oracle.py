@@ -303,6 +303,34 @@ def test_stability_checker_detects_unstable():
     assert not defs.is_stable(5, src, act, dst, [0, 0, 2, 3, 3])
 
 
+def test_packed_and_row_wise_checks_agree(monkeypatch):
+    """The stability and refinement checks pack each row into one int64 when
+    the column ranges allow it; on random LTSs and random, coarsest and
+    perturbed partitions both paths give the same answers."""
+    rng = np.random.default_rng(123)
+    answers = []
+    for seed in range(60):
+        n = int(rng.integers(1, 30))
+        lts = lts_gen.random_small(seed, n, int(rng.integers(1, 4)), int(rng.integers(0, 4 * n)), blocks=2)
+        coarsest = oracle.ks_lts(lts)
+        parts = [coarsest, rng.integers(0, 3, n), np.arange(n), np.zeros(n, np.int64)]
+        if n > 1:
+            bad = coarsest.copy()
+            bad[0] = bad[1]
+            parts.append(bad)
+        for part in parts:
+            got = []
+            for disabled in (False, True):
+                monkeypatch.setattr(defs, "packed_disabled", disabled)
+                got.append((defs.is_stable(lts.n, lts.src, lts.act, lts.dst, part),
+                            defs.refines(part, coarsest), defs.refines(coarsest, part)))
+            assert got[0] == got[1], (seed, list(part))
+            answers.append(got[0])
+    # both outcomes occur, so the comparison is not vacuous
+    assert {a[0] for a in answers} == {True, False}
+    assert {a[1] for a in answers} == {True, False}
+
+
 def test_invalid_inputs_rejected():
     s = np.array([0, 5], dtype=np.int32)
     z = np.zeros(2, dtype=np.int32)
