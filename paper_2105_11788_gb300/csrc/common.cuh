@@ -103,10 +103,15 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 
 // Grid-wide barrier for a cooperative (co-resident) launch. The counter is
 // monotonic and zeroed before the launch; every CTA adds one per barrier and
-// waits until the counter reaches (barriers passed) x gridDim.x. Every wait is
-// bounded: after timeout_ns (measured with the global timer) or a spin cap,
-// or when another CTA has raised an abort bit, the CTA gives up, records
-// ST_TIMEOUT, and the caller returns. Returns false when the caller must stop.
+// waits until the counter reaches (barriers passed) x gridDim.x. Ordering:
+// __syncthreads orders the CTA's writes before thread 0's arrive, a release
+// add at GPU scope (cumulative, so it publishes them), and the acquire load
+// that ends the wait, followed by __syncthreads, orders the other CTAs'
+// writes before everything this CTA does next; no separate fences are needed.
+// Every wait is bounded: after timeout_ns (measured with the global timer) or
+// a spin cap, or when another CTA has raised an abort bit, the CTA gives up,
+// records ST_TIMEOUT, and the caller returns. Returns false when the caller
+// must stop.
 struct GridBarrier {
     unsigned long long* counter;
     int* status;
@@ -119,7 +124,6 @@ __device__ __forceinline__ bool grid_sync(const GridBarrier& gb, unsigned long l
     target += gridDim.x;
     if (threadIdx.x == 0) {
         int ab = 0;
-        __threadfence();
         red_release_add_u64(gb.counter, 1ull);
         unsigned long long t0 = 0;
         unsigned spins = 0;
@@ -140,7 +144,6 @@ __device__ __forceinline__ bool grid_sync(const GridBarrier& gb, unsigned long l
                 }
             }
         }
-        __threadfence();
         s_abort = ab;
     }
     __syncthreads();
