@@ -116,6 +116,16 @@ typedef struct bisim_opts {
                                  half of the splitters won or that took more than
                                  25 us each; negative = never (hybrid or grid
                                  schedule from the start) */
+    int32_t peel;             /* frontier engine, grid rounds with several splitters:
+                                 0 = several splitters may split one block in the same
+                                 round when each of them marks exactly one member of
+                                 it and not its leader (the members are split off one
+                                 by one, as the iterations would do one after the
+                                 other); -1 = every touched block is taken by one
+                                 splitter per round */
+    int32_t peel_items;       /* frontier engine, grid rounds with several splitters:
+                                 at most this many splitters of one state per warp of
+                                 the grid (0 = 8) */
 } bisim_opts;
 
 typedef struct bisim_stats {
@@ -278,6 +288,18 @@ int bisim_barrier_cost(int32_t ctas, int32_t threads, int32_t iters, void* strea
  */
 int bisim_phase_times(uint64_t* out16);
 int bisim_phase_reset(void);
+
+/*
+ * bisim_phase_trace - diagnostic, same build and purpose as bisim_phase_times:
+ * a per-round record of the hybrid rounds of the last launches (rounds
+ * 1 .. 65536, later rounds are not recorded; cleared by bisim_phase_reset).
+ * out: host array of 6 * max_rounds uint32, per round: splitters selected,
+ * worklist entries before the selection, touched blocks, splitter iterations
+ * carried out, round time in ns (CTA 0's view), 1 if the round ran on CTA 0
+ * alone. Synchronises the device. Errors: BISIM_EINVAL (out NULL or
+ * max_rounds < 0), BISIM_ECUDA, BISIM_ENOTSUP (default build).
+ */
+int bisim_phase_trace(uint32_t* out, int32_t max_rounds);
 
 /* Largest n accepted by bisim_canonical_ids_noalloc. */
 #define BISIM_NOALLOC_MAX_N (1 << 20)

@@ -51,6 +51,8 @@ class bisim_opts(ctypes.Structure):
         ("split_budget", ctypes.c_int32),
         ("multi_min_states", ctypes.c_int32),
         ("local_states", ctypes.c_int32),
+        ("peel", ctypes.c_int32),
+        ("peel_items", ctypes.c_int32),
     ]
 
 
@@ -158,10 +160,11 @@ def make_opts(engine: int = ENGINE_AUTO, rcpp_alg2: bool = False, raw_labels: bo
               test_hook: int = 0, max_ctas: int = 0, light_edges: int = 0,
               preprocess: int = 0, wide_threads: int = 0, wide_min_states: int = 0,
               splitters: int = 0, split_budget: int = 0, multi_min_states: int = 0,
-              local_states: int = 0) -> bisim_opts:
+              local_states: int = 0, peel: int = 0, peel_items: int = 0) -> bisim_opts:
     return bisim_opts(engine, int(rcpp_alg2), int(raw_labels), threads, ctas_per_sm, test_hook,
                       round_cap, timeout_ms, max_ctas, light_edges, preprocess, wide_threads,
-                      wide_min_states, splitters, split_budget, multi_min_states, local_states)
+                      wide_min_states, splitters, split_budget, multi_min_states, local_states, peel,
+                      peel_items)
 
 
 # ----------------------------------------------------------- C-ABI mirrors
@@ -312,6 +315,18 @@ def bisim_phase_times() -> dict:
     buf = (ctypes.c_uint64 * 16)()
     _check(f(ctypes.addressof(buf)), "bisim_phase_times")
     return {k: int(v) for k, v in zip(PHASE_NAMES, buf)}
+
+
+def bisim_phase_trace(max_rounds: int = 1 << 16):
+    """Per-round trace of a phase-timer build: a list of (selected, worklist,
+    touched, carried out, ns, on CTA 0 alone) per recorded round."""
+    f = load().bisim_phase_trace
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int32]
+    f.restype = ctypes.c_int
+    buf = (ctypes.c_uint32 * (6 * max_rounds))()
+    _check(f(ctypes.addressof(buf), max_rounds), "bisim_phase_trace")
+    v = list(buf)
+    return [tuple(v[6 * i:6 * i + 6]) for i in range(max_rounds)]
 
 
 def bisim_canonical_ids_noalloc(labels: int, n: int, out_ids: int, stream: int = 0) -> int:

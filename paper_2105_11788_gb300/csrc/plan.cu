@@ -434,6 +434,9 @@ int reserve_stamps(bisim_plan_s* p, int64_t rounds, uint32_t* base) {
                 BISIM_CUDA_TRY(cudaMemsetAsync(p->smark.p, 0, sizeof(uint32_t) * p->n, p->st));
                 BISIM_CUDA_TRY(cudaMemsetAsync(p->kmark.p, 0, sizeof(uint32_t) * p->n, p->st));
                 BISIM_CUDA_TRY(cudaMemsetAsync(p->claim.p, 0xff, sizeof(uint64_t) * p->n, p->st));
+                BISIM_CUDA_TRY(cudaMemsetAsync(p->minx.p, 0xff, sizeof(uint64_t) * p->n, p->st));
+                BISIM_CUDA_TRY(cudaMemsetAsync(p->smark64.p, 0xff, sizeof(uint64_t) * p->n, p->st));
+                BISIM_CUDA_TRY(cudaMemsetAsync(p->lostl.p, 0, sizeof(uint32_t) * p->n, p->st));
             }
         }
         p->stamp = 0;

@@ -37,6 +37,11 @@ struct bisim_ctrl {
     int handoff;                       // one LTS on one CTA: 1 = the grid takes over
     int pad4;
     unsigned long long start_heads[32];  // worklist heads at the hand-off to the grid
+    // hybrid engine, a published round with several splitters: its splitters of
+    // one state, taken by position from the ring of size bucket 0
+    int cmd_K0;                          // how many
+    int pad5;
+    unsigned long long cmd_h0;           // ring-0 head before them
 };
 
 // Most splitters one multi-splitter round takes: grid rounds of the hybrid
@@ -102,6 +107,9 @@ struct bisim_plan_s {
     bisim::DevMem bspl;      // int32 [n]: per touched label, the splitter that touched it
     bisim::DevMem msel;      // int32 [2 * KMAX_GRID + 1] + uint32 [KMAX_GRID]: published splitters,
                              // their size prefix, and the round in which each lost a claim
+    bisim::DevMem minx;      // uint64 [n]: per label, the least key of this round's exclusive claims
+    bisim::DevMem smark64;   // uint64 [n]: per state, the least key of the splitters that peel it
+    bisim::DevMem lostl;     // uint32 [n]: per splitter label, the round in which it lost a claim
 
     // batch plans: k LTSs over disjoint state ranges of one union LTS
     int32_t batch_k = 0;

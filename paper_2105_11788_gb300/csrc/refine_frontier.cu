@@ -31,6 +31,8 @@
 // barrier, split, barrier (see the section on rounds with several splitters
 // below). Rounds run on the whole grid, on CTA 0 alone (light rounds of the
 // hybrid schedule) or on the CTA that owns an LTS of a batch.
+#include <algorithm>
+
 #include "plan.cuh"
 
 using namespace bisim;
@@ -45,10 +47,45 @@ using namespace bisim;
 // their states, 14 touched blocks, 15 time between rounds.
 #ifdef BISIM_PHASE_TIMERS
 __device__ unsigned long long g_phase_acc[16];
+// per-round trace of the hybrid kernel (rounds 1 .. BISIM_TRACE_MAX): splitters
+// selected, worklist entries before the selection, touched blocks, winners,
+// round time in ns, and 1 for a round on CTA 0 alone
+constexpr int BISIM_TRACE_MAX = 1 << 16;
+__device__ unsigned g_round_trace[BISIM_TRACE_MAX][6];
+__device__ unsigned long long g_trace_wins;
 __device__ __forceinline__ unsigned long long* phase_slots() {
-    __shared__ unsigned long long s[17];  // [16] holds the time of the last mark
+    __shared__ unsigned long long s[20];  // [16] time of the last mark, [17] touched blocks of the round,
+                                          // [18] wins before the round, [19] round start time
     return s;
 }
+#define TRACE_WIN() atomicAdd(&g_trace_wins, 1ull)
+#define TRACE_TOUCHED(v)                                                      \
+    do {                                                                      \
+        if (blockIdx.x == 0 && threadIdx.x == 0) phase_slots()[17] = (v);     \
+    } while (0)
+#define TRACE_BEGIN(r, K, wl, head)                                           \
+    do {                                                                      \
+        if (blockIdx.x == 0 && threadIdx.x == 0 && (r) >= 1 && (r) <= BISIM_TRACE_MAX) { \
+            unsigned long long av_ = 0;                                       \
+            for (int b_ = 0; b_ < BISIM_BUCKETS; b_++)                        \
+                av_ += *(volatile const unsigned long long*)&(wl).tail[b_] - (head)[b_]; \
+            g_round_trace[(r) - 1][0] = (unsigned)(K);                        \
+            g_round_trace[(r) - 1][1] = (unsigned)(av_ + (K));                \
+            phase_slots()[17] = 0;                                            \
+            phase_slots()[18] = *(volatile unsigned long long*)&g_trace_wins; \
+            phase_slots()[19] = globaltimer_ns();                             \
+        }                                                                     \
+    } while (0)
+#define TRACE_END(r, local)                                                   \
+    do {                                                                      \
+        if (blockIdx.x == 0 && threadIdx.x == 0 && (r) >= 1 && (r) <= BISIM_TRACE_MAX) { \
+            g_round_trace[(r) - 1][2] = (unsigned)phase_slots()[17];          \
+            g_round_trace[(r) - 1][3] =                                       \
+                (unsigned)(*(volatile unsigned long long*)&g_trace_wins - phase_slots()[18]); \
+            g_round_trace[(r) - 1][4] = (unsigned)(globaltimer_ns() - phase_slots()[19]); \
+            g_round_trace[(r) - 1][5] = (local);                              \
+        }                                                                     \
+    } while (0)
 #define PHASE_RESET()                                                         \
     do {                                                                      \
         if (threadIdx.x == 0) {                                               \
@@ -78,6 +115,10 @@ __device__ __forceinline__ unsigned long long* phase_slots() {
 #define PHASE(i) do {} while (0)
 #define PHASE_ADD(i, v) do {} while (0)
 #define PHASE_FLUSH() do {} while (0)
+#define TRACE_WIN() do {} while (0)
+#define TRACE_TOUCHED(v) do {} while (0)
+#define TRACE_BEGIN(r, K, wl, head) do {} while (0)
+#define TRACE_END(r, local) do {} while (0)
 #endif
 
 namespace {
@@ -104,7 +145,12 @@ struct FrontierArgs {
     uint32_t* kmark;  // [n] per state: stamp of the round it was in a kept part
     int4* tlist;      // [2n]: warp list, CTA list of touched blocks (label, range begin, range end, 0)
     int32_t* queue;   // [n]
-    unsigned long long* claim;  // [n] per label: (~stamp << 32) | index of the claiming splitter
+    unsigned long long* claim;  // [n] per label: (~stamp << 32) | index of the claiming splitter;
+                                // peel rounds: the least key of all the round's claims
+    unsigned long long* minx;   // [n] per label, peel rounds: the least key of the exclusive claims
+    unsigned long long* smark64;  // [n] per state, peel rounds: the least key of the splitters
+                                  // that mark it (the first to split it off)
+    uint32_t* lostl;  // [n] per splitter label, peel rounds: the round in which it lost a claim
     int32_t* bspl;    // [n] per touched label: its splitter (multi-splitter rounds)
     bisim_ctrl* ctrl;
     GridBarrier gb;
@@ -268,6 +314,8 @@ struct CtaShared {
     int bn[BISIM_BUCKETS];  // select_many: entries taken from each bucket at most
     int hp[BISIM_BUCKETS];  // select_many: ring position of each bucket's head
     unsigned long long head[BISIM_BUCKETS];  // this CTA's copy of the worklist heads
+    int k0;                 // select_peel: labels taken from size bucket 0
+    unsigned long long h0;  // select_peel: ring-0 head before them
 };
 
 // Block-wide exclusive rank of predicate p and the block total (sh.total).
@@ -566,6 +614,148 @@ __device__ void warp_split_sparse(const FrontierArgs& a, const Worklist& wl, int
     finish_split_warp(a, wl, b, kk, leader, e0 - b0 - kk, C);
 }
 
+// ------------------------------------------------ splits of peel rounds
+//
+// In a peel round a block may be touched by several winning splitters, each
+// of which marked exactly one member of it and not its leader (the round's
+// rule, see peel_round). Carried out one after the other in increasing label
+// order, each such iteration finds the leader unmarked, so its split part is
+// exactly its marked member: the first splitter to mark a member splits it
+// off into a block of its own, a later one that marks the same member finds
+// it alone and splits nothing. So every marked member ends in a block of one
+// state, the block keeps its label and the unmarked members, and the
+// splitters that split something are, per member, the least label among its
+// markers - the low word of smark64. Pushes as Algorithm 3: the block's
+// label, every new label, and (not with Algorithm 2) those splitters.
+
+// set_unstable for every lane with `active` (every lane of the warp calls
+// it); each size bucket's ring slots are taken with one atomicAdd per warp
+__device__ __forceinline__ void set_unstable_warp(const FrontierArgs& a, const Worklist& wl, int32_t label,
+                                                  int32_t size, bool active) {
+    const unsigned lane = threadIdx.x & 31u;
+    bool need = active && atomicExch(&a.unstable[label], 1u) == 0u;
+    int bk = 32 + (int)lane;  // a group of its own when nothing is pushed
+    if (need) {
+        if (size < 0) size = ld(&a.bend[label]) - ld(&a.bbeg[label]);
+        bk = size_bucket(size);
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, bk);
+    const int first = __ffs(peers) - 1;
+    unsigned long long pos = 0;
+    if (need && (int)lane == first) pos = atomicAdd(&wl.tail[bk], (unsigned long long)__popc(peers));
+    pos = __shfl_sync(0xffffffffu, pos, first) + __popc(peers & lanemask_lt());
+    if (need) wl.queue[(size_t)bk * wl.stride + wl.base + pos % (unsigned long long)wl.cap] = label;
+}
+
+__device__ __forceinline__ bool peeled(const FrontierArgs& a, int32_t s, uint32_t stamp, unsigned long long* key) {
+    const unsigned long long k = ld(&a.smark64[s]);
+    *key = k;
+    return (uint32_t)(k >> 32) == ~stamp;
+}
+
+// A peeled member s at position q: a block of its own labelled s; its own
+// label and the splitter that split it off become unstable.
+__device__ __forceinline__ void peel_member(const FrontierArgs& a, int32_t s, int32_t q) {
+    a.block[s] = s;
+    a.bbeg[s] = q;
+    a.bend[s] = q + 1;
+}
+
+__device__ __forceinline__ void peel_pushes(const FrontierArgs& a, const Worklist& wl, int32_t s,
+                                            unsigned long long key, bool active) {
+    set_unstable_warp(a, wl, s, 1, active);
+    set_unstable_warp(a, wl, (int32_t)(uint32_t)key, -1, active && !a.alg2);
+}
+
+// One warp peels block b (range [b0, e0), at most 64 members) from the members.
+__device__ void warp_peel(const FrontierArgs& a, const Worklist& wl, int32_t b, int32_t b0, int32_t e0,
+                          uint32_t stamp, long long& states) {
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned lt = lanemask_lt();
+    const int32_t sz = e0 - b0;
+    const int32_t s0 = (int)lane < sz ? ld(&a.elems[b0 + lane]) : -1;
+    const int32_t s1 = (int)lane + 32 < sz ? ld(&a.elems[b0 + 32 + lane]) : -1;
+    if (lane == 0) a.mcnt[b] = 0;
+    unsigned long long k0 = 0, k1 = 0;
+    const bool p0 = s0 >= 0 && peeled(a, s0, stamp, &k0);
+    const bool p1 = s1 >= 0 && peeled(a, s1, stamp, &k1);
+    const unsigned m0 = __ballot_sync(0xffffffffu, p0), m1 = __ballot_sync(0xffffffffu, p1);
+    if (lane == 0) states += sz;
+    const unsigned v0 = __ballot_sync(0xffffffffu, s0 >= 0), v1 = __ballot_sync(0xffffffffu, s1 >= 0);
+    const int32_t nkeep = sz - __popc(m0) - __popc(m1);
+    if (nkeep < 1 || (m0 | m1) == 0u) {  // the leader is never marked here, and a listed block has a mark
+        if (lane == 0) atomicOr(&a.ctrl->status, ST_INTERNAL);
+        return;
+    }
+    if (s0 >= 0) {
+        const int32_t pos = b0 + (p0 ? nkeep + __popc(m0 & lt) : __popc(~m0 & v0 & lt));
+        a.elems[pos] = s0;
+        a.loc[s0] = pos;
+        if (p0) peel_member(a, s0, pos);
+    }
+    if (s1 >= 0) {
+        const int32_t pos = b0 + (p1 ? nkeep + __popc(m0) + __popc(m1 & lt)
+                                     : __popc(~m0 & v0) + __popc(~m1 & v1 & lt));
+        a.elems[pos] = s1;
+        a.loc[s1] = pos;
+        if (p1) peel_member(a, s1, pos);
+    }
+    if (lane == 0) a.bend[b] = b0 + nkeep;
+    __syncwarp();
+    set_unstable_warp(a, wl, b, nkeep, lane == 0);
+    peel_pushes(a, wl, s0, k0, p0);
+    peel_pushes(a, wl, s1, k1, p1);
+}
+
+// One warp peels block b (more than WARP_MAX members) with km <= 32 marked
+// members, listed in mscr[e0 - km, e0).
+__device__ void warp_peel_sparse(const FrontierArgs& a, const Worklist& wl, int32_t b, int32_t b0, int32_t e0,
+                                 int32_t km, uint32_t stamp, long long& states) {
+    const unsigned lane = threadIdx.x & 31u;
+    const int32_t t0 = e0 - km;
+    const int32_t s = (int)lane < km ? ld(&a.mscr[t0 + lane]) : -1;
+    __syncwarp();
+    if (lane == 0) a.mcnt[b] = 0;
+    const unsigned long long k = s >= 0 ? ld(&a.smark64[s]) : 0ull;
+    const unsigned hi = ~stamp;
+    warp_gather(a, s, km, t0, [&](int32_t u) { return (uint32_t)(ld(&a.smark64[u]) >> 32) == hi; });
+    if (s >= 0) peel_member(a, s, ld(&a.loc[s]));
+    if (lane == 0) {
+        states += km;
+        a.bend[b] = t0;
+    }
+    __syncwarp();
+    set_unstable_warp(a, wl, b, t0 - b0, lane == 0);
+    peel_pushes(a, wl, s, k, s >= 0);
+}
+
+// One CTA peels block b with more than 32 marked members.
+__device__ void cta_peel(const FrontierArgs& a, const Worklist& wl, CtaShared& sh, int32_t b, uint32_t stamp,
+                         long long& states) {
+    const int32_t b0 = ld(&a.bbeg[b]), e0 = ld(&a.bend[b]);
+    const int32_t km = ld(&a.mcnt[b]);
+    const int32_t t0 = e0 - km;
+    const unsigned hi = ~stamp;
+    __syncthreads();
+    if (threadIdx.x == 0) a.mcnt[b] = 0;
+    cta_gather_range(a, sh, t0, km, t0, [&](int32_t u) { return (uint32_t)(ld(&a.smark64[u]) >> 32) == hi; });
+    for (int32_t base = 0; base < km; base += blockDim.x) {
+        const int32_t i = base + (int32_t)threadIdx.x;
+        const bool act = i < km;
+        const int32_t s = act ? ld(&a.elems[t0 + i]) : -1;
+        const unsigned long long k = act ? ld(&a.smark64[s]) : 0ull;
+        if (act) peel_member(a, s, t0 + i);
+        peel_pushes(a, wl, s, k, act);
+    }
+    if (threadIdx.x == 0) {
+        states += km;
+        a.bend[b] = t0;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) set_unstable_warp(a, wl, b, t0 - b0, threadIdx.x == 0);
+    __syncthreads();
+}
+
 // Split step of a round for the touched blocks listed by the mark step:
 // blocks of at most WARP_MAX states one per warp; larger blocks one per warp
 // when at most 32 members are marked, otherwise one per CTA. CTA `cta` of
@@ -584,10 +774,14 @@ __device__ void split_step(const FrontierArgs& a, const Worklist& wl, CtaShared&
     auto mid_entry = [&](int i) {
         const int4 t = ld(&mid_list[i]);
         const int32_t km = ld(&a.mcnt[t.x]);
-        if (km <= 32)
-            warp_split_sparse(a, wl, t.x, t.y, t.z, km, stamp, C, states);
-        else if ((threadIdx.x & 31) == 0)
-            defer[atomicAdd(ndefer, 1)] = t.x;
+        if (km <= 32) {
+            if (t.w)
+                warp_peel_sparse(a, wl, t.x, t.y, t.z, km, stamp, states);
+            else
+                warp_split_sparse(a, wl, t.x, t.y, t.z, km, stamp, C, states);
+        } else if ((threadIdx.x & 31) == 0) {
+            defer[atomicAdd(ndefer, 1)] = t.w ? ~t.x : t.x;  // a peeled block is listed as ~label
+        }
     };
     if (threadIdx.x == 0) *ndefer = 0;
     __syncthreads();
@@ -597,11 +791,20 @@ __device__ void split_step(const FrontierArgs& a, const Worklist& wl, CtaShared&
         if (base == 0)
             for (int64_t q = cta + (int64_t)wid * ncta; q < ns; q += (int64_t)ncta * nw) {
                 const int4 t = ld(&small_list[q]);
-                warp_split(a, wl, t.x, t.y, t.z, stamp, C, states);
+                if (t.w)
+                    warp_peel(a, wl, t.x, t.y, t.z, stamp, states);
+                else
+                    warp_split(a, wl, t.x, t.y, t.z, stamp, C, states);
             }
         __syncthreads();
         const int nd = *ndefer;
-        for (int jd = 0; jd < nd; jd++) cta_split(a, wl, sh, defer[jd], stamp, C, states);
+        for (int jd = 0; jd < nd; jd++) {
+            const int d = defer[jd];
+            if (d < 0)
+                cta_peel(a, wl, sh, ~d, stamp, states);
+            else
+                cta_split(a, wl, sh, d, stamp, C, states);
+        }
         __syncthreads();
         if (threadIdx.x == 0) *ndefer = 0;
         __syncthreads();
@@ -619,18 +822,22 @@ __device__ void split_step(const FrontierArgs& a, const Worklist& wl, CtaShared&
 // The part of a mark step after the first mark of a source s in its block b
 // (range [bb, be)): rank s among the block's marked members and list b when
 // it is the first. Blocks of one state cannot split and are skipped.
+// mode (the list entry's fourth field): 0 = the block is split by one splitter
+// (Algorithm 3's rule); 1 = peel rounds: every marked member is split off on
+// its own (each was marked by splitters that mark no other member of the
+// block and not its leader).
 __device__ __forceinline__ void rank_marked(const FrontierArgs& a, int32_t s, int32_t b, int32_t bb, int32_t be,
                                             int32_t Cw, int* n_small, int* n_mid, int4* small_list,
-                                            int4* mid_list) {
+                                            int4* mid_list, int mode = 0) {
     if (be - bb <= 1) return;
     const int32_t rk = atomicAdd(&a.mcnt[b], 1);
     a.mscr[be - 1 - rk] = s;
     if (rk == 0) {
         if (Cw >= 0) a.bspl[b] = Cw;
         if (be - bb <= WARP_MAX)
-            small_list[atomicAdd(n_small, 1)] = make_int4(b, bb, be, 0);
+            small_list[atomicAdd(n_small, 1)] = make_int4(b, bb, be, mode);
         else
-            mid_list[atomicAdd(n_mid, 1)] = make_int4(b, bb, be, 0);
+            mid_list[atomicAdd(n_mid, 1)] = make_int4(b, bb, be, mode);
     }
 }
 
@@ -843,6 +1050,7 @@ __device__ void mark_many(const FrontierArgs& a, const Worklist& wl, const int32
             } else {
                 a.unstable[C] = 0u;
                 commits++;
+                TRACE_WIN();
             }
         }
         if (lose) continue;
@@ -997,6 +1205,7 @@ __device__ __forceinline__ void mark_item(const FrontierArgs& a, const Worklist&
         } else {
             a.unstable[ic.C] = 0u;
             commits++;
+            TRACE_WIN();
         }
     }
     if (lose) return;
@@ -1028,6 +1237,8 @@ struct HybridArgs {
     int32_t* g_selC;   // [BISIM_KMAX_GRID] published splitters
     int32_t* g_selP;   // [BISIM_KMAX_GRID + 1] their size prefix
     uint32_t* g_lost;  // [BISIM_KMAX_GRID] round in which each lost a claim
+    int peel;          // 1: grid rounds with several splitters are peel rounds
+    int cap0;          // peel rounds: most splitters of one state per round
 };
 
 // The three phases of a round with several splitters, by the warps gw,
@@ -1058,6 +1269,388 @@ __device__ __forceinline__ bool multi_round(const FrontierArgs& a, const Worklis
     PHASE(5);
     const int ns = ld_volatile_i32(n_small), nm = ld_volatile_i32(n_mid);
     PHASE_ADD(14, (unsigned long long)(ns + nm));
+    TRACE_TOUCHED((unsigned long long)(ns + nm));
+    split_step(a, wl, sh, defer, ndefer, stamp, MULTI, ns, small_list, nm, mid_list, cta, ncta, states);
+    PHASE(6);
+    const bool ok = sync();
+    PHASE(7);
+    return ok;
+}
+
+// ------------------------------------------------------------- peel rounds
+//
+// Grid rounds with several splitters, generalising the claim rule above so
+// that a block may be split by several splitters of the same round. Keys
+// order the round's splitters by label: key = (~stamp << 32) | (C << 1) | x.
+// A splitter touches a block b (of more than one state) that holds a
+// predecessor of one of its members; the touch is a "peel" (x = 0) when the
+// splitter has one state, all its incoming transitions are walked by one
+// warp, and among them exactly one member of b and not b's leader is a
+// source; every other touch, and a splitter's claim on its own block when it
+// has several states, is exclusive (x = 1). Every touch lowers claim[b] to
+// its key, exclusive ones also minx[b]. The least touch of b decides:
+//   exclusive (minx[b] == claim[b]): that splitter alone splits b, with
+//     Algorithm 3's rule, and every other toucher of b loses;
+//   peel (otherwise): every exclusive toucher of b loses, the peeling ones
+//     do not, and b is split as described before warp_peel.
+// A splitter that loses anywhere goes back to the worklist and marks nothing
+// (exclusive losers are known from the claims themselves: an exclusive touch
+// that meets or is displaced by a lesser key records the loss in lostl; a
+// peeling splitter checks its blocks' words after the barrier). The least
+// splitter of the round never loses, so every round carries out at least one
+// iteration. The winners' iterations touch disjoint data except on peeled
+// blocks, where running them one after the other in label order gives the
+// same split; so a round again has the effect of a sequence of Algorithm 3
+// iterations. The splitters of one state come by position from the ring of
+// size bucket 0, so a round may take tens of thousands of them.
+
+constexpr int PEEL_CHUNKS = 4;  // chunks of 32 transitions a warp loads at once
+
+__device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long* p) {
+    return *(volatile const unsigned long long*)p;
+}
+
+__device__ __forceinline__ unsigned long long peel_key(uint32_t stamp, int32_t C, bool x) {
+    return ((unsigned long long)(~stamp) << 32) | ((unsigned long long)(uint32_t)C << 1) | (x ? 1ull : 0ull);
+}
+
+__device__ __forceinline__ void claim_peel(const FrontierArgs& a, int32_t b, unsigned long long key, bool x,
+                                           uint32_t stamp) {
+    const unsigned long long old = atomicMin(&a.claim[b], key);
+    if (x) atomicMin(&a.minx[b], key);
+    if ((old >> 32) == (key >> 32)) {
+        if (old < key) {
+            if (x) a.lostl[(uint32_t)key >> 1] = stamp;
+        } else if (old > key && (old & 1ull)) {
+            a.lostl[(uint32_t)old >> 1] = stamp;
+        }
+    }
+}
+
+// Selection of a peel round by every CTA: K0 labels of size bucket 0 (blocks
+// of one state; blocks only shrink and are never empty) from the head of its
+// ring, at most cap0 (sh.k0, and the ring-0 head before them in sh.h0), and
+// up to kmax1 labels of the higher buckets (lowest first, FIFO inside a
+// bucket) while their blocks hold at most budget1 states together, listed in
+// selC with the exclusive prefix of their sizes in selP. Returns the number
+// of the higher-bucket labels to every thread.
+__device__ int select_peel(const FrontierArgs& a, const Worklist& wl, unsigned long long* head, CtaShared& sh,
+                           int32_t* selC, int32_t* selP, int kmax1, int32_t budget1, int cap0) {
+    const unsigned lane = threadIdx.x & 31u;
+    kmax1 = min(kmax1, SEL_E * (int)blockDim.x);
+    if (threadIdx.x < 32) {
+        const unsigned long long h = head[lane];
+        const unsigned long long t = *(volatile const unsigned long long*)&wl.tail[lane];
+        const int av = lane == 0 ? 0 : (int)min(t - h, (unsigned long long)kmax1);
+        int x = av;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if ((int)lane >= o) x += y;
+        }
+        sh.bx[lane] = x - av;
+        sh.bn[lane] = av;
+        sh.hp[lane] = (int)(h % (unsigned long long)wl.cap);
+        if (lane == 0) {
+            sh.k0 = (int)min(t - h, (unsigned long long)max(cap0, 0));
+            sh.h0 = h;
+        }
+        if (lane == 31) sh.total = min(x, kmax1);
+    }
+    __syncthreads();
+    const int k1 = sh.total;
+    const int K0 = sh.k0;
+    {
+        int32_t lv[SEL_E];
+        int bk = 1;
+#pragma unroll
+        for (int e = 0; e < SEL_E; e++) {
+            const int j = e * (int)blockDim.x + (int)threadIdx.x;
+            lv[e] = -1;
+            if (j < k1) {
+                while (j >= sh.bx[bk] + sh.bn[bk]) bk++;
+                int pos = sh.hp[bk] + (j - sh.bx[bk]);
+                if (pos >= wl.cap) pos -= wl.cap;
+                lv[e] = ld(&wl.queue[(size_t)bk * wl.stride + wl.base + pos]);
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < SEL_E; e++) {
+            const int j = e * (int)blockDim.x + (int)threadIdx.x;
+            if (j < k1) selC[j] = lv[e];
+        }
+    }
+    if (threadIdx.x == 0) selP[0] = 0;
+    __syncthreads();
+    const int E = (k1 + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int j0 = (int)threadIdx.x * E;
+    int32_t cs[SEL_E];
+    int sz[SEL_E];
+    int mine = 0;
+#pragma unroll
+    for (int e = 0; e < SEL_E; e++) {
+        const int j = j0 + e;
+        cs[e] = e < E && j < k1 ? selC[j] : -1;
+        sz[e] = cs[e] < 0 ? 0 : ld(&a.bend[cs[e]]) - ld(&a.bbeg[cs[e]]);
+        mine += sz[e];
+    }
+    int tot;
+    int ex = cta_scan(mine, sh, tot);
+    int taken = 0;
+#pragma unroll
+    for (int e = 0; e < SEL_E; e++) {
+        const int j = j0 + e;
+        // the first is taken when nothing else is, so a round is never empty
+        if (cs[e] >= 0 && ((j == 0 && K0 == 0) || ex + sz[e] <= budget1)) {
+            selP[j] = ex;
+            selP[j + 1] = ex + sz[e];
+            taken++;
+        }
+        ex += sz[e];
+    }
+    int K1;
+    cta_scan(taken, sh, K1);
+    if (threadIdx.x < 32) {
+        if (lane == 0)
+            head[0] += (unsigned long long)K0;
+        else
+            head[lane] += (unsigned long long)max(0, min(sh.bn[lane], K1 - sh.bx[lane]));
+    }
+    __syncthreads();
+    return K1;
+}
+
+// One item of a peel round: a member t of splitter C with its incoming range.
+struct PeelItem {
+    int32_t C, t, d0, deg;
+    bool first;   // the first member of its splitter
+    bool single;  // the splitter has one state
+};
+
+__device__ __forceinline__ PeelItem peel_item(const FrontierArgs& a, const Worklist& wl, unsigned long long h0,
+                                              int K0, const int32_t* selC, const int32_t* selP, int K1,
+                                              int64_t item) {
+    PeelItem it;
+    if (item < K0) {
+        it.C = ld(&wl.queue[wl.base + (h0 + (unsigned long long)item) % (unsigned long long)wl.cap]);
+        it.t = it.C;
+        it.first = true;
+        it.single = true;
+    } else {
+        const int32_t i = (int32_t)(item - K0);
+        const int j = find_sel(selP, K1, i);
+        it.C = selC[j];
+        it.first = i == selP[j];
+        it.single = selP[j + 1] - selP[j] == 1;
+        it.t = it.single ? it.C : ld(&a.elems[ld(&a.bbeg[it.C]) + i - selP[j]]);
+    }
+    it.d0 = a.in_ptr[it.t];
+    it.deg = a.in_ptr[it.t + 1] - it.d0;
+    return it;
+}
+
+// The loads of one packed chunk lane: its transition, source, source block
+// and the block's range.
+struct PeelEdge {
+    unsigned long long e;
+    int32_t b, bb, be;
+};
+
+// The claim (pass 0) and mark (pass 1) work of a warp on the items
+// [g0, g1) of the round (at most 32; lane l holds item g0 + l). Items with
+// at most 32 incoming transitions are packed whole into chunks of 32 lanes
+// (so one ballot sees all of an item's transitions); larger ones are walked
+// by the whole warp afterwards and touch exclusively.
+template <int PASS>
+__device__ void peel_items(const FrontierArgs& a, const Worklist& wl, unsigned long long h0, int K0,
+                           const int32_t* selC, const int32_t* selP, int K1, int64_t g0, int64_t g1,
+                           uint32_t stamp, int* n_small, int* n_mid, int4* small_list, int4* mid_list,
+                           long long& edges, long long& commits) {
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned FULL = 0xffffffffu;
+    const int ng = (int)(g1 - g0);
+    PeelItem it;
+    it.C = -1;
+    it.deg = 0;
+    it.single = true;
+    it.first = false;
+    it.t = 0;
+    it.d0 = 0;
+    if ((int)lane < ng) it = peel_item(a, wl, h0, K0, selC, selP, K1, g0 + lane);
+    // pass 1: exclusive losses recorded by the claims
+    bool lost_x = false;
+    if (PASS == 1 && (int)lane < ng) lost_x = ld_volatile_u32(&a.lostl[it.C]) == stamp;
+    const bool packable = (int)lane < ng && it.deg > 0 && it.deg <= 32;
+    // greedy packing: chunk and first lane of every packable item
+    int my_chunk = -1, my_start = 0, nchunks = 0;
+    {
+        int cur = 0, chunk = 0;
+        const int dp = packable ? it.deg : 0;
+        for (int i = 0; i < ng; i++) {
+            const int d = __shfl_sync(FULL, dp, i);
+            if (d == 0) continue;
+            if (cur + d > 32) {
+                chunk++;
+                cur = 0;
+            }
+            if ((int)lane == i) {
+                my_chunk = chunk;
+                my_start = cur;
+            }
+            cur += d;
+        }
+        nchunks = cur > 0 ? chunk + 1 : chunk;
+    }
+    // pass 1: the item's loss as seen from its peel touches (filled per chunk)
+    bool lost_p = false;
+    for (int c0 = 0; c0 < nchunks; c0 += PEEL_CHUNKS) {
+        PeelEdge ed[PEEL_CHUNKS];
+        int src_lane[PEEL_CHUNKS];
+        bool val[PEEL_CHUNKS];
+#pragma unroll
+        for (int u = 0; u < PEEL_CHUNKS; u++) {
+            const int c = c0 + u;
+            const unsigned mc = __ballot_sync(FULL, my_chunk == c);
+            const unsigned starts = __reduce_or_sync(FULL, my_chunk == c ? (1u << my_start) : 0u);
+            // the r-th item of the chunk owns this lane
+            const int r = __popc(starts & (0xffffffffu >> (31 - lane))) - 1;
+            const int il = (mc != 0u && r >= 0) ? (int)__fns(mc, 0, r + 1) : 0;
+            const int st = __shfl_sync(FULL, my_start, il);
+            const int dg = __shfl_sync(FULL, it.deg, il);
+            const int d0 = __shfl_sync(FULL, it.d0, il);
+            val[u] = c < nchunks && mc != 0u && r >= 0 && (int)lane < st + dg;
+            src_lane[u] = il;
+            ed[u].e = val[u] ? a.in_edge[d0 + (int)lane - st] : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < PEEL_CHUNKS; u++) ed[u].b = val[u] ? ld(&a.block[(int32_t)(ed[u].e >> 32)]) : 0;
+#pragma unroll
+        for (int u = 0; u < PEEL_CHUNKS; u++) {
+            ed[u].bb = val[u] ? ld(&a.bbeg[ed[u].b]) : 0;
+            ed[u].be = val[u] ? ld(&a.bend[ed[u].b]) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < PEEL_CHUNKS; u++) {
+            if (c0 + u >= nchunks) break;  // warp-uniform
+            const int il = src_lane[u];
+            const int32_t s = (int32_t)(ed[u].e >> 32);
+            const int32_t b = ed[u].b;
+            const bool ns = val[u] && ed[u].be - ed[u].bb > 1;
+            const int32_t C = __shfl_sync(FULL, it.C, il);
+            const bool single = __shfl_sync(FULL, it.single, il);
+            // lanes of this item that reach block b, and those among them from source s
+            const unsigned long long vb = ns ? ((unsigned long long)il << 32) | (uint32_t)b : ~0ull - lane;
+            const unsigned mb = __match_any_sync(FULL, vb);
+            const unsigned long long vbs = ns ? ((unsigned long long)(uint32_t)b << 32) | (uint32_t)s : ~0ull - lane;
+            const unsigned mbs = __match_any_sync(FULL, vbs) & mb;
+            const bool lead = (__ballot_sync(FULL, ns && s == b) & mb) != 0u;
+            const bool x = !single || mbs != mb || lead;
+            if (PASS == 0) {
+                if (ns && (mb & lanemask_lt()) == 0u) claim_peel(a, b, peel_key(stamp, C, x), x, stamp);
+            } else {
+                // a peel touch of a block whose least touch is exclusive: this splitter loses
+                const bool lp = ns && !x && ld_volatile_u64(&a.minx[b]) == ld_volatile_u64(&a.claim[b]);
+                const unsigned lpm = __ballot_sync(FULL, lp);
+                const int st = __shfl_sync(FULL, my_start, il);
+                const int dg = __shfl_sync(FULL, it.deg, il);
+                const unsigned range = (dg >= 32 ? 0xffffffffu : ((1u << dg) - 1u)) << st;
+                const bool lose = __shfl_sync(FULL, lost_x, il) || (lpm & range) != 0u;
+                if (my_chunk == c0 + u) {
+                    const unsigned mine = (it.deg >= 32 ? 0xffffffffu : ((1u << it.deg) - 1u)) << my_start;
+                    lost_p = lost_x || (lpm & mine) != 0u;
+                }
+                if (ns && !lose) {
+                    if (x) {
+                        a.mark[(uint32_t)ed[u].e] = stamp;
+                        if (atomicExch(&a.smark[s], stamp) != stamp)
+                            rank_marked(a, s, b, ed[u].bb, ed[u].be, C, n_small, n_mid, small_list, mid_list, 0);
+                    } else {
+                        const unsigned long long pk = ((unsigned long long)(~stamp) << 32) | (uint32_t)C;
+                        const unsigned long long old = atomicMin(&a.smark64[s], pk);
+                        if ((old >> 32) != (pk >> 32))
+                            rank_marked(a, s, b, ed[u].bb, ed[u].be, C, n_small, n_mid, small_list, mid_list, 1);
+                    }
+                }
+            }
+        }
+    }
+    // items with more than 32 incoming transitions: the whole warp walks each;
+    // all their touches are exclusive (no unit check across chunks)
+    unsigned big = __ballot_sync(FULL, (int)lane < ng && it.deg > 32);
+    while (big) {
+        const int il = __ffs(big) - 1;
+        big &= big - 1u;
+        const int32_t C = __shfl_sync(FULL, it.C, il);
+        const int32_t d0 = __shfl_sync(FULL, it.d0, il);
+        const int32_t dg = __shfl_sync(FULL, it.deg, il);
+        const bool lose = PASS == 1 && __shfl_sync(FULL, lost_x, il);
+        for (int32_t q0 = 0; q0 < dg; q0 += 32) {
+            const bool v = q0 + (int32_t)lane < dg;
+            const unsigned long long e = v ? a.in_edge[d0 + q0 + (int32_t)lane] : 0ull;
+            const int32_t s = (int32_t)(e >> 32);
+            const int32_t b = v ? ld(&a.block[s]) : 0;
+            const int32_t bb = v ? ld(&a.bbeg[b]) : 0, be = v ? ld(&a.bend[b]) : 0;
+            const bool ns = v && be - bb > 1;
+            if (PASS == 0) {
+                const unsigned mb = __match_any_sync(FULL, ns ? b : -1 - (int)lane);
+                if (ns && (mb & lanemask_lt()) == 0u) claim_peel(a, b, peel_key(stamp, C, true), true, stamp);
+            } else if (ns && !lose) {
+                a.mark[(uint32_t)e] = stamp;
+                if (atomicExch(&a.smark[s], stamp) != stamp)
+                    rank_marked(a, s, b, bb, be, C, n_small, n_mid, small_list, mid_list, 0);
+            }
+        }
+        if ((int)lane == il) lost_p = lost_x;
+    }
+    if ((int)lane < ng) {
+        if (PASS == 0) {
+            // a splitter of several states claims its own block
+            if (it.first && !it.single) claim_peel(a, it.C, peel_key(stamp, it.C, true), true, stamp);
+        } else {
+            const bool lose = lost_x || lost_p;
+            if (it.first) {
+                if (lose) {
+                    push(a, wl, it.C);
+                } else {
+                    a.unstable[it.C] = 0u;
+                    commits++;
+                    TRACE_WIN();
+                }
+            }
+            if (!lose) edges += it.deg;
+        }
+    }
+}
+
+// A peel round on the whole grid: claim pass, barrier, mark pass, barrier,
+// split step, barrier. The items (members of the round's splitters: K0 of
+// one state from the ring of bucket 0, then the members of the K1 listed
+// ones) are cut into one contiguous share per warp.
+template <typename Sync>
+__device__ __forceinline__ bool peel_round(const FrontierArgs& a, const Worklist& wl, CtaShared& sh, int* defer,
+                                           int* ndefer, const int32_t* selC, const int32_t* selP, int K1, int K0,
+                                           unsigned long long h0, uint32_t stamp, int64_t gw, int64_t nwarps,
+                                           int* n_small, int* n_mid, int4* small_list, int4* mid_list, int cta,
+                                           int ncta, long long& edges, long long& states, long long& commits,
+                                           Sync sync) {
+    const int64_t I = (int64_t)K0 + selP[K1];
+    const int64_t per = (I + nwarps - 1) / nwarps;
+    const int64_t i0 = gw * per, i1 = min(I, i0 + per);
+    for (int64_t g = i0; g < i1; g += 32)
+        peel_items<0>(a, wl, h0, K0, selC, selP, K1, g, min(i1, g + 32), stamp, n_small, n_mid, small_list,
+                      mid_list, edges, commits);
+    PHASE(2);
+    if (!sync()) return false;
+    PHASE(3);
+    for (int64_t g = i0; g < i1; g += 32)
+        peel_items<1>(a, wl, h0, K0, selC, selP, K1, g, min(i1, g + 32), stamp, n_small, n_mid, small_list,
+                      mid_list, edges, commits);
+    PHASE(4);
+    if (!sync()) return false;
+    PHASE(5);
+    const int ns = ld_volatile_i32(n_small), nm = ld_volatile_i32(n_mid);
+    PHASE_ADD(14, (unsigned long long)(ns + nm));
+    TRACE_TOUCHED((unsigned long long)(ns + nm));
     split_step(a, wl, sh, defer, ndefer, stamp, MULTI, ns, small_list, nm, mid_list, cta, ncta, states);
     PHASE(6);
     const bool ok = sync();
@@ -1084,13 +1677,15 @@ __global__ void __launch_bounds__(MAXT, 1) k_frontier_hybrid(FrontierArgs a, Hyb
     __shared__ CtaShared sh;
     __shared__ int s_defer[32];
     __shared__ int s_ndefer;
-    __shared__ int s_ns, s_nm, s_heavy, s_cmd, s_K;
+    __shared__ int s_ns, s_nm, s_heavy, s_cmd, s_K, s_K0;
+    __shared__ unsigned long long s_h0;
     __shared__ unsigned s_stamp;
     __shared__ uint32_t s_lost[32];  // rounds on CTA 0 alone take at most 32 splitters
     extern __shared__ int32_t s_dyn[];
     const int kmax = max(h.kmax, 1);
+    // kmax labels plus 32 for the singletons a CTA-0 round of a peel selection appends
     int32_t* s_selC = s_dyn;
-    int32_t* s_selP = s_dyn + kmax;
+    int32_t* s_selP = s_dyn + kmax + 32;
     const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
     const int32_t n = a.n;
@@ -1107,10 +1702,14 @@ __global__ void __launch_bounds__(MAXT, 1) k_frontier_hybrid(FrontierArgs a, Hyb
         __syncthreads();
         return true;
     };
-    // a grid round: K > 1 splitters in selC / selP, or the single splitter C
-    auto grid_round = [&](int K, int32_t C, uint32_t stamp, int par) -> bool {
+    // a grid round: K > 1 splitters in selC / selP (peel rounds: K listed ones
+    // and K0 of one state from ring 0 after h0), or the single splitter C
+    auto grid_round = [&](int K, int K0, unsigned long long h0, int32_t C, uint32_t stamp, int par) -> bool {
         int* ns = &c->n_touched[par];
         int* nm = &c->n_mid[par];
+        if (h.peel && K + K0 > 1)
+            return peel_round(a, wl, sh, s_defer, &s_ndefer, s_selC, s_selP, K, K0, h0, stamp, gw, nwarps, ns, nm,
+                              a.tlist, a.tlist + n, (int)blockIdx.x, (int)gridDim.x, edges, states, commits, gsync);
         if (K > 1)
             return multi_round(a, wl, sh, s_defer, &s_ndefer, s_selC, s_selP, K, h.g_lost, stamp, gw, nwarps, ns, nm,
                                a.tlist, a.tlist + n, (int)blockIdx.x, (int)gridDim.x, edges, states, commits, gsync);
@@ -1159,11 +1758,15 @@ __global__ void __launch_bounds__(MAXT, 1) k_frontier_hybrid(FrontierArgs a, Hyb
                 s_cmd = ab ? -1 : ldcg(&c->cmd_C);
                 s_stamp = ldcg(&c->cmd_stamp);
                 s_K = ldcg(&c->cmd_K);
+                s_K0 = ldcg(&c->cmd_K0);
+                s_h0 = ldcg(&c->cmd_h0);
             }
             __syncthreads();
             const int32_t C = s_cmd;
             const uint32_t stamp = s_stamp;
             const int K = s_K;
+            const int K0c = s_K0;
+            const unsigned long long h0c = s_h0;
             if (C == -1) break;
             if (threadIdx.x < BISIM_BUCKETS) sh.head[threadIdx.x] = ldcg(&c->cmd_heads[threadIdx.x]);
             if (C == MULTI) {
@@ -1184,7 +1787,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_frontier_hybrid(FrontierArgs a, Hyb
             }
             __syncthreads();
             r = (int64_t)(stamp - a.stamp0);
-            if (!grid_round(C == MULTI ? K : 1, C, stamp, (int)(r & 1))) return;
+            if (!grid_round(C == MULTI ? K : 1, C == MULTI ? K0c : 0, h0c, C, stamp, (int)(r & 1))) return;
             in_step = true;
             continue;
         }
@@ -1192,14 +1795,25 @@ __global__ void __launch_bounds__(MAXT, 1) k_frontier_hybrid(FrontierArgs a, Hyb
         r++;
         const uint32_t stamp = a.stamp0 + (uint32_t)r;
         const int par = (int)(r & 1);
-        int K;
+        int K;       // splitters of the round
+        int K1 = 0;  // of those, listed in s_selC / s_selP (the rest: ring 0 after h0, peel rounds)
+        int K0 = 0;
+        unsigned long long h0 = 0;
         int32_t C;
-        if (kmax > 1) {
+        if (kmax > 1 && h.peel) {
+            K1 = select_peel(a, wl, sh.head, sh, s_selC, s_selP, kmax, h.budget, h.cap0);
+            K0 = sh.k0;
+            h0 = sh.h0;
+            K = K0 + K1;
+            C = K0 > 0 ? ld(&wl.queue[wl.base + h0 % (unsigned long long)wl.cap]) : K1 > 0 ? s_selC[0] : -1;
+        } else if (kmax > 1) {
             K = select_many(a, wl, sh.head, sh, s_selC, s_selP, kmax, h.budget);
+            K1 = K;
             C = K > 0 ? s_selC[0] : -1;
         } else {
             C = select_splitter(wl, sh.head, sh);
             K = C >= 0 ? 1 : 0;
+            K1 = K;
         }
         PHASE(0);
         PHASE_ADD(K > 1 ? 9 : 10, K > 0 ? 1ull : 0ull);
@@ -1221,7 +1835,17 @@ __global__ void __launch_bounds__(MAXT, 1) k_frontier_hybrid(FrontierArgs a, Hyb
         // CTA 0 alone, or the grid?
         bool local;
         if (K > 1) {
-            local = s_selP[K] <= h.local_budget;
+            local = K0 + s_selP[K1] <= h.local_budget;
+            if (local && K0 > 0) {
+                // the splitters of one state join the list (at most local_budget <= 32 of them)
+                for (int i = threadIdx.x; i < K0; i += blockDim.x) {
+                    s_selC[K1 + i] = ld(&wl.queue[wl.base + (h0 + (unsigned long long)i) % (unsigned long long)wl.cap]);
+                    s_selP[K1 + i + 1] = s_selP[K1] + i + 1;
+                }
+                __syncthreads();
+                K1 = K;
+                K0 = 0;
+            }
         } else {
             if (threadIdx.x < 32) {
                 const int32_t b0 = ld(&a.bbeg[C]), e0 = ld(&a.bend[C]);
@@ -1245,8 +1869,10 @@ __global__ void __launch_bounds__(MAXT, 1) k_frontier_hybrid(FrontierArgs a, Hyb
             if (K == 1) {
                 a.unstable[C] = 0u;
                 commits++;
+                TRACE_WIN();
             }
         }
+        TRACE_BEGIN(r, K, wl, sh.head);
         if (local) {
             if (!lead) {
                 in_step = false;  // park until CTA 0 publishes a grid round
@@ -1268,14 +1894,15 @@ __global__ void __launch_bounds__(MAXT, 1) k_frontier_hybrid(FrontierArgs a, Hyb
                 __syncthreads();
             }
             if (threadIdx.x == 0) *(volatile unsigned long long*)&c->heartbeat = (unsigned long long)r;
+            TRACE_END(r, 1u);
             in_step = false;
             continue;
         }
         if (lead && !in_step) {
             // wake the parked CTAs with this round and the heads after its selection
             if (K > 1)
-                for (int i = threadIdx.x; i <= K; i += blockDim.x) {
-                    if (i < K) h.g_selC[i] = s_selC[i];
+                for (int i = threadIdx.x; i <= K1; i += blockDim.x) {
+                    if (i < K1) h.g_selC[i] = s_selC[i];
                     h.g_selP[i] = s_selP[i];
                 }
             if (threadIdx.x < BISIM_BUCKETS) c->cmd_heads[threadIdx.x] = sh.head[threadIdx.x];
@@ -1283,7 +1910,9 @@ __global__ void __launch_bounds__(MAXT, 1) k_frontier_hybrid(FrontierArgs a, Hyb
             __syncthreads();
             if (threadIdx.x == 0) {
                 c->cmd_C = K > 1 ? MULTI : C;
-                c->cmd_K = K;
+                c->cmd_K = K > 1 ? K1 : K;
+                c->cmd_K0 = K > 1 ? K0 : 0;
+                c->cmd_h0 = h0;
                 c->cmd_stamp = stamp;
                 __threadfence();
                 atomicAdd(&c->cmd_seq, 1ull);
@@ -1293,10 +1922,11 @@ __global__ void __launch_bounds__(MAXT, 1) k_frontier_hybrid(FrontierArgs a, Hyb
         PHASE(1);
         if (K > 1) {
             PHASE_ADD(12, (unsigned long long)K);
-            PHASE_ADD(13, (unsigned long long)s_selP[K]);
+            PHASE_ADD(13, (unsigned long long)(K0 + s_selP[K1]));
         }
-        if (!grid_round(K, C, stamp, par)) return;
+        if (!grid_round(K > 1 ? K1 : 1, K > 1 ? K0 : 0, h0, C, stamp, par)) return;
         if (K == 1) PHASE(8);
+        TRACE_END(r, 0u);
     }
     PHASE_FLUSH();
     if (edges) atomicAdd((unsigned long long*)&c->edges, (unsigned long long)edges);
@@ -1545,7 +2175,13 @@ int ensure_frontier(bisim_plan_s* p) {
     BISIM_TRY(p->claim.alloc(8 * n, st));
     BISIM_TRY(p->bspl.alloc(4 * n, st));
     BISIM_TRY(p->msel.alloc(4 * (3 * (size_t)BISIM_KMAX_GRID + 1), st));
+    BISIM_TRY(p->minx.alloc(8 * n, st));
+    BISIM_TRY(p->smark64.alloc(8 * n, st));
+    BISIM_TRY(p->lostl.alloc(4 * n, st));
     BISIM_CUDA_TRY(cudaMemsetAsync(p->claim.p, 0xff, 8 * n, st));  // older than every round
+    BISIM_CUDA_TRY(cudaMemsetAsync(p->minx.p, 0xff, 8 * n, st));
+    BISIM_CUDA_TRY(cudaMemsetAsync(p->smark64.p, 0xff, 8 * n, st));
+    BISIM_CUDA_TRY(cudaMemsetAsync(p->lostl.p, 0, 4 * n, st));
     BISIM_CUDA_TRY(cudaMemsetAsync(p->smark.p, 0, 4 * n, st));
     BISIM_CUDA_TRY(cudaMemsetAsync(p->kmark.p, 0, 4 * n, st));
     p->frontier_ready = true;
@@ -1615,6 +2251,9 @@ FrontierArgs make_args(bisim_plan_s* p, uint32_t base, int64_t cap) {
     a.tlist = p->tlist.as<int4>();
     a.queue = p->queue.as<int32_t>();
     a.claim = p->claim.as<unsigned long long>();
+    a.minx = p->minx.as<unsigned long long>();
+    a.smark64 = p->smark64.as<unsigned long long>();
+    a.lostl = p->lostl.as<uint32_t>();
     a.bspl = p->bspl.as<int32_t>();
     a.ctrl = c;
     a.gb.counter = &c->barrier;
@@ -1735,8 +2374,13 @@ int refine_frontier(bisim_plan_s* p, bisim_stats* stats) {
         if (p->opts.max_ctas > 0) g = std::min(g, p->opts.max_ctas);
         const int per_warp = p->opts.split_budget > 0 ? p->opts.split_budget : 1;
         h.budget = (int)std::min<int64_t>((int64_t)per_warp * g * (threads / 32), 1 << 30);
+        h.peel = p->opts.peel >= 0 && h.kmax > 1 ? 1 : 0;
+        const int peel_items = p->opts.peel_items > 0 ? std::min(p->opts.peel_items, 1 << 12) : 8;
+        int64_t cap0 = (int64_t)peel_items * g * (threads / 32);
+        if (p->opts.splitters > 0) cap0 = std::min<int64_t>(cap0, p->opts.splitters);
+        h.cap0 = (int)std::min<int64_t>(cap0, 1 << 30);
         BISIM_TRY(launch_persistent(fn, args, threads, p, &grid, 1,
-                                    sizeof(int32_t) * (2 * (size_t)h.kmax + 1)));
+                                    sizeof(int32_t) * (2 * ((size_t)h.kmax + 32) + 1)));
     }
     BISIM_TRY(read_ctrl(p));
     p->stamp = base + (uint32_t)std::min<long long>(done + p->ctrl_h->rounds + 1, cap + 1);
@@ -1863,11 +2507,29 @@ int bisim_phase_times(uint64_t* out16) {
 #endif
 }
 
+int bisim_phase_trace(uint32_t* out, int32_t max_rounds) {
+#ifdef BISIM_PHASE_TIMERS
+    if (!out || max_rounds < 0) return BISIM_EINVAL;
+    BISIM_CUDA_TRY(cudaDeviceSynchronize());
+    const size_t nr = (size_t)std::min(max_rounds, BISIM_TRACE_MAX);
+    BISIM_CUDA_TRY(cudaMemcpyFromSymbol(out, g_round_trace, nr * 6 * sizeof(unsigned)));
+    return BISIM_OK;
+#else
+    (void)out;
+    (void)max_rounds;
+    set_last_error("built without BISIM_PHASE_TIMERS");
+    return BISIM_ENOTSUP;
+#endif
+}
+
 int bisim_phase_reset(void) {
 #ifdef BISIM_PHASE_TIMERS
     unsigned long long z[16] = {0};
     BISIM_CUDA_TRY(cudaDeviceSynchronize());
     BISIM_CUDA_TRY(cudaMemcpyToSymbol(g_phase_acc, z, sizeof(z)));
+    void* tr = nullptr;
+    BISIM_CUDA_TRY(cudaGetSymbolAddress(&tr, g_round_trace));
+    BISIM_CUDA_TRY(cudaMemset(tr, 0, sizeof(g_round_trace)));
     return BISIM_OK;
 #else
     set_last_error("built without BISIM_PHASE_TIMERS");

@@ -69,6 +69,19 @@ def test_random_small_vs_oracle(engine):
         assert st.num_blocks == defs.num_blocks(want)
 
 
+@pytest.mark.slow
+def test_dense_matches_pram_on_the_full_chain():
+    """The 50,000-state chain (99,999 iterations): the dense engine's leader
+    labels and iteration count equal the lock-step PRAM simulation exactly,
+    with Algorithm 3 and with Algorithm 2 (one label)."""
+    lts = lts_gen.chain(seed=2, n=50000)
+    for alg2 in (False, True):
+        labels, rounds, pre = oracle.pram_lts(lts, alg2=alg2)
+        got, st = run(lts, bisim.ENGINE_DENSE, raw_labels=True, rcpp_alg2=alg2)
+        assert got.tolist() == labels.tolist()
+        assert st.rounds == rounds and st.pre_rounds == pre
+
+
 def test_dense_matches_pram_rounds_and_leaders():
     """Priority rule on both sides: identical leader labels and iteration
     counts (Algorithm 3, and Algorithm 2 for one label)."""
@@ -105,6 +118,9 @@ def test_quotient_expansion_full_size(engine):
     assert got.tolist() == defs.pullback(lts.cls, oracle.ks_lts(lts.quotient)).tolist()
     B = defs.num_blocks(want)
     assert B + 1 <= st.rounds <= 3 * B - st.initial_blocks + 1
+    # the definitions, checked on the GPU's output directly
+    assert defs.is_stable(lts.n, lts.src, lts.act, lts.dst, got)
+    assert defs.refines(got, np.zeros(lts.n, dtype=np.int32))
 
 
 @pytest.mark.parametrize("engine", ENGINES, ids=ENGINE_IDS)
@@ -338,6 +354,49 @@ def test_several_splitters_large_worklist():
     got, st = run(lts, bisim.ENGINE_FRONTIER)
     assert got.tolist() == oracle.ks_lts(lts).tolist()
     assert st.steps * 4 < st.rounds  # many splitters per barrier round
+
+
+def _hub_lts(seed, n, hubs, hub_deg, deg=6, num_act=2):
+    """A few states with very many successors (hubs) among states of small
+    out-degree, two initial blocks: the hubs share label sets and initial
+    blocks, so their blocks are split state by state by many splitters."""
+    rng = np.random.default_rng(seed)
+    src = [np.repeat(np.arange(n, dtype=np.int64), deg)]
+    src.append(np.repeat(np.arange(hubs, dtype=np.int64), hub_deg))
+    src = np.concatenate(src)
+    dst = rng.integers(0, n, src.size)
+    act = rng.integers(0, num_act, src.size)
+    init = rng.integers(0, 2, n).astype(np.int32)
+    init[:hubs] = 0
+    perm = rng.permutation(src.size)
+    return lts_gen.LTS(f"hubs_s{seed}_n{n}", n, num_act, src[perm].astype(np.int32), act[perm].astype(np.int32),
+                       dst[perm].astype(np.int32), init)
+
+
+@pytest.mark.parametrize("peel,items", [(0, 0), (0, 1), (0, 64), (-1, 0)],
+                         ids=["default", "one-per-warp", "64-per-warp", "exclusive-only"])
+def test_peel_rounds(peel, items):
+    """Grid rounds where several splitters of one state may split the same
+    block (each marking one member of it, not its leader): the oracle's
+    partition, the iteration bounds of Theorem 3, and - with the default - far
+    fewer barrier rounds than iterations on LTSs with hub blocks."""
+    cases = [_hub_lts(1, 5000, 50, 400), _hub_lts(2, 20000, 200, 2000, num_act=3),
+             _hub_lts(3, 3000, 3, 3000, deg=2, num_act=1),
+             lts_gen.powerlaw(seed=3, n=200000), lts_gen.powerlaw(seed=8, n=50000, num_act=4),
+             lts_gen.kripke_uniform(seed=3, n=20000, m=80000),
+             lts_gen.quotient_expansion(seed=6, classes=500, trans=5000, copies_hi=40),
+             lts_gen.fan_out(300), lts_gen.chain(n=2000)]
+    cases += [lts_gen.random_small(700 + s, 60, 1 + s % 3, 240, blocks=1 + s % 3) for s in range(20)]
+    for lts in cases:
+        got, st = run(lts, bisim.ENGINE_FRONTIER, local_states=-1, peel=peel, peel_items=items)
+        want = oracle.ks_lts(lts)
+        assert got.tolist() == want.tolist(), lts.name
+        B = defs.num_blocks(want)
+        assert B + 1 <= st.rounds <= 3 * B - st.initial_blocks + 1, lts.name
+        assert st.steps <= st.rounds
+    if peel == 0 and items == 0:
+        _, st = run(lts_gen.powerlaw(seed=3, n=200000), bisim.ENGINE_FRONTIER, local_states=-1)
+        assert st.steps * 20 < st.rounds
 
 
 @pytest.mark.parametrize("n,local", [(10_000, 0), (10_000, 1 << 30), (200_000, 0)])
