@@ -4,12 +4,17 @@ A step is one whole reduction through the C ABI: bisim_plan (validation,
 sort by (source, label), mark slots, incoming-transition CSR, initial
 leaders, action-set preprocessing) and bisim_refine (the main loop and the
 canonical output) on inputs already resident in device memory. The default
-workload is the labelled LTS built by quotient expansion (seed 1: 2,000
-classes, 20,000 quotient transitions, 8 Zipf labels, 1..100 copies, 10%
-duplicates: about 101,658 states and 1,114,407 transitions).
+workload is the large power-law LTS (seed 3: 10,000,000 states, 99,917,783
+transitions, out-degree Pareto alpha = 2.1 with mean 10, 32 uniform labels,
+4 initial blocks from two atomic propositions). Single-LTS throughput is
+reported in transitions of the LTS reduced per second (m / reduction time),
+which stays comparable when the CPU oracle of the reference arm reduces a
+smaller member of the same family.
 
 Prints one JSON line (rank 0). `--impl reference` times the CPU oracle
-(Kanellakis-Smolka, single thread) on the same workload instead.
+(Kanellakis-Smolka, single thread) on the same workload instead (on a
+bounded sample where a full reduction takes the oracle more than a few
+seconds).
 """
 from __future__ import annotations
 
@@ -32,13 +37,14 @@ if ROOT not in sys.path:
 from paper_2105_11788_gb300 import lts_gen  # noqa: E402
 
 WORKLOADS = {
+    "powerlaw": ("large power-law LTS (seed 3, n=10,000,000, m=99,917,783, out-degree Pareto alpha=2.1 "
+                 "mean 10 capped at 10,000, uniform targets, |Act|=32 uniform, 4 initial blocks from 2 "
+                 "atomic propositions)", lambda: lts_gen.powerlaw(seed=3)),
     "qexp": ("labelled LTS by quotient expansion (seed 1, ~101.7k states, ~1.11M transitions, "
              "|Act|=8 Zipf, single initial block)", lambda: lts_gen.quotient_expansion(seed=1)),
     "kripke": ("Kripke structure (seed 0, n=1000, m=4000, 4 AP blocks)",
                lambda: lts_gen.kripke_uniform(seed=0)),
     "chain": ("deep-refinement chain (seed 2, n=50000)", lambda: lts_gen.chain(seed=2, n=50000)),
-    "powerlaw": ("power-law LTS (seed 3, n=10M, m~100M, |Act|=32, 4 AP blocks)",
-                 lambda: lts_gen.powerlaw(seed=3)),
     "powerlaw2m": ("power-law LTS (seed 3, n=2M, m~20M, |Act|=32, 4 AP blocks)",
                    lambda: lts_gen.powerlaw(seed=3, n=2_000_000)),
 }
@@ -56,10 +62,23 @@ def workload(args):
     return WORKLOADS[args.workload]
 
 
+# the reference arm's oracle reduces this smaller member of the same family
+# per step where a full reduction of the workload takes it tens of seconds
+REF_SAMPLE = {
+    "powerlaw": ("the power-law LTS of the same generator and seed with n=1,000,000 (m~10M), one full "
+                 "reduction per step", lambda: lts_gen.powerlaw(seed=3, n=1_000_000)),
+}
+
+SINGLE_METRIC = "LTS reduction throughput (transitions of the LTS reduced per second)"
+SINGLE_UNIT = "transitions/s"
+
+
 def vs_paper(args, value):
-    """value / the paper's number for this exact workload and metric (LTS/s), else None."""
+    """value / the paper's number for this exact workload and metric
+    (transitions/s of Fan_out_n at the paper's run time), else None."""
     if args.workload == "fanout" and args.fanout_n in PAPER_FANOUT_MS:
-        return value / (1000.0 / PAPER_FANOUT_MS[args.fanout_n])
+        n = args.fanout_n
+        return value / ((3 * n - 3) * 1000.0 / PAPER_FANOUT_MS[n])
     return None
 
 
@@ -215,7 +234,9 @@ def frontier_bytes_per_launch(st):
 
 
 def run_reference(args, world, rank):
-    """CPU oracle (Kanellakis-Smolka, one thread) on the same workload."""
+    """CPU oracle (Kanellakis-Smolka, one thread) on the same workload, or on
+    its bounded sample (REF_SAMPLE); throughput in transitions reduced per
+    second, like the GPU arm."""
     import oracle
 
     if world > 1 and rank != 0:
@@ -224,29 +245,32 @@ def run_reference(args, world, rank):
         run_reference_stream(args, world)
         return
     desc, make = workload(args)
-    lts = make()
+    if args.workload in REF_SAMPLE:
+        sample_desc, make_sample = REF_SAMPLE[args.workload]
+        lts = make_sample()
+        sample = f"{sample_desc} by oracle_ks (single-threaded C), {args.steps} timed steps"
+    else:
+        lts = make()
+        sample = f"{args.steps} full reductions of the workload (oracle_ks, single-threaded C)"
     for _ in range(args.warmup):
         oracle.ks_lts(lts)
     times = []
-    t_total = time.perf_counter()
     for _ in range(args.steps):
         t0 = time.perf_counter()
         oracle.ks_lts(lts)
         times.append(time.perf_counter() - t0)
-    t_total = time.perf_counter() - t_total
     ms = 1000.0 * sum(times) / len(times)
-    value = 1000.0 / ms
-    sample = f"{args.steps} full reductions of the workload (oracle_ks, single-threaded C)"
+    value = lts.m * 1000.0 / ms
     line = {
-        "impl": "reference", "metric": "LTS reduction throughput", "value": value,
-        "unit": "LTS/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "impl": "reference", "metric": SINGLE_METRIC, "value": value,
+        "unit": SINGLE_UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": vs_paper(args, value),
         "dtype": "int32", "data": "synthetic",
-        "config": {"workload": desc, "n": lts.n, "m": lts.m, "num_act": lts.num_act,
+        "config": {"workload": desc, "sample_n": lts.n, "sample_m": lts.m, "num_act": lts.num_act,
                    "l2": "CPU run"},
-        "cpu_baseline": {"value": value, "unit": "LTS/s", "cores": 1, "kind": "oracle",
-                         "sample": sample},
-        "e2e": {"value": value, "unit": "LTS/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "cpu_baseline": {"value": value, "unit": SINGLE_UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample, "ms_per_reduction": ms},
+        "e2e": {"value": value, "unit": SINGLE_UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
@@ -255,14 +279,24 @@ STREAM_DESC = ("batched stream (seed 4): LTSs with n log-uniform in [100, 200000
                "[1, 32], quotient expansion with n/20 classes")
 
 
+def stream_sample(ltss, k):
+    """k LTSs of the stream spread evenly over its size order (every
+    (len/k)-th by state count), so the sample follows the stream's size mix."""
+    order = sorted(range(len(ltss)), key=lambda i: (ltss[i].n, i))
+    k = max(1, min(k, len(order)))
+    return [order[int((j + 0.5) * len(order) / k)] for j in range(k)]
+
+
 def run_reference_stream(args, world):
     """CPU oracle on the stream: every step reduces the same bounded sample
-    (the first `--ref-sample` LTSs of the stream, a random draw of its size
-    mix) one after the other; LTS/s = sample size / step time."""
+    (`--ref-sample` LTSs spread evenly over the stream's size order) one after
+    the other; LTS/s = sample size / step time."""
     import oracle
 
-    k = max(1, min(args.ref_sample, args.stream_k))
-    ltss, _ = lts_gen.batch_stream(seed=4, k=k)
+    ltss_all, _ = lts_gen.batch_stream(seed=4, k=args.stream_k)
+    idx = stream_sample(ltss_all, args.ref_sample)
+    ltss = [ltss_all[i] for i in idx]
+    k = len(ltss)
     for _ in range(args.warmup):
         for lts in ltss:
             oracle.ks_lts(lts)
@@ -274,15 +308,20 @@ def run_reference_stream(args, world):
         times.append(time.perf_counter() - t0)
     ms = 1000.0 * sum(times) / len(times)
     value = k * 1000.0 / ms
-    sample = (f"the first {k} LTSs of the {args.stream_k}-LTS stream ({sum(l.n for l in ltss)} states) "
-              f"reduced one after the other by oracle_ks (single-threaded C), {args.steps} times")
+    n_sample = sum(l.n for l in ltss)
+    mean_stream = sum(l.n for l in ltss_all) / len(ltss_all)
+    sample = (f"{k} LTSs spread evenly over the size order of the {args.stream_k}-LTS stream "
+              f"(mean {n_sample / k:.0f} states against {mean_stream:.0f} for the whole stream), reduced one "
+              f"after the other by oracle_ks (single-threaded C), {args.steps} times")
     line = {
         "impl": "reference", "metric": "batched LTS reduction throughput", "value": value,
         "unit": "LTS/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "int32", "data": "synthetic",
         "config": {"workload": STREAM_DESC, "k": args.stream_k, "sample": k, "l2": "CPU run"},
-        "cpu_baseline": {"value": value, "unit": "LTS/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "LTS/s", "cores": 1, "kind": "oracle", "sample": sample,
+                         "states_per_s": n_sample * 1000.0 / ms, "sample_mean_n": n_sample / k,
+                         "stream_mean_n": mean_stream},
         "e2e": {"value": value, "unit": "LTS/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -448,7 +487,8 @@ def cpu_baseline(lts, budget_s):
         if time.perf_counter() - t0 > budget_s:
             break
     el = time.perf_counter() - t0
-    return {"value": k / el, "unit": "LTS/s", "cores": 1, "kind": "oracle",
+    return {"value": k * lts.m / el, "unit": SINGLE_UNIT, "cores": 1, "kind": "oracle",
+            "ms_per_reduction": 1000.0 * el / k,
             "sample": f"{k} full reductions of the same workload by oracle_ks (single-threaded C), "
                       f"{el:.1f} s"}
 
@@ -459,7 +499,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="qexp", choices=sorted(WORKLOADS) + ["fanout", "stream"])
+    ap.add_argument("--workload", default="powerlaw", choices=sorted(WORKLOADS) + ["fanout", "stream"])
     ap.add_argument("--fanout-n", type=int, default=700, help="fanout: states of Fan_out_n")
     ap.add_argument("--stream-k", type=int, default=4096, help="LTSs in the stream workload")
     ap.add_argument("--plain-sample", type=int, default=128,
@@ -558,7 +598,7 @@ def main():
     barrier(world)
     clk = clocks.stop()
     ms_step = max_over_ranks(total_ms / args.steps, world, dev)
-    value = world * 1000.0 / ms_step
+    value = world * lts.m * 1000.0 / ms_step
     st = stats[-1]
     hbm, peak_kind = read_peaks()
     achieved = (sum(kernel_bytes) / len(kernel_bytes)) / (sum(kernel_ms) / len(kernel_ms) * 1e-3) / 1e9
@@ -569,18 +609,38 @@ def main():
     elif st.grid_ctas == 1:
         kname, schedule = "k_frontier_batch", "one CTA (sparse LTS)"
     elif st.local_steps > 0:
-        # started on one CTA, handed to the hybrid: name the kernel that ran more rounds
-        kname = "k_frontier_batch" if 2 * st.local_steps >= st.steps else "k_frontier_hybrid"
+        # started on one CTA, handed to the hybrid: the main loop is two
+        # launches, whose bytes and time the achieved figure sums
+        kname = "k_frontier_batch+k_frontier_hybrid"
         schedule = f"one CTA for {st.local_steps} of {st.steps} rounds, then hybrid"
     elif args.light_edges < 0:
         kname, schedule = "k_frontier_main", "every round on the whole grid"
     else:
         kname, schedule = "k_frontier_hybrid", "hybrid (light rounds on one CTA)"
+    km_avg = sum(kernel_ms) / len(kernel_ms)
     roof = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm, "peak_kind": peak_kind,
-            "traffic": recorded_traffic(kname, args.workload),
-            "kernel_ms": sum(kernel_ms) / len(kernel_ms),
+            "traffic": None if "+" in kname else recorded_traffic(kname, args.workload),
+            "kernel_ms": km_avg,
             "bytes_per_launch": sum(kernel_bytes) / len(kernel_bytes)}
+    # the rounds' other bound: barriers and dependent loads. Measured grid
+    # barrier cost at this launch's grid size, beside the time per round
+    latency = None
+    if st.engine != bisim.ENGINE_DENSE and st.steps > 0:
+        bar_ns = None
+        try:
+            ctas = max(1, st.grid_ctas)
+            thr = args.threads or (1024 if ctas == 1 else 512)
+            bar_ns = min(bisim.bisim_barrier_cost(ctas, thr, 5000, sp) for _ in range(3))
+        except bisim.BisimError:
+            pass
+        per_round = 2 if st.rounds - 1 <= st.steps else 3  # one splitter per round: mark, split
+        us_step = 1000.0 * st.t_main_ms / st.steps
+        latency = {"us_per_round": us_step, "rounds": st.steps,
+                   "barrier_us": None if bar_ns is None else bar_ns / 1000.0,
+                   "barriers_per_round": per_round,
+                   "barrier_share": None if bar_ns is None else per_round * bar_ns / 1000.0 / us_step,
+                   "splitter_iterations_per_round": (st.rounds - 1) / st.steps}
 
     # end to end through the host-buffer entry point
     pin = lambda a: torch.from_numpy(a).pin_memory()  # noqa: E731
@@ -589,6 +649,9 @@ def main():
     ho = torch.empty(max(lts.n, 1), dtype=torch.int32).pin_memory()
     e2e_ms = []
     for i in range(max(3, args.steps // 2) + 1):
+        if flush is not None:
+            flush.fill_(1)  # untimed: evicts L2, as between the device-timed steps
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
         bisim.bisim_reduce_host(lts.n, lts.m, lts.num_act, hs.data_ptr(), ha.data_ptr(),
                                 hd.data_ptr(), hi.data_ptr() if hi is not None else None,
@@ -611,7 +674,7 @@ def main():
     if rank == 0:
         visits = (st.pre_rounds + st.rounds) * lts.m
         line = {
-            "metric": "LTS reduction throughput", "value": value, "unit": "LTS/s",
+            "metric": SINGLE_METRIC, "value": value, "unit": SINGLE_UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": vs_paper(args, value),
             "dtype": "int32", "data": "synthetic",
@@ -622,8 +685,9 @@ def main():
                              else "inputs larger than L2",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "roofline": roof,
+            "latency": latency,
             "hbm_rounds": paper_hbm,
-            "e2e": {"value": world * 1000.0 / e2e_step, "unit": "LTS/s",
+            "e2e": {"value": world * lts.m * 1000.0 / e2e_step, "unit": SINGLE_UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4 * lts.n,
                     "ms_per_step": e2e_step},
             "cpu_baseline": cpu,
@@ -634,9 +698,17 @@ def main():
                        "initial_blocks": st.initial_blocks, "num_blocks": st.num_blocks,
                        "mark_length": st.mark_length, "t_plan_ms": st.t_plan_ms,
                        "t_refine_ms": st.t_refine_ms, "t_pre_ms": st.t_pre_ms,
-                       "t_main_ms": st.t_main_ms, "us_per_round": 1000 * st.t_main_ms / max(st.rounds, 1),
+                       "t_main_ms": st.t_main_ms, "reduction_ms": ms_step,
+                       "lts_per_s": world * 1000.0 / ms_step,
+                       "us_per_round": 1000 * st.t_main_ms / max(st.steps, 1),
+                       "us_per_iteration": 1000 * st.t_main_ms / max(st.rounds, 1),
                        "edges_visited": st.edges_visited, "states_visited": st.states_visited,
                        "grid_ctas": st.grid_ctas,
+                       # incoming transitions the main loop's kernels walked, per second of main loop
+                       "transition_visits_per_s": st.edges_visited / (st.t_main_ms * 1e-3)
+                       if st.t_main_ms > 0 else None,
+                       # (pre_rounds + rounds) * m / step time: the visits of the paper's
+                       # m-thread rounds, which touch every transition every iteration
                        "pram_transition_visits_per_s": visits / (ms_step * 1e-3)},
         }
         print(json.dumps(line), flush=True)

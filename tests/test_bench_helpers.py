@@ -62,8 +62,28 @@ def test_algorithmic_bytes():
 def test_ratio_to_the_paper_fan_out_time():
     args = types.SimpleNamespace(workload="fanout", fanout_n=700)
     ms = bench.PAPER_FANOUT_MS[700]
-    assert abs(bench.vs_paper(args, 1000.0 / ms) - 1.0) < 1e-12
+    # the paper's run time as transitions of Fan_out_700 (3n - 3) reduced per second
+    assert abs(bench.vs_paper(args, (3 * 700 - 3) * 1000.0 / ms) - 1.0) < 1e-12
     assert bench.vs_paper(types.SimpleNamespace(workload="qexp", fanout_n=700), 5.0) is None
+
+
+def test_default_workload_is_the_large_power_law_lts():
+    import inspect
+
+    src = inspect.getsource(bench.main)
+    assert 'default="powerlaw"' in src
+    assert "n=10,000,000" in bench.WORKLOADS["powerlaw"][0]
+    # the reference arm reduces a smaller member of the same family per step
+    assert "powerlaw" in bench.REF_SAMPLE
+
+
+def test_stream_sample_follows_the_size_mix():
+    ltss = [types.SimpleNamespace(n=n) for n in [5, 1, 9, 3, 7, 2, 8, 4, 6, 10]]
+    idx = bench.stream_sample(ltss, 5)
+    assert len(set(idx)) == 5
+    sizes = sorted(ltss[i].n for i in idx)
+    assert sizes == [2, 4, 6, 8, 10]
+    assert len(bench.stream_sample(ltss, 50)) == 10
 
 
 def test_reference_arm_lines():
@@ -72,12 +92,13 @@ def test_reference_arm_lines():
     import subprocess
     import sys
 
-    for extra in (["--workload", "kripke"], ["--workload", "stream", "--ref-sample", "4"]):
+    for extra in (["--workload", "kripke"], ["--workload", "stream", "--stream-k", "64", "--ref-sample", "4"]):
         r = subprocess.run([sys.executable, os.path.join(bench.ROOT, "bench.py"), "--impl", "reference",
                             "--steps", "1", "--warmup", "0", *extra],
                            capture_output=True, text=True, timeout=600, cwd=bench.ROOT)
         assert r.returncode == 0, r.stderr
         line = json.loads([x for x in r.stdout.splitlines() if x.startswith("{")][-1])
-        assert line["impl"] == "reference" and line["unit"] == "LTS/s" and line["value"] > 0
+        unit = "LTS/s" if "stream" in extra else "transitions/s"
+        assert line["impl"] == "reference" and line["unit"] == unit and line["value"] > 0
         assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
         assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
