@@ -126,6 +126,11 @@ typedef struct bisim_opts {
     int32_t peel_items;       /* frontier engine, grid rounds with several splitters:
                                  at most this many splitters of one state per warp of
                                  the grid (0 = 8) */
+    int32_t slots;            /* mark-slot layout (Section 4.1.1): 0 = from every state's
+                                 label set when |Act| <= 128 (the validation pass
+                                 records the label sets; no sort), else by sorting
+                                 the transitions by (source, label); 1 = always by
+                                 the sort. Same arrays */
 } bisim_opts;
 
 typedef struct bisim_stats {
@@ -199,6 +204,26 @@ int bisim_refine(bisim_plan_t plan, int32_t* out_block, bisim_stats* stats);
 
 /* Release the plan's device memory (stream-ordered). NULL is ignored. */
 void bisim_plan_destroy(bisim_plan_t plan);
+
+/*
+ * bisim_plan_arrays - copy a plan's mark-slot layout and incoming-transition
+ * index to host memory (for checking them against Section 4.1.1; not needed
+ * to reduce an LTS). With the transitions sorted by (source, label), off is
+ * the exclusive prefix sum of nr_marks (off[n] = mark_length, Algorithm 4's
+ * off read as start offsets), and the slot of a transition s -a-> t is
+ * off(s) + order, order = the number of labels of s smaller than a.
+ * off_h       int32 [n + 1] or NULL
+ * slot_src_h  int32 [mark_length] or NULL: the state owning each slot
+ * slot_act_h  int32 [mark_length] or NULL: its label
+ * in_ptr_h    int32 [n + 1] or NULL: incoming transitions of t are entries
+ *             in_ptr[t] .. in_ptr[t+1]-1 of in_edge
+ * in_edge_h   int64 [m] or NULL: (source << 32) | slot per incoming
+ *             transition (the order inside one target's range is arbitrary)
+ * mark_length NULL or receives mark_length
+ * Synchronises the plan's stream. Errors: BISIM_EINVAL (plan NULL), BISIM_ECUDA.
+ */
+int bisim_plan_arrays(bisim_plan_t plan, int32_t* off_h, int32_t* slot_src_h, int32_t* slot_act_h,
+                      int32_t* in_ptr_h, int64_t* in_edge_h, int64_t* mark_length);
 
 /*
  * bisim_reduce_host - one whole reduction from HOST buffers: copies the
@@ -300,6 +325,30 @@ int bisim_phase_reset(void);
  * max_rounds < 0), BISIM_ECUDA, BISIM_ENOTSUP (default build).
  */
 int bisim_phase_trace(uint32_t* out, int32_t max_rounds);
+
+/*
+ * Device memory of the library (the paper has no counterpart; this is for
+ * admission control by a serving loop). Plans allocate stream-ordered from the
+ * current device's default memory pool, whose release threshold the library
+ * raises so that memory a destroyed plan frees is kept for the next plan
+ * instead of being returned at every synchronisation. So the pool can hold
+ * more than the plans alive use:
+ *
+ * bisim_pool_usage      used: bytes of the pool in use by live allocations;
+ *                       used_high: the most in use since the last
+ *                       bisim_pool_reset_high; reserved: bytes the pool holds
+ *                       from the device, in use or not. Any pointer may be NULL.
+ * bisim_pool_reset_high restarts the high-water mark at the current use.
+ * bisim_pool_trim       synchronises the device, then returns the pool's unused
+ *                       memory to the device until at most keep_bytes of
+ *                       unused memory stay reserved.
+ * These act on the default pool of the current device, which other users of
+ * that pool (cudaMallocAsync with the default pool) share.
+ * Errors: BISIM_ECUDA.
+ */
+int bisim_pool_usage(uint64_t* used, uint64_t* used_high, uint64_t* reserved);
+int bisim_pool_reset_high(void);
+int bisim_pool_trim(uint64_t keep_bytes);
 
 /* Largest n accepted by bisim_canonical_ids_noalloc. */
 #define BISIM_NOALLOC_MAX_N (1 << 20)

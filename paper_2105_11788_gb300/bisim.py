@@ -53,6 +53,7 @@ class bisim_opts(ctypes.Structure):
         ("local_states", ctypes.c_int32),
         ("peel", ctypes.c_int32),
         ("peel_items", ctypes.c_int32),
+        ("slots", ctypes.c_int32),
     ]
 
 
@@ -160,11 +161,11 @@ def make_opts(engine: int = ENGINE_AUTO, rcpp_alg2: bool = False, raw_labels: bo
               test_hook: int = 0, max_ctas: int = 0, light_edges: int = 0,
               preprocess: int = 0, wide_threads: int = 0, wide_min_states: int = 0,
               splitters: int = 0, split_budget: int = 0, multi_min_states: int = 0,
-              local_states: int = 0, peel: int = 0, peel_items: int = 0) -> bisim_opts:
+              local_states: int = 0, peel: int = 0, peel_items: int = 0, slots: int = 0) -> bisim_opts:
     return bisim_opts(engine, int(rcpp_alg2), int(raw_labels), threads, ctas_per_sm, test_hook,
                       round_cap, timeout_ms, max_ctas, light_edges, preprocess, wide_threads,
                       wide_min_states, splitters, split_budget, multi_min_states, local_states, peel,
-                      peel_items)
+                      peel_items, slots)
 
 
 # ----------------------------------------------------------- C-ABI mirrors
@@ -315,6 +316,54 @@ def bisim_phase_times() -> dict:
     buf = (ctypes.c_uint64 * 16)()
     _check(f(ctypes.addressof(buf)), "bisim_phase_times")
     return {k: int(v) for k, v in zip(PHASE_NAMES, buf)}
+
+
+def bisim_pool_usage() -> dict:
+    """Bytes of the device's default memory pool: in use, most in use since
+    the last reset, reserved from the device."""
+    f = load().bisim_pool_usage
+    U = ctypes.POINTER(ctypes.c_uint64)
+    f.argtypes = [U, U, U]
+    f.restype = ctypes.c_int
+    u, h, r = ctypes.c_uint64(0), ctypes.c_uint64(0), ctypes.c_uint64(0)
+    _check(f(ctypes.byref(u), ctypes.byref(h), ctypes.byref(r)), "bisim_pool_usage")
+    return {"used": int(u.value), "used_high": int(h.value), "reserved": int(r.value)}
+
+
+def bisim_pool_reset_high() -> None:
+    f = load().bisim_pool_reset_high
+    f.argtypes = []
+    f.restype = ctypes.c_int
+    _check(f(), "bisim_pool_reset_high")
+
+
+def bisim_pool_trim(keep_bytes: int = 0) -> None:
+    """Return the pool's unused memory to the device (keeping keep_bytes)."""
+    f = load().bisim_pool_trim
+    f.argtypes = [ctypes.c_uint64]
+    f.restype = ctypes.c_int
+    _check(f(int(keep_bytes)), "bisim_pool_trim")
+
+
+def bisim_plan_arrays(handle: int, n: int, m: int) -> dict:
+    """The plan's mark-slot layout and incoming-transition index on the host."""
+    import numpy as np
+
+    f = load().bisim_plan_arrays
+    P = ctypes.c_void_p
+    f.argtypes = [P, P, P, P, P, P, ctypes.POINTER(ctypes.c_int64)]
+    f.restype = ctypes.c_int
+    L = ctypes.c_int64(0)
+    _check(f(handle, None, None, None, None, None, ctypes.byref(L)), "bisim_plan_arrays")
+    off = np.zeros(n + 1, np.int32)
+    in_ptr = np.zeros(n + 1, np.int32)
+    ss = np.zeros(max(L.value, 1), np.int32)
+    sa = np.zeros(max(L.value, 1), np.int32)
+    ie = np.zeros(max(m, 1), np.int64)
+    ptr = lambda a: a.ctypes.data_as(P)  # noqa: E731
+    _check(f(handle, ptr(off), ptr(ss), ptr(sa), ptr(in_ptr), ptr(ie), ctypes.byref(L)), "bisim_plan_arrays")
+    return {"off": off, "slot_src": ss[:L.value], "slot_act": sa[:L.value], "in_ptr": in_ptr, "in_edge": ie[:m],
+            "mark_length": int(L.value)}
 
 
 def bisim_phase_trace(max_rounds: int = 1 << 16):

@@ -168,6 +168,27 @@ void bisim_plan_destroy(bisim_plan_t p) {
     delete p;
 }
 
+int bisim_plan_arrays(bisim_plan_t p, int32_t* off_h, int32_t* slot_src_h, int32_t* slot_act_h, int32_t* in_ptr_h,
+                      int64_t* in_edge_h, int64_t* mark_length) {
+    if (!p) {
+        set_last_error("bad argument");
+        return BISIM_EINVAL;
+    }
+    const size_t n1 = (size_t)p->n + 1, L = (size_t)p->L, m = (size_t)p->m;
+    if (mark_length) *mark_length = p->L;
+    if (off_h && p->off.p) BISIM_CUDA_TRY(cudaMemcpyAsync(off_h, p->off.p, 4 * n1, cudaMemcpyDeviceToHost, p->st));
+    if (in_ptr_h && p->in_ptr.p)
+        BISIM_CUDA_TRY(cudaMemcpyAsync(in_ptr_h, p->in_ptr.p, 4 * n1, cudaMemcpyDeviceToHost, p->st));
+    if (slot_src_h && L)
+        BISIM_CUDA_TRY(cudaMemcpyAsync(slot_src_h, p->slot_src.p, 4 * L, cudaMemcpyDeviceToHost, p->st));
+    if (slot_act_h && L)
+        BISIM_CUDA_TRY(cudaMemcpyAsync(slot_act_h, p->slot_act.p, 4 * L, cudaMemcpyDeviceToHost, p->st));
+    if (in_edge_h && m)
+        BISIM_CUDA_TRY(cudaMemcpyAsync(in_edge_h, p->in_edge.p, 8 * m, cudaMemcpyDeviceToHost, p->st));
+    BISIM_CUDA_TRY(cudaStreamSynchronize(p->st));
+    return BISIM_OK;
+}
+
 int bisim_reduce_host(int32_t n, int64_t m, int32_t num_act, const int32_t* src_h,
                       const int32_t* act_h, const int32_t* dst_h, const int32_t* init_h,
                       int32_t* out_block_h, const bisim_opts* opts, void* stream,

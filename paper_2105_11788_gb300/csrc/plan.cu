@@ -120,6 +120,199 @@ __global__ void k_csr_scatter(const uint32_t* __restrict__ tkey, const uint64_t*
         in_edge[atomicAdd(&cursor[tkey[i]], 1u)] = tval[i];
 }
 
+// Mark-slot layout from label sets (|Act| <= 32 * MASK_WORDS_MAX). One pass
+// over the transitions validates them and, for valid ones, ORs the label
+// into its source's label-set bitmask and counts the target's in-degree.
+// Then for a state s with label set M(s): nr_marks(s) = |M(s)|, off = the
+// exclusive prefix sum of nr_marks, and the slot of a transition s -a-> t is
+// off(s) + |{b in M(s) : b < a}| - the rank of (s, a) among the distinct
+// (source, label) pairs in (source, label) order, which is exactly what
+// Algorithm 4's sort, action_switch and segmented scans compute.
+constexpr int MASK_WORDS_MAX = 4;
+
+__device__ __forceinline__ void count_transition(int32_t s, int32_t a, int32_t d, int mask_words, uint32_t* amask,
+                                                 uint32_t* indeg) {
+    atomicOr(&amask[(size_t)s * mask_words + (a >> 5)], 1u << (a & 31));
+    atomicAdd(&indeg[d], 1u);
+}
+
+__global__ void k_validate_count(const int32_t* __restrict__ src, const int32_t* __restrict__ act,
+                                 const int32_t* __restrict__ dst, const int32_t* __restrict__ init, int32_t n,
+                                 int64_t m, int32_t A, int* status, uint32_t* used, int vec, int mask_words,
+                                 uint32_t* amask, uint32_t* indeg) {
+    const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
+    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int bad = 0;
+    const int64_t m4 = vec ? m / 4 : 0;
+    for (int64_t q = gtid; q < m4; q += gsz) {
+        const int4 s = ld4(src, q), d = ld4(dst, q);
+        const int4 a = act ? ld4(act, q) : make_int4(0, 0, 0, 0);
+        const int b0 = check_transition(s.x, a.x, d.x, n, A, used), b1 = check_transition(s.y, a.y, d.y, n, A, used);
+        const int b2 = check_transition(s.z, a.z, d.z, n, A, used), b3 = check_transition(s.w, a.w, d.w, n, A, used);
+        if (!b0) count_transition(s.x, a.x, d.x, mask_words, amask, indeg);
+        if (!b1) count_transition(s.y, a.y, d.y, mask_words, amask, indeg);
+        if (!b2) count_transition(s.z, a.z, d.z, mask_words, amask, indeg);
+        if (!b3) count_transition(s.w, a.w, d.w, mask_words, amask, indeg);
+        bad |= b0 | b1 | b2 | b3;
+    }
+    for (int64_t i = 4 * m4 + gtid; i < m; i += gsz) {
+        const int32_t s = src[i], a = act ? act[i] : 0, d = dst[i];
+        const int b = check_transition(s, a, d, n, A, used);
+        if (!b) count_transition(s, a, d, mask_words, amask, indeg);
+        bad |= b;
+    }
+    if (init)
+        for (int64_t i = gtid; i < n; i += gsz)
+            if ((unsigned)init[i] >= (unsigned)n) bad = 1;
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, ST_INVALID);
+}
+
+// nr_marks of every state (into off, scanned afterwards)
+__global__ void k_mask_count(const uint32_t* __restrict__ amask, int32_t n, int mask_words, uint32_t* nr) {
+    const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gsz) {
+        uint32_t c = 0;
+        for (int w = 0; w < mask_words; w++) c += __popc(amask[(size_t)s * mask_words + w]);
+        nr[s] = c;
+    }
+}
+
+// owner and label of every mark slot
+__global__ void k_mask_slots(const uint32_t* __restrict__ amask, const uint32_t* __restrict__ off, int32_t n,
+                             int mask_words, int32_t* slot_src, int32_t* slot_act) {
+    const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gsz) {
+        uint32_t k = off[s];
+        for (int w = 0; w < mask_words; w++) {
+            uint32_t bits = amask[(size_t)s * mask_words + w];
+            while (bits) {
+                const int b = __ffs(bits) - 1;
+                bits &= bits - 1u;
+                slot_src[k] = (int32_t)s;
+                slot_act[k] = 32 * w + b;
+                k++;
+            }
+        }
+    }
+}
+
+// incoming-transition CSR by target with (source << 32 | slot) entries
+__device__ __forceinline__ void csr_put(int32_t s, int32_t a, int32_t d, const uint32_t* __restrict__ amask,
+                                        const uint32_t* __restrict__ off, int mask_words, uint32_t* cursor,
+                                        unsigned long long* in_edge) {
+    uint32_t order = 0;
+    const uint32_t* ms = amask + (size_t)s * mask_words;
+    for (int w = 0; w < (a >> 5); w++) order += __popc(ms[w]);
+    order += __popc(ms[a >> 5] & ((1u << (a & 31)) - 1u));
+    const uint32_t slot = off[s] + order;
+    in_edge[atomicAdd(&cursor[d], 1u)] = ((unsigned long long)(uint32_t)s << 32) | slot;  // (large n only)
+}
+
+__global__ void k_mask_csr(const int32_t* __restrict__ src, const int32_t* __restrict__ act,
+                           const int32_t* __restrict__ dst, int64_t m, const uint32_t* __restrict__ amask,
+                           const uint32_t* __restrict__ off, int mask_words, int vec, uint32_t* cursor,
+                           unsigned long long* in_edge) {
+    const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
+    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t m4 = vec ? m / 4 : 0;
+    for (int64_t q = gtid; q < m4; q += gsz) {
+        const int4 s = ld4(src, q), d = ld4(dst, q);
+        const int4 a = act ? ld4(act, q) : make_int4(0, 0, 0, 0);
+        csr_put(s.x, a.x, d.x, amask, off, mask_words, cursor, in_edge);
+        csr_put(s.y, a.y, d.y, amask, off, mask_words, cursor, in_edge);
+        csr_put(s.z, a.z, d.z, amask, off, mask_words, cursor, in_edge);
+        csr_put(s.w, a.w, d.w, amask, off, mask_words, cursor, in_edge);
+    }
+    for (int64_t i = 4 * m4 + gtid; i < m; i += gsz)
+        csr_put(src[i], act ? act[i] : 0, dst[i], amask, off, mask_words, cursor, in_edge);
+}
+
+// The incoming-transition CSR in two passes, without a returning global
+// atomic per transition. Targets are cut into bins of 2^bin_bits states;
+// since in_ptr is already known, a bin's entries occupy the known range
+// [in_ptr[first target], in_ptr[last target + 1]) of in_edge.
+//   pass A: a CTA takes a tile of transitions, ranks them per bin with
+//     shared-memory atomics, reserves each bin's share of the tile with one
+//     global atomic per (CTA, bin), and writes (target, source << 32 | slot)
+//     records into the bin's range of two scratch arrays;
+//   pass B: one CTA per bin places the bin's records by target with
+//     shared-memory counters: entry in_ptr[t] + (rank among t's records).
+constexpr int CSR_A_THREADS = 1024;
+constexpr int CSR_A_ITEMS = 16;   // transitions per thread of pass A
+constexpr int CSR_MAX_BINS = 4096;
+constexpr int CSR_B_THREADS = 1024;
+
+__device__ __forceinline__ uint32_t slot_of(int32_t s, int32_t a, const uint32_t* __restrict__ amask,
+                                            const uint32_t* __restrict__ off, int mask_words) {
+    uint32_t order = 0;
+    const uint32_t* ms = amask + (size_t)s * mask_words;
+    for (int w = 0; w < (a >> 5); w++) order += __popc(ms[w]);
+    order += __popc(ms[a >> 5] & ((1u << (a & 31)) - 1u));
+    return off[s] + order;
+}
+
+__global__ void __launch_bounds__(CSR_A_THREADS) k_csr_bin(const int32_t* __restrict__ src,
+                                                           const int32_t* __restrict__ act,
+                                                           const int32_t* __restrict__ dst, int64_t m,
+                                                           const uint32_t* __restrict__ amask,
+                                                           const uint32_t* __restrict__ off, int mask_words,
+                                                           int bin_bits, int nbins, uint32_t* bin_cursor,
+                                                           uint32_t* rec_t, unsigned long long* rec_v) {
+    __shared__ uint32_t cnt[CSR_MAX_BINS];
+    __shared__ uint32_t base[CSR_MAX_BINS];
+    const int64_t tile0 = (int64_t)blockIdx.x * (CSR_A_THREADS * CSR_A_ITEMS);
+    for (int b = threadIdx.x; b < nbins; b += CSR_A_THREADS) cnt[b] = 0;
+    __syncthreads();
+    int32_t t[CSR_A_ITEMS];
+    uint32_t rk[CSR_A_ITEMS];
+#pragma unroll
+    for (int j = 0; j < CSR_A_ITEMS; j++) {
+        const int64_t i = tile0 + (int64_t)j * CSR_A_THREADS + threadIdx.x;
+        t[j] = i < m ? dst[i] : -1;
+    }
+#pragma unroll
+    for (int j = 0; j < CSR_A_ITEMS; j++)
+        if (t[j] >= 0) rk[j] = atomicAdd(&cnt[t[j] >> bin_bits], 1u);
+    __syncthreads();
+    for (int b = threadIdx.x; b < nbins; b += CSR_A_THREADS)
+        if (cnt[b]) base[b] = atomicAdd(&bin_cursor[b], cnt[b]);
+    __syncthreads();
+    // the tile's sources and labels again (just read, so close), its slots, and the records
+#pragma unroll
+    for (int j = 0; j < CSR_A_ITEMS; j++)
+        if (t[j] >= 0) {
+            const int64_t i = tile0 + (int64_t)j * CSR_A_THREADS + threadIdx.x;
+            const int32_t s = src[i], a = act ? act[i] : 0;
+            const uint32_t q = base[t[j] >> bin_bits] + rk[j];
+            rec_t[q] = (uint32_t)t[j];
+            rec_v[q] = ((unsigned long long)(uint32_t)s << 32) | slot_of(s, a, amask, off, mask_words);
+        }
+}
+
+__global__ void __launch_bounds__(CSR_B_THREADS) k_csr_place(const uint32_t* __restrict__ in_ptr, int32_t n,
+                                                             int bin_bits, const uint32_t* __restrict__ rec_t,
+                                                             const unsigned long long* __restrict__ rec_v,
+                                                             unsigned long long* in_edge) {
+    extern __shared__ uint32_t tcnt[];  // 2^bin_bits counters
+    const int64_t lo = (int64_t)blockIdx.x << bin_bits;
+    const int64_t hi = min((int64_t)n, lo + ((int64_t)1 << bin_bits));
+    for (int64_t i = threadIdx.x; i < hi - lo; i += CSR_B_THREADS) tcnt[i] = 0;
+    __syncthreads();
+    const uint32_t r0 = in_ptr[lo], r1 = in_ptr[hi];
+    for (uint32_t i = r0 + threadIdx.x; i < r1; i += CSR_B_THREADS) {
+        const uint32_t tt = rec_t[i];
+        const uint32_t r = atomicAdd(&tcnt[tt - (uint32_t)lo], 1u);
+        in_edge[in_ptr[tt] + r] = rec_v[i];
+    }
+}
+
+// the bins' first entries: bin_cursor[b] = in_ptr[b << bin_bits]
+__global__ void k_bin_starts(const uint32_t* __restrict__ in_ptr, int32_t n, int bin_bits, int nbins,
+                             uint32_t* bin_cursor) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nbins; b += gridDim.x * blockDim.x)
+        bin_cursor[b] = in_ptr[min((int64_t)n, (int64_t)b << bin_bits)];
+}
+
 // label set of every state as a bitmask of mask_words 32-bit words
 __global__ void k_label_masks(const int32_t* __restrict__ slot_src, const int32_t* __restrict__ slot_act,
                               int64_t L, int mask_words, uint32_t* amask) {
@@ -475,43 +668,18 @@ int persistent_ms(bisim_plan_s* p, double* ms) {
     return BISIM_OK;
 }
 
-int plan_build(bisim_plan_s* p, const int32_t* src, const int32_t* act, const int32_t* dst,
-               const int32_t* init) {
+// a2 + a3 by Algorithm 4's route: sort the transitions by (source, label),
+// flag where a new (source, label) pair starts, scan the flags; the slots,
+// nr_marks and off follow, then the incoming-transition CSR by target
+// (counting sort; the order inside one target's list is whatever the atomics
+// give: marking is idempotent, so it never matters).
+static int slots_by_sort(bisim_plan_s* p, const int32_t* src, const int32_t* act, const int32_t* dst, int vec) {
     const int32_t n = p->n;
     const int64_t m = p->m;
     const int32_t A = p->A;
     cudaStream_t st = p->st;
-
-    BISIM_TRY(p->ctrl.alloc(sizeof(bisim_ctrl), st));
-    BISIM_CUDA_TRY(cudaMemsetAsync(p->ctrl.p, 0, sizeof(bisim_ctrl), st));
-    int* status = &p->ctrl.as<bisim_ctrl>()->status;
-
-    // a1: validation and the set of labels that occur
-    DevMem used;
-    BISIM_TRY(used.alloc(sizeof(uint32_t) * (size_t)A, st));
-    BISIM_CUDA_TRY(cudaMemsetAsync(used.p, 0, sizeof(uint32_t) * (size_t)A, st));
-    const int vec = (((uintptr_t)src | (uintptr_t)dst | (uintptr_t)act) & 15u) == 0 ? 1 : 0;
-    k_validate<<<grid_for(std::max<int64_t>(m, n), T), T, 0, st>>>(src, act, dst, init, n, m, A,
-                                                                   status, used.as<uint32_t>(), vec);
-    BISIM_LAUNCHED();
-    BISIM_CUDA_TRY(cudaGetLastError());
-    std::vector<uint32_t> used_h((size_t)A);
-    BISIM_CUDA_TRY(cudaMemcpyAsync(used_h.data(), used.p, sizeof(uint32_t) * (size_t)A,
-                                   cudaMemcpyDeviceToHost, st));
-    BISIM_TRY(read_ctrl(p));
-    if (p->ctrl_h->status & ST_INVALID) {
-        set_last_error("an input array entry is out of range");
-        return BISIM_EINVAL;
-    }
-    std::vector<int32_t> labels_h;
-    for (int32_t a = 0; a < A; a++)
-        if (used_h[a]) labels_h.push_back(a);
-    p->n_labels = (int64_t)labels_h.size();
-    // the pair engine splits by one label per round and needs no preprocessing
-    p->pre_rounds = p->opts.engine == BISIM_ENGINE_PAIR ? 0 : p->n_labels;
-
-    // a2: sort by (source, label); slots, off, nr
     const uint64_t keyspace = (uint64_t)n * (uint64_t)A;
+
     const bool wide = keyspace > 0xffffffffull;
     const int kbits = ceil_log2_u64(keyspace);
     const size_t ksz = wide ? 8 : 4;
@@ -586,9 +754,7 @@ int plan_build(bisim_plan_s* p, const int32_t* src, const int32_t* act, const in
     BISIM_TRY(scan_exclusive_u32(p->in_ptr.as<uint32_t>(), p->in_ptr.as<uint32_t>(), (int64_t)n + 1,
                                  nullptr, st));
 
-    // a3: incoming transitions grouped by target (counting sort; the order
-    // inside one target's list is whatever the atomics give: marking is
-    // idempotent, so it never matters)
+    // a3: incoming transitions grouped by target
     {
         DevMem cursor;
         BISIM_TRY(cursor.alloc(4 * ((size_t)n + 1), st));
@@ -601,6 +767,137 @@ int plan_build(bisim_plan_s* p, const int32_t* src, const int32_t* act, const in
     }
     tkey.release();
     tval.release();
+
+    return BISIM_OK;
+}
+
+// a2 + a3 from the label sets recorded by k_validate_count (see there).
+static int slots_from_masks(bisim_plan_s* p, const int32_t* src, const int32_t* act, const int32_t* dst,
+                            const uint32_t* amask, int mask_words, int vec) {
+    const int32_t n = p->n;
+    const int64_t m = p->m;
+    cudaStream_t st = p->st;
+    const unsigned gn = grid_for(n, T);
+    uint32_t* off = p->off.as<uint32_t>();
+    if (n) {
+        k_mask_count<<<gn, T, 0, st>>>(amask, n, mask_words, off);
+        BISIM_LAUNCHED();
+        BISIM_CUDA_TRY(cudaGetLastError());
+    }
+    // off = exclusive sum of nr_marks (off[n] = L); in_ptr likewise over in-degrees
+    BISIM_TRY(scan_exclusive_u32(off, off, (int64_t)n + 1, nullptr, st));
+    BISIM_TRY(scan_exclusive_u32(p->in_ptr.as<uint32_t>(), p->in_ptr.as<uint32_t>(), (int64_t)n + 1, nullptr, st));
+    uint32_t L_h = 0;
+    BISIM_CUDA_TRY(cudaMemcpyAsync(&L_h, off + n, 4, cudaMemcpyDeviceToHost, st));
+    BISIM_CUDA_TRY(cudaStreamSynchronize(st));
+    p->L = (int64_t)L_h;
+    BISIM_TRY(p->slot_src.alloc(4 * (size_t)p->L, st));
+    BISIM_TRY(p->slot_act.alloc(4 * (size_t)p->L, st));
+    if (n) {
+        k_mask_slots<<<gn, T, 0, st>>>(amask, off, n, mask_words, p->slot_src.as<int32_t>(),
+                                       p->slot_act.as<int32_t>());
+        BISIM_LAUNCHED();
+        BISIM_CUDA_TRY(cudaGetLastError());
+    }
+    BISIM_TRY(p->in_edge.alloc(8 * (size_t)m, st));
+    if (!m) return BISIM_OK;
+    // a3: bins of 2^bin_bits targets, at most CSR_MAX_BINS of them, whose
+    // counters fit in shared memory (2^15 targets: 128 KB)
+    int bin_bits = 11;
+    while (((int64_t)n + ((int64_t)1 << bin_bits) - 1) >> bin_bits > CSR_MAX_BINS) bin_bits++;
+    if (bin_bits <= 15) {
+        const int nbins = (int)(((int64_t)n + ((int64_t)1 << bin_bits) - 1) >> bin_bits);
+        DevMem bin_cursor, rec_t, rec_v;
+        BISIM_TRY(bin_cursor.alloc(4 * (size_t)nbins, st));
+        BISIM_TRY(rec_t.alloc(4 * (size_t)m, st));
+        BISIM_TRY(rec_v.alloc(8 * (size_t)m, st));
+        k_bin_starts<<<grid_for(nbins, T), T, 0, st>>>(p->in_ptr.as<uint32_t>(), n, bin_bits, nbins,
+                                                       bin_cursor.as<uint32_t>());
+        BISIM_LAUNCHED();
+        const int64_t tile = (int64_t)CSR_A_THREADS * CSR_A_ITEMS;
+        k_csr_bin<<<(unsigned)((m + tile - 1) / tile), CSR_A_THREADS, 0, st>>>(
+            src, act, dst, m, amask, off, mask_words, bin_bits, nbins, bin_cursor.as<uint32_t>(),
+            rec_t.as<uint32_t>(), rec_v.as<unsigned long long>());
+        BISIM_LAUNCHED();
+        BISIM_CUDA_TRY(cudaGetLastError());
+        const size_t smem = sizeof(uint32_t) << bin_bits;
+        BISIM_CUDA_TRY(cudaFuncSetAttribute(k_csr_place, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_csr_place<<<nbins, CSR_B_THREADS, smem, st>>>(p->in_ptr.as<uint32_t>(), n, bin_bits,
+                                                        rec_t.as<uint32_t>(), rec_v.as<unsigned long long>(),
+                                                        p->in_edge.as<unsigned long long>());
+        BISIM_LAUNCHED();
+        BISIM_CUDA_TRY(cudaGetLastError());
+        return BISIM_OK;
+    }
+    // very many states: one returning atomic per transition on a cursor per target
+    DevMem cursor;
+    BISIM_TRY(cursor.alloc(4 * ((size_t)n + 1), st));
+    BISIM_CUDA_TRY(cudaMemcpyAsync(cursor.p, p->in_ptr.p, 4 * ((size_t)n + 1), cudaMemcpyDeviceToDevice, st));
+    k_mask_csr<<<grid_for(m, T), T, 0, st>>>(src, act, dst, m, amask, off, mask_words, vec,
+                                             cursor.as<uint32_t>(), p->in_edge.as<unsigned long long>());
+    BISIM_LAUNCHED();
+    BISIM_CUDA_TRY(cudaGetLastError());
+    return BISIM_OK;
+}
+
+int plan_build(bisim_plan_s* p, const int32_t* src, const int32_t* act, const int32_t* dst,
+               const int32_t* init) {
+    const int32_t n = p->n;
+    const int64_t m = p->m;
+    const int32_t A = p->A;
+    cudaStream_t st = p->st;
+
+    BISIM_TRY(p->ctrl.alloc(sizeof(bisim_ctrl), st));
+    BISIM_CUDA_TRY(cudaMemsetAsync(p->ctrl.p, 0, sizeof(bisim_ctrl), st));
+    int* status = &p->ctrl.as<bisim_ctrl>()->status;
+
+    // a1: validation and the set of labels that occur (with label sets of at
+    // most MASK_WORDS_MAX words, the same pass records every state's label
+    // set and every state's in-degree)
+    DevMem used;
+    BISIM_TRY(used.alloc(sizeof(uint32_t) * (size_t)A, st));
+    BISIM_CUDA_TRY(cudaMemsetAsync(used.p, 0, sizeof(uint32_t) * (size_t)A, st));
+    const int vec = (((uintptr_t)src | (uintptr_t)dst | (uintptr_t)act) & 15u) == 0 ? 1 : 0;
+    const int mask_words = (A + 31) / 32;
+    const bool by_masks = mask_words <= MASK_WORDS_MAX && p->opts.slots == 0;
+    DevMem amask;
+    if (by_masks) {
+        BISIM_TRY(amask.alloc(4 * (size_t)mask_words * n, st));
+        BISIM_TRY(p->off.alloc(4 * ((size_t)n + 1), st));
+        BISIM_TRY(p->in_ptr.alloc(4 * ((size_t)n + 1), st));
+        BISIM_CUDA_TRY(cudaMemsetAsync(amask.p, 0, 4 * (size_t)mask_words * n, st));
+        BISIM_CUDA_TRY(cudaMemsetAsync(p->off.p, 0, 4 * ((size_t)n + 1), st));
+        BISIM_CUDA_TRY(cudaMemsetAsync(p->in_ptr.p, 0, 4 * ((size_t)n + 1), st));
+        k_validate_count<<<grid_for(std::max<int64_t>(m, n), T), T, 0, st>>>(
+            src, act, dst, init, n, m, A, status, used.as<uint32_t>(), vec, mask_words, amask.as<uint32_t>(),
+            p->in_ptr.as<uint32_t>());
+    } else {
+        k_validate<<<grid_for(std::max<int64_t>(m, n), T), T, 0, st>>>(src, act, dst, init, n, m, A,
+                                                                       status, used.as<uint32_t>(), vec);
+    }
+    BISIM_LAUNCHED();
+    BISIM_CUDA_TRY(cudaGetLastError());
+    std::vector<uint32_t> used_h((size_t)A);
+    BISIM_CUDA_TRY(cudaMemcpyAsync(used_h.data(), used.p, sizeof(uint32_t) * (size_t)A,
+                                   cudaMemcpyDeviceToHost, st));
+    BISIM_TRY(read_ctrl(p));
+    if (p->ctrl_h->status & ST_INVALID) {
+        set_last_error("an input array entry is out of range");
+        return BISIM_EINVAL;
+    }
+    std::vector<int32_t> labels_h;
+    for (int32_t a = 0; a < A; a++)
+        if (used_h[a]) labels_h.push_back(a);
+    p->n_labels = (int64_t)labels_h.size();
+    // the pair engine splits by one label per round and needs no preprocessing
+    p->pre_rounds = p->opts.engine == BISIM_ENGINE_PAIR ? 0 : p->n_labels;
+
+    if (by_masks) {
+        BISIM_TRY(slots_from_masks(p, src, act, dst, amask.as<uint32_t>(), mask_words, vec));
+    } else {
+        BISIM_TRY(slots_by_sort(p, src, act, dst, vec));
+    }
+    const int64_t L = p->L;
 
     if (!labels_h.empty()) {
         BISIM_TRY(p->labels.alloc(4 * labels_h.size(), st));
@@ -657,10 +954,11 @@ int plan_build(bisim_plan_s* p, const int32_t* src, const int32_t* act, const in
         a.nl64 = p->nl64.as<unsigned long long>();
         a.split = p->split.as<uint8_t>();
         a.stamp0 = base;
-        DevMem amask;
         a.amask = nullptr;
         a.mask_words = (A + 31) / 32;
-        if (a.mask_words <= 4) {  // up to 128 labels: 16 B or less per state
+        if (by_masks) {
+            a.amask = amask.as<uint32_t>();  // recorded by the validation pass
+        } else if (a.mask_words <= MASK_WORDS_MAX) {  // up to 128 labels: 16 B or less per state
             BISIM_TRY(amask.alloc(4 * (size_t)a.mask_words * n, st));
             BISIM_CUDA_TRY(cudaMemsetAsync(amask.p, 0, 4 * (size_t)a.mask_words * n, st));
             k_label_masks<<<grid_for(L, T), T, 0, st>>>(a.slot_src, a.slot_act, L, a.mask_words,

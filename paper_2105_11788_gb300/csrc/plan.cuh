@@ -40,7 +40,7 @@ struct bisim_ctrl {
     // hybrid engine, a published round with several splitters: its splitters of
     // one state, taken by position from the ring of size bucket 0
     int cmd_K0;                          // how many
-    int pad5;
+    int cmd_peel;                        // 1: the published round is a peel round
     unsigned long long cmd_h0;           // ring-0 head before them
 };
 

@@ -23,6 +23,55 @@ int retain_pool_memory() {
     return BISIM_OK;
 }
 
+}  // namespace bisim
+
+extern "C" {
+
+int bisim_pool_usage(uint64_t* used, uint64_t* used_high, uint64_t* reserved) {
+    int dev = 0;
+    BISIM_CUDA_TRY(cudaGetDevice(&dev));
+    cudaMemPool_t pool;
+    BISIM_CUDA_TRY(cudaDeviceGetDefaultMemPool(&pool, dev));
+    uint64_t v = 0;
+    if (used) {
+        BISIM_CUDA_TRY(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &v));
+        *used = v;
+    }
+    if (used_high) {
+        BISIM_CUDA_TRY(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &v));
+        *used_high = v;
+    }
+    if (reserved) {
+        BISIM_CUDA_TRY(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &v));
+        *reserved = v;
+    }
+    return BISIM_OK;
+}
+
+int bisim_pool_reset_high(void) {
+    int dev = 0;
+    BISIM_CUDA_TRY(cudaGetDevice(&dev));
+    cudaMemPool_t pool;
+    BISIM_CUDA_TRY(cudaDeviceGetDefaultMemPool(&pool, dev));
+    uint64_t zero = 0;
+    BISIM_CUDA_TRY(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &zero));
+    return BISIM_OK;
+}
+
+int bisim_pool_trim(uint64_t keep_bytes) {
+    int dev = 0;
+    BISIM_CUDA_TRY(cudaGetDevice(&dev));
+    cudaMemPool_t pool;
+    BISIM_CUDA_TRY(cudaDeviceGetDefaultMemPool(&pool, dev));
+    BISIM_CUDA_TRY(cudaDeviceSynchronize());
+    BISIM_CUDA_TRY(cudaMemPoolTrimTo(pool, (size_t)keep_bytes));
+    return BISIM_OK;
+}
+
+}  // extern "C"
+
+namespace bisim {
+
 namespace {
 
 constexpr int SCAN_THREADS = 256;

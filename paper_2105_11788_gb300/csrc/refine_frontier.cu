@@ -315,6 +315,7 @@ struct CtaShared {
     int hp[BISIM_BUCKETS];  // select_many: ring position of each bucket's head
     unsigned long long head[BISIM_BUCKETS];  // this CTA's copy of the worklist heads
     int k0;                 // select_peel: labels taken from size bucket 0
+    int n1;                 // select_peel: listed labels whose block has one state
     unsigned long long h0;  // select_peel: ring-0 head before them
 };
 
@@ -1334,10 +1335,12 @@ __device__ __forceinline__ void claim_peel(const FrontierArgs& a, int32_t b, uns
 // bucket) while their blocks hold at most budget1 states together, listed in
 // selC with the exclusive prefix of their sizes in selP. Returns the number
 // of the higher-bucket labels to every thread.
+constexpr int PEEL_SEL_E = 16;  // listed labels per thread of a peel selection at most
+
 __device__ int select_peel(const FrontierArgs& a, const Worklist& wl, unsigned long long* head, CtaShared& sh,
                            int32_t* selC, int32_t* selP, int kmax1, int32_t budget1, int cap0) {
     const unsigned lane = threadIdx.x & 31u;
-    kmax1 = min(kmax1, SEL_E * (int)blockDim.x);
+    kmax1 = min(kmax1, PEEL_SEL_E * (int)blockDim.x);
     if (threadIdx.x < 32) {
         const unsigned long long h = head[lane];
         const unsigned long long t = *(volatile const unsigned long long*)&wl.tail[lane];
@@ -1361,10 +1364,10 @@ __device__ int select_peel(const FrontierArgs& a, const Worklist& wl, unsigned l
     const int k1 = sh.total;
     const int K0 = sh.k0;
     {
-        int32_t lv[SEL_E];
+        int32_t lv[PEEL_SEL_E];
         int bk = 1;
 #pragma unroll
-        for (int e = 0; e < SEL_E; e++) {
+        for (int e = 0; e < PEEL_SEL_E; e++) {
             const int j = e * (int)blockDim.x + (int)threadIdx.x;
             lv[e] = -1;
             if (j < k1) {
@@ -1375,7 +1378,7 @@ __device__ int select_peel(const FrontierArgs& a, const Worklist& wl, unsigned l
             }
         }
 #pragma unroll
-        for (int e = 0; e < SEL_E; e++) {
+        for (int e = 0; e < PEEL_SEL_E; e++) {
             const int j = e * (int)blockDim.x + (int)threadIdx.x;
             if (j < k1) selC[j] = lv[e];
         }
@@ -1384,32 +1387,47 @@ __device__ int select_peel(const FrontierArgs& a, const Worklist& wl, unsigned l
     __syncthreads();
     const int E = (k1 + (int)blockDim.x - 1) / (int)blockDim.x;
     const int j0 = (int)threadIdx.x * E;
-    int32_t cs[SEL_E];
-    int sz[SEL_E];
-    int mine = 0;
+    int32_t cs[PEEL_SEL_E];
+    int sz[PEEL_SEL_E];
+    int mine = 0, mine_w = 0;  // states, and states of blocks of several states
 #pragma unroll
-    for (int e = 0; e < SEL_E; e++) {
+    for (int e = 0; e < PEEL_SEL_E; e++) {
         const int j = j0 + e;
         cs[e] = e < E && j < k1 ? selC[j] : -1;
         sz[e] = cs[e] < 0 ? 0 : ld(&a.bend[cs[e]]) - ld(&a.bbeg[cs[e]]);
         mine += sz[e];
+        mine_w += sz[e] > 1 ? sz[e] : 0;
     }
     int tot;
     int ex = cta_scan(mine, sh, tot);
+    // the budget counts the splitters of several states only (a label pushed
+    // with a larger block whose block now has one state costs as little as a
+    // label of bucket 0); the costs are non-negative, so the taken entries
+    // are again a prefix
+    int exw = cta_scan(mine_w, sh, tot);
     int taken = 0;
 #pragma unroll
-    for (int e = 0; e < SEL_E; e++) {
+    for (int e = 0; e < PEEL_SEL_E; e++) {
         const int j = j0 + e;
+        const int w = sz[e] > 1 ? sz[e] : 0;
         // the first is taken when nothing else is, so a round is never empty
-        if (cs[e] >= 0 && ((j == 0 && K0 == 0) || ex + sz[e] <= budget1)) {
+        if (cs[e] >= 0 && ((j == 0 && K0 == 0) || exw + w <= budget1)) {
             selP[j] = ex;
             selP[j + 1] = ex + sz[e];
             taken++;
         }
         ex += sz[e];
+        exw += w;
     }
     int K1;
     cta_scan(taken, sh, K1);
+    // listed labels whose block now has one state (they may peel)
+    int ones = 0;
+#pragma unroll
+    for (int e = 0; e < PEEL_SEL_E; e++) ones += (cs[e] >= 0 && j0 + e < K1 && sz[e] == 1) ? 1 : 0;
+    int n1;
+    cta_scan(ones, sh, n1);
+    if (threadIdx.x == 0) sh.n1 = n1;
     if (threadIdx.x < 32) {
         if (lane == 0)
             head[0] += (unsigned long long)K0;
@@ -1622,6 +1640,188 @@ __device__ void peel_items(const FrontierArgs& a, const Worklist& wl, unsigned l
     }
 }
 
+// What a warp's claim pass keeps in registers for its mark pass when its
+// share of the round is one group of at most 32 items in at most
+// PEEL_CHUNKS chunks with no item of more than 32 transitions: per lane its
+// item, and per chunk the lane's transition, its source's block and flags
+// (the lane of the transition's item, whether the block has several states,
+// whether the touch is exclusive).
+struct PeelCarry {
+    int32_t C, deg;
+    bool first, pending;  // pending: the item is decided in the mark pass
+    int my_chunk, my_start;
+    unsigned long long e[PEEL_CHUNKS];
+    int32_t b[PEEL_CHUNKS];
+    int fl[PEEL_CHUNKS];  // item lane | 32 (block of several states) | 64 (exclusive touch)
+};
+
+// Claim pass of a warp's items [g0, g1) (g1 - g0 <= 32). Returns true (to
+// every lane) when everything the mark pass needs is in `cy`; then the items
+// of one state that touched no block of several states are carried out here
+// already (they claim nothing, so they cannot lose, and they mark nothing).
+// Otherwise the claims are made by peel_items<0> and the mark pass must
+// recompute.
+__device__ bool peel_claim(const FrontierArgs& a, const Worklist& wl, unsigned long long h0, int K0,
+                           const int32_t* selC, const int32_t* selP, int K1, int64_t g0, int64_t g1, uint32_t stamp,
+                           PeelCarry& cy, long long& edges, long long& commits) {
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned FULL = 0xffffffffu;
+    const int ng = (int)(g1 - g0);
+    PeelItem it;
+    it.C = -1;
+    it.deg = 0;
+    it.single = true;
+    it.first = false;
+    it.t = 0;
+    it.d0 = 0;
+    if ((int)lane < ng) it = peel_item(a, wl, h0, K0, selC, selP, K1, g0 + lane);
+    const bool packable = (int)lane < ng && it.deg > 0 && it.deg <= 32;
+    int cur = 0, chunk = 0;
+    cy.my_chunk = -1;
+    cy.my_start = 0;
+    {
+        const int dp = packable ? it.deg : 0;
+        for (int i = 0; i < ng; i++) {
+            const int d = __shfl_sync(FULL, dp, i);
+            if (d == 0) continue;
+            if (cur + d > 32) {
+                chunk++;
+                cur = 0;
+            }
+            if ((int)lane == i) {
+                cy.my_chunk = chunk;
+                cy.my_start = cur;
+            }
+            cur += d;
+        }
+    }
+    const int nchunks = cur > 0 ? chunk + 1 : chunk;
+    const bool fits = nchunks <= PEEL_CHUNKS && __ballot_sync(FULL, (int)lane < ng && it.deg > 32) == 0u;
+    if (!fits) {
+        peel_items<0>(a, wl, h0, K0, selC, selP, K1, g0, g1, stamp, nullptr, nullptr, nullptr, nullptr, edges,
+                      commits);
+        return false;
+    }
+    cy.C = it.C;
+    cy.deg = it.deg;
+    cy.first = it.first;
+    bool val[PEEL_CHUNKS];
+    int bb[PEEL_CHUNKS], be[PEEL_CHUNKS];
+#pragma unroll
+    for (int u = 0; u < PEEL_CHUNKS; u++) {
+        const unsigned mc = __ballot_sync(FULL, cy.my_chunk == u);
+        const unsigned starts = __reduce_or_sync(FULL, cy.my_chunk == u ? (1u << cy.my_start) : 0u);
+        const int r = __popc(starts & (0xffffffffu >> (31 - lane))) - 1;
+        const int il = (mc != 0u && r >= 0) ? (int)__fns(mc, 0, r + 1) : 0;
+        const int st = __shfl_sync(FULL, cy.my_start, il);
+        const int dg = __shfl_sync(FULL, it.deg, il);
+        const int d0 = __shfl_sync(FULL, it.d0, il);
+        val[u] = u < nchunks && mc != 0u && r >= 0 && (int)lane < st + dg;
+        cy.fl[u] = il;
+        cy.e[u] = val[u] ? a.in_edge[d0 + (int)lane - st] : 0ull;
+    }
+#pragma unroll
+    for (int u = 0; u < PEEL_CHUNKS; u++) cy.b[u] = val[u] ? ld(&a.block[(int32_t)(cy.e[u] >> 32)]) : 0;
+#pragma unroll
+    for (int u = 0; u < PEEL_CHUNKS; u++) {
+        bb[u] = val[u] ? ld(&a.bbeg[cy.b[u]]) : 0;
+        be[u] = val[u] ? ld(&a.bend[cy.b[u]]) : 0;
+    }
+    bool touched = false;  // item lane: one of its transitions comes from a block of several states
+#pragma unroll
+    for (int u = 0; u < PEEL_CHUNKS; u++) {
+        const int il = cy.fl[u];
+        const int32_t s = (int32_t)(cy.e[u] >> 32);
+        const int32_t b = cy.b[u];
+        const bool ns = val[u] && be[u] - bb[u] > 1;
+        const int32_t C = __shfl_sync(FULL, it.C, il);
+        const bool single = __shfl_sync(FULL, it.single, il);
+        const unsigned long long vb = ns ? ((unsigned long long)il << 32) | (uint32_t)b : ~0ull - lane;
+        const unsigned mb = __match_any_sync(FULL, vb);
+        const unsigned long long vbs = ns ? ((unsigned long long)(uint32_t)b << 32) | (uint32_t)s : ~0ull - lane;
+        const unsigned mbs = __match_any_sync(FULL, vbs) & mb;
+        const bool lead = (__ballot_sync(FULL, ns && s == b) & mb) != 0u;
+        const bool x = !single || mbs != mb || lead;
+        cy.fl[u] = il | (ns ? 32 : 0) | (x ? 64 : 0);
+        if (ns && (mb & lanemask_lt()) == 0u) claim_peel(a, b, peel_key(stamp, C, x), x, stamp);
+        const unsigned nsm = __ballot_sync(FULL, ns);
+        if (cy.my_chunk == u) {
+            const unsigned mine = (it.deg >= 32 ? 0xffffffffu : ((1u << it.deg) - 1u)) << cy.my_start;
+            touched = (nsm & mine) != 0u;
+        }
+    }
+    cy.pending = false;
+    if ((int)lane < ng) {
+        if (it.first && !it.single) claim_peel(a, it.C, peel_key(stamp, it.C, true), true, stamp);
+        if (it.single && !touched) {
+            // nothing to claim, nothing to mark: this iteration is carried out now
+            a.unstable[it.C] = 0u;
+            commits++;
+            edges += it.deg;
+            TRACE_WIN();
+        } else {
+            cy.pending = true;
+        }
+    }
+    return true;
+}
+
+// Mark pass from the claim pass's registers (the block ranges are read again
+// for the few transitions from blocks of several states).
+__device__ void peel_mark_carried(const FrontierArgs& a, const Worklist& wl, uint32_t stamp, const PeelCarry& cy,
+                                  int* n_small, int* n_mid, int4* small_list, int4* mid_list, long long& edges,
+                                  long long& commits) {
+    const unsigned FULL = 0xffffffffu;
+    if (__ballot_sync(FULL, cy.pending) == 0u) return;
+    const bool lost_x = cy.pending && ld_volatile_u32(&a.lostl[cy.C]) == stamp;
+    bool lost_p = false;
+#pragma unroll
+    for (int u = 0; u < PEEL_CHUNKS; u++) {
+        const int il = cy.fl[u] & 31;
+        const bool pend = __shfl_sync(FULL, cy.pending, il);
+        const bool ns = pend && (cy.fl[u] & 32);
+        const bool x = cy.fl[u] & 64;
+        const int32_t b = cy.b[u];
+        const bool lp = ns && !x && ld_volatile_u64(&a.minx[b]) == ld_volatile_u64(&a.claim[b]);
+        const unsigned lpm = __ballot_sync(FULL, lp);
+        const int st = __shfl_sync(FULL, cy.my_start, il);
+        const int dg = __shfl_sync(FULL, cy.deg, il);
+        const int32_t C = __shfl_sync(FULL, cy.C, il);
+        const unsigned range = (dg >= 32 ? 0xffffffffu : ((1u << dg) - 1u)) << st;
+        const bool lose = __shfl_sync(FULL, lost_x, il) || (lpm & range) != 0u;
+        if (cy.my_chunk == u) {
+            const unsigned mine = (cy.deg >= 32 ? 0xffffffffu : ((1u << cy.deg) - 1u)) << cy.my_start;
+            lost_p = (lpm & mine) != 0u;
+        }
+        if (ns && !lose) {
+            const int32_t s = (int32_t)(cy.e[u] >> 32);
+            const int32_t bb = ld(&a.bbeg[b]), be = ld(&a.bend[b]);
+            if (x) {
+                a.mark[(uint32_t)cy.e[u]] = stamp;
+                if (atomicExch(&a.smark[s], stamp) != stamp)
+                    rank_marked(a, s, b, bb, be, C, n_small, n_mid, small_list, mid_list, 0);
+            } else {
+                const unsigned long long pk = ((unsigned long long)(~stamp) << 32) | (uint32_t)C;
+                const unsigned long long old = atomicMin(&a.smark64[s], pk);
+                if ((old >> 32) != (pk >> 32)) rank_marked(a, s, b, bb, be, C, n_small, n_mid, small_list, mid_list, 1);
+            }
+        }
+    }
+    if (cy.pending) {
+        const bool lose = lost_x || lost_p;
+        if (cy.first) {
+            if (lose) {
+                push(a, wl, cy.C);
+            } else {
+                a.unstable[cy.C] = 0u;
+                commits++;
+                TRACE_WIN();
+            }
+        }
+        if (!lose) edges += cy.deg;
+    }
+}
+
 // A peel round on the whole grid: claim pass, barrier, mark pass, barrier,
 // split step, barrier. The items (members of the round's splitters: K0 of
 // one state from the ring of bucket 0, then the members of the K1 listed
@@ -1636,15 +1836,30 @@ __device__ __forceinline__ bool peel_round(const FrontierArgs& a, const Worklist
     const int64_t I = (int64_t)K0 + selP[K1];
     const int64_t per = (I + nwarps - 1) / nwarps;
     const int64_t i0 = gw * per, i1 = min(I, i0 + per);
-    for (int64_t g = i0; g < i1; g += 32)
-        peel_items<0>(a, wl, h0, K0, selC, selP, K1, g, min(i1, g + 32), stamp, n_small, n_mid, small_list,
-                      mid_list, edges, commits);
-    PHASE(2);
-    if (!sync()) return false;
-    PHASE(3);
-    for (int64_t g = i0; g < i1; g += 32)
-        peel_items<1>(a, wl, h0, K0, selC, selP, K1, g, min(i1, g + 32), stamp, n_small, n_mid, small_list,
-                      mid_list, edges, commits);
+    if (per <= 32) {
+        // one group per warp: the claim pass's loads stay in registers
+        PeelCarry cy;
+        const bool carried =
+            i0 < i1 && peel_claim(a, wl, h0, K0, selC, selP, K1, i0, i1, stamp, cy, edges, commits);
+        PHASE(2);
+        if (!sync()) return false;
+        PHASE(3);
+        if (carried)
+            peel_mark_carried(a, wl, stamp, cy, n_small, n_mid, small_list, mid_list, edges, commits);
+        else if (i0 < i1)
+            peel_items<1>(a, wl, h0, K0, selC, selP, K1, i0, i1, stamp, n_small, n_mid, small_list, mid_list,
+                          edges, commits);
+    } else {
+        for (int64_t g = i0; g < i1; g += 32)
+            peel_items<0>(a, wl, h0, K0, selC, selP, K1, g, min(i1, g + 32), stamp, n_small, n_mid, small_list,
+                          mid_list, edges, commits);
+        PHASE(2);
+        if (!sync()) return false;
+        PHASE(3);
+        for (int64_t g = i0; g < i1; g += 32)
+            peel_items<1>(a, wl, h0, K0, selC, selP, K1, g, min(i1, g + 32), stamp, n_small, n_mid, small_list,
+                          mid_list, edges, commits);
+    }
     PHASE(4);
     if (!sync()) return false;
     PHASE(5);
@@ -1678,6 +1893,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_frontier_hybrid(FrontierArgs a, Hyb
     __shared__ int s_defer[32];
     __shared__ int s_ndefer;
     __shared__ int s_ns, s_nm, s_heavy, s_cmd, s_K, s_K0;
+    __shared__ bool s_peel;
     __shared__ unsigned long long s_h0;
     __shared__ unsigned s_stamp;
     __shared__ uint32_t s_lost[32];  // rounds on CTA 0 alone take at most 32 splitters
@@ -1704,10 +1920,11 @@ __global__ void __launch_bounds__(MAXT, 1) k_frontier_hybrid(FrontierArgs a, Hyb
     };
     // a grid round: K > 1 splitters in selC / selP (peel rounds: K listed ones
     // and K0 of one state from ring 0 after h0), or the single splitter C
-    auto grid_round = [&](int K, int K0, unsigned long long h0, int32_t C, uint32_t stamp, int par) -> bool {
+    auto grid_round = [&](int K, int K0, unsigned long long h0, int32_t C, uint32_t stamp, int par,
+                          bool peel_now) -> bool {
         int* ns = &c->n_touched[par];
         int* nm = &c->n_mid[par];
-        if (h.peel && K + K0 > 1)
+        if (peel_now && K + K0 > 1)
             return peel_round(a, wl, sh, s_defer, &s_ndefer, s_selC, s_selP, K, K0, h0, stamp, gw, nwarps, ns, nm,
                               a.tlist, a.tlist + n, (int)blockIdx.x, (int)gridDim.x, edges, states, commits, gsync);
         if (K > 1)
@@ -1760,6 +1977,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_frontier_hybrid(FrontierArgs a, Hyb
                 s_K = ldcg(&c->cmd_K);
                 s_K0 = ldcg(&c->cmd_K0);
                 s_h0 = ldcg(&c->cmd_h0);
+                s_peel = ldcg(&c->cmd_peel) != 0;
             }
             __syncthreads();
             const int32_t C = s_cmd;
@@ -1769,25 +1987,14 @@ __global__ void __launch_bounds__(MAXT, 1) k_frontier_hybrid(FrontierArgs a, Hyb
             const unsigned long long h0c = s_h0;
             if (C == -1) break;
             if (threadIdx.x < BISIM_BUCKETS) sh.head[threadIdx.x] = ldcg(&c->cmd_heads[threadIdx.x]);
-            if (C == MULTI) {
-                // K <= SEL_E * blockDim: every load is issued before the first store
-                int32_t vc[SEL_E], vp[SEL_E + 1];
-#pragma unroll
-                for (int e = 0; e <= SEL_E; e++) {
-                    const int i = e * (int)blockDim.x + (int)threadIdx.x;
-                    if (e < SEL_E) vc[e] = i < K ? ldcg(&h.g_selC[i]) : 0;
-                    vp[e] = i <= K ? ldcg(&h.g_selP[i]) : 0;
+            if (C == MULTI)
+                for (int i = threadIdx.x; i <= K; i += blockDim.x) {
+                    if (i < K) s_selC[i] = ldcg(&h.g_selC[i]);
+                    s_selP[i] = ldcg(&h.g_selP[i]);
                 }
-#pragma unroll
-                for (int e = 0; e <= SEL_E; e++) {
-                    const int i = e * (int)blockDim.x + (int)threadIdx.x;
-                    if (e < SEL_E && i < K) s_selC[i] = vc[e];
-                    if (i <= K) s_selP[i] = vp[e];
-                }
-            }
             __syncthreads();
             r = (int64_t)(stamp - a.stamp0);
-            if (!grid_round(C == MULTI ? K : 1, C == MULTI ? K0c : 0, h0c, C, stamp, (int)(r & 1))) return;
+            if (!grid_round(C == MULTI ? K : 1, C == MULTI ? K0c : 0, h0c, C, stamp, (int)(r & 1), s_peel)) return;
             in_step = true;
             continue;
         }
@@ -1796,6 +2003,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_frontier_hybrid(FrontierArgs a, Hyb
         const uint32_t stamp = a.stamp0 + (uint32_t)r;
         const int par = (int)(r & 1);
         int K;       // splitters of the round
+        bool peel_now = false;  // a peel round (else a multi_round with these listed splitters)
         int K1 = 0;  // of those, listed in s_selC / s_selP (the rest: ring 0 after h0, peel rounds)
         int K0 = 0;
         unsigned long long h0 = 0;
@@ -1806,6 +2014,9 @@ __global__ void __launch_bounds__(MAXT, 1) k_frontier_hybrid(FrontierArgs a, Hyb
             h0 = sh.h0;
             K = K0 + K1;
             C = K0 > 0 ? ld(&wl.queue[wl.base + h0 % (unsigned long long)wl.cap]) : K1 > 0 ? s_selC[0] : -1;
+            // without a splitter of one state nothing can peel: the claim
+            // rule of multi_round (one splitter per touched block) is cheaper
+            peel_now = K0 > 0 || sh.n1 > 0;
         } else if (kmax > 1) {
             K = select_many(a, wl, sh.head, sh, s_selC, s_selP, kmax, h.budget);
             K1 = K;
@@ -1913,6 +2124,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_frontier_hybrid(FrontierArgs a, Hyb
                 c->cmd_K = K > 1 ? K1 : K;
                 c->cmd_K0 = K > 1 ? K0 : 0;
                 c->cmd_h0 = h0;
+                c->cmd_peel = peel_now ? 1 : 0;
                 c->cmd_stamp = stamp;
                 __threadfence();
                 atomicAdd(&c->cmd_seq, 1ull);
@@ -1924,7 +2136,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_frontier_hybrid(FrontierArgs a, Hyb
             PHASE_ADD(12, (unsigned long long)K);
             PHASE_ADD(13, (unsigned long long)(K0 + s_selP[K1]));
         }
-        if (!grid_round(K > 1 ? K1 : 1, K > 1 ? K0 : 0, h0, C, stamp, par)) return;
+        if (!grid_round(K > 1 ? K1 : 1, K > 1 ? K0 : 0, h0, C, stamp, par, peel_now)) return;
         if (K == 1) PHASE(8);
         TRACE_END(r, 0u);
     }
@@ -2358,7 +2570,7 @@ int refine_frontier(bisim_plan_s* p, bisim_stats* stats) {
         HybridArgs h;
         h.light_edges = light;
         h.kmax = p->opts.splitters > 0 ? std::min(p->opts.splitters, BISIM_KMAX_GRID) : BISIM_KMAX_GRID;
-        h.kmax = std::min(h.kmax, SEL_E * threads);
+        h.kmax = std::min(h.kmax, (p->opts.peel >= 0 ? PEEL_SEL_E : SEL_E) * threads);
         h.local_budget = std::min(threads / 32, 32);
         h.g_selC = p->msel.as<int32_t>();
         h.g_selP = h.g_selC + BISIM_KMAX_GRID;

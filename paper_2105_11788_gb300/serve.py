@@ -34,11 +34,30 @@ from typing import Callable, List, Optional, Sequence
 import numpy as np
 
 
-def footprint_bytes(n: int, m: int) -> int:
-    """Device bytes one LTS needs during a batched reduction: inputs, plan
-    arrays and sort temporaries (about 80 B per transition) and refinement
-    state with the bucketed worklist (about 256 B per state)."""
-    return 80 * int(m) + 256 * int(n) + (1 << 20)
+def footprint_bytes(n: int, m: int, num_act: int = 1) -> int:
+    """Device bytes one LTS needs at most during a batched reduction, from the
+    sizes of what the path allocates per transition and per state:
+      transitions: the inputs on the device (src, act, dst: 12 B), their copy
+        in the batch's union (12 B), the incoming-transition index (8 B) and
+        per mark slot (at most one per transition) its owner, label and mark
+        (12 B): 44 B; with more than 128 labels the sort by (source, label)
+        adds 32 B of temporaries;
+      states: initial labels and output (8 B), their union copy (4 B), the
+        plan's per-state arrays (29 B), the frontier state with the 32 worklist
+        rings (228 B), the label sets and the set-up and output temporaries
+        (at most 40 B): 309 B;
+    plus 1 MiB for the small per-batch arrays."""
+    per_t = 44 + (32 if num_act > 128 else 0)
+    return per_t * int(m) + 309 * int(n) + (1 << 20)
+
+
+def gpu_trim(keep_bytes: int = 0) -> None:
+    """Give the memory that finished plans left in the device's memory pool
+    back to the device (the library keeps freed plan memory for reuse while a
+    process serves, so that later plans need no new mappings)."""
+    from . import bisim
+
+    bisim.bisim_pool_trim(keep_bytes)
 
 
 @dataclasses.dataclass
@@ -101,9 +120,9 @@ def gpu_single_executor(opts=None, device: str = "cuda"):
 class BatchServer:
     def __init__(self, executor: Callable[[Sequence], List[np.ndarray]], mem_budget: int,
                  workers: int = 2, max_batch: int = 1024,
-                 footprint: Callable[[object], int] = lambda l: footprint_bytes(l.n, l.m),
+                 footprint: Callable[[object], int] = lambda l: footprint_bytes(l.n, l.m, l.num_act),
                  big_executor: Optional[Callable[[object], np.ndarray]] = None, big_states: int = 0,
-                 big_backlog: int = 2):
+                 big_backlog: int = 2, on_idle: Optional[Callable[[], None]] = None):
         self.executor = executor
         self.big_executor = big_executor
         self.big_states = int(big_states)
@@ -113,6 +132,7 @@ class BatchServer:
         self.workers = int(workers)
         self.max_batch = int(max_batch)
         self.footprint = footprint
+        self.on_idle = on_idle  # called when serve() has drained every request (e.g. gpu_trim)
         self.max_inflight_bytes = 0
         self.batches = 0
         self.max_concurrent = 0
@@ -190,6 +210,8 @@ class BatchServer:
                 elif timeout > 0:
                     time.sleep(timeout)
         results.sort(key=lambda r: r.rid)
+        if self.on_idle is not None:
+            self.on_idle()
         return results
 
 

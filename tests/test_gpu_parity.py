@@ -431,3 +431,53 @@ def test_vector_and_unaligned_input_paths():
     with bisim.Plan(lts.n, lts.num_act, src, act, dst, torch.from_numpy(lts.init).cuda()) as p:
         got, _ = p.refine()
     assert got.cpu().numpy().tolist() == oracle.ks_lts(lts).tolist()
+
+
+def _plan_arrays(lts, **kw):
+    import torch
+
+    d = lambda a: None if a is None else torch.from_numpy(a).cuda()  # noqa: E731
+    with bisim.Plan(lts.n, lts.num_act, d(lts.src), d(lts.act), d(lts.dst), d(lts.init),
+                    bisim.make_opts(**kw)) as p:
+        return bisim.bisim_plan_arrays(p.handle, lts.n, lts.m)
+
+
+@pytest.mark.parametrize("slots", [0, 1], ids=["label-sets", "sort"])
+def test_plan_arrays_equal_algorithm4(slots):
+    """The plan's mark-slot layout and incoming-transition index against the
+    oracle's Algorithm 4 (sort by (source, label), order, nr_marks, off as
+    start offsets): off, the owner and label of every slot, in_ptr, and per
+    target the multiset of (source, slot) entries. Both routes (label sets;
+    the sort) give the same arrays."""
+    g = _golden("fig3_preprocessing.json")
+    cases = [_lts_from_golden(g)]
+    cases += [lts_gen.random_small(900 + s, 40, a, 200, blocks=2) for s, a in enumerate((1, 3, 32, 33, 70, 128))]
+    cases += [lts_gen.random_small(950, 30, 200, 150), lts_gen.fan_out(50),
+              lts_gen.quotient_expansion(seed=6, classes=300, trans=3000, copies_hi=20),
+              lts_gen.powerlaw(seed=3, n=20000)]
+    for lts in cases:
+        got = _plan_arrays(lts, slots=slots)
+        ref = oracle.plan(lts.n, lts.num_act, lts.src, lts.act, lts.dst)
+        off = ref["off"].astype(np.int64)
+        L = ref["mark_length"]
+        assert got["mark_length"] == L, lts.name
+        assert got["off"][:lts.n].tolist() == off.tolist() and got["off"][lts.n] == L, lts.name
+        s_sorted = lts.src[ref["perm"]].astype(np.int64)
+        a_sorted = lts.act[ref["perm"]].astype(np.int64)
+        slot_sorted = off[s_sorted] + ref["order"]
+        want_src = np.zeros(L, np.int64)
+        want_act = np.zeros(L, np.int64)
+        want_src[slot_sorted] = s_sorted
+        want_act[slot_sorted] = a_sorted
+        assert got["slot_src"].tolist() == want_src.tolist(), lts.name
+        assert got["slot_act"].tolist() == want_act.tolist(), lts.name
+        indeg = np.bincount(lts.dst, minlength=lts.n)
+        assert got["in_ptr"].tolist() == np.concatenate([[0], np.cumsum(indeg)]).tolist(), lts.name
+        # per target, the multiset of (source << 32 | slot)
+        d_sorted = lts.dst[ref["perm"]].astype(np.int64)
+        want = np.sort((d_sorted << 40) | (s_sorted << 20) | slot_sorted) if lts.n < (1 << 20) else None
+        ie = got["in_edge"]
+        tgt = np.repeat(np.arange(lts.n, dtype=np.int64), indeg)
+        have = np.sort((tgt << 40) | ((ie >> 32) << 20) | (ie & 0xffffffff))
+        if want is not None:
+            assert have.tolist() == want.tolist(), lts.name

@@ -42,3 +42,30 @@ def test_large_request_lane_overlaps_the_batches():
     for r, a in zip(res, alone):
         assert np.array_equal(r.labels, a)
     assert srv.big_served == sum(1 for l in ltss if l.n >= thr) > 0
+
+
+def test_footprint_covers_what_the_library_allocates():
+    """Admission counts footprint_bytes per request. The library's own
+    allocations (the device pool's high-water mark over a batched and a
+    single-LTS reduction; the inputs on the device come from torch's
+    allocator and footprint_bytes counts them too) stay within it, and not
+    far below it; trimming gives the pool's unused memory back."""
+    rng = np.random.default_rng(23)
+    ltss = [lts_gen.stream_instance(rng, n_lo=1000, n_hi=100000, idx=i) for i in range(48)]
+    cases = [("batch", ltss, lambda: bisim.reduce_batch(ltss)),
+             ("single", [ltss[0]], lambda: bisim.reduce(ltss[0]))]
+    for name, group, run in cases:
+        import torch
+
+        torch.cuda.synchronize()
+        before = bisim.bisim_pool_usage()["used"]
+        bisim.bisim_pool_reset_high()
+        run()
+        torch.cuda.synchronize()
+        peak = bisim.bisim_pool_usage()["used_high"] - before
+        budget = sum(serve.footprint_bytes(l.n, l.m, l.num_act) for l in group)
+        assert 0 < peak <= budget, (name, peak, budget)
+        assert peak >= budget // 4, (name, peak, budget)
+    serve.gpu_trim()
+    u = bisim.bisim_pool_usage()
+    assert u["reserved"] - u["used"] <= 64 << 20
