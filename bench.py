@@ -606,6 +606,8 @@ def main():
         kname, schedule = "k_dense_main", "dense rounds on the whole grid"
     elif st.engine == bisim.ENGINE_PAIR:
         kname, schedule = "k_pair_main", "pair rounds on the whole grid"
+    elif st.engine == bisim.ENGINE_SMALL:
+        kname, schedule = "k_small", "one CTA in shared memory (the whole reduction in one launch)"
     elif st.grid_ctas == 1:
         kname, schedule = "k_frontier_batch", "one CTA (sparse LTS)"
     elif st.local_steps > 0:
@@ -626,7 +628,7 @@ def main():
     # the rounds' other bound: barriers and dependent loads. Measured grid
     # barrier cost at this launch's grid size, beside the time per round
     latency = None
-    if st.engine != bisim.ENGINE_DENSE and st.steps > 0:
+    if st.engine not in (bisim.ENGINE_DENSE, bisim.ENGINE_SMALL) and st.steps > 0:
         bar_ns = None
         try:
             ctas = max(1, st.grid_ctas)

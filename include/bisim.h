@@ -63,6 +63,9 @@ extern "C" {
  * is 0) and up to |Act| times as many rounds; a second, independent engine
  * for cross-checks. Single LTSs only (bisim_batch_plan rejects it). */
 #define BISIM_ENGINE_PAIR 3
+/* Reported in bisim_stats.engine only (not an option): a small LTS reduced by
+ * one CTA in shared memory with the frontier engine's rounds (opts.small). */
+#define BISIM_ENGINE_SMALL 4
 
 typedef struct bisim_opts {
     int32_t engine;      /* BISIM_ENGINE_* (0 = auto) */
@@ -126,6 +129,13 @@ typedef struct bisim_opts {
     int32_t peel_items;       /* frontier engine, grid rounds with several splitters:
                                  at most this many splitters of one state per warp of
                                  the grid (0 = 8) */
+    int32_t small;            /* engine auto or frontier with the default schedule: an
+                                 LTS with |Act| <= 32 whose arrays fit in one CTA's
+                                 shared memory (about 12 B per transition and 116 B
+                                 per state, at most 227 KB: e.g. 1,000 states and
+                                 9,000 transitions) is reduced by one kernel launch
+                                 on one CTA (bisim_plan validates and keeps a copy
+                                 of the inputs). 0 = when it fits, -1 = never */
     int32_t slots;            /* mark-slot layout (Section 4.1.1): 0 = from every state's
                                  label set when |Act| <= 128 (the validation pass
                                  records the label sets; no sort), else by sorting

@@ -30,6 +30,7 @@ ENGINE_AUTO = 0
 ENGINE_DENSE = 1
 ENGINE_FRONTIER = 2
 ENGINE_PAIR = 3
+ENGINE_SMALL = 4  # reported in stats only: a small LTS on one CTA in shared memory
 
 
 class bisim_opts(ctypes.Structure):
@@ -53,6 +54,7 @@ class bisim_opts(ctypes.Structure):
         ("local_states", ctypes.c_int32),
         ("peel", ctypes.c_int32),
         ("peel_items", ctypes.c_int32),
+        ("small", ctypes.c_int32),
         ("slots", ctypes.c_int32),
     ]
 
@@ -161,11 +163,12 @@ def make_opts(engine: int = ENGINE_AUTO, rcpp_alg2: bool = False, raw_labels: bo
               test_hook: int = 0, max_ctas: int = 0, light_edges: int = 0,
               preprocess: int = 0, wide_threads: int = 0, wide_min_states: int = 0,
               splitters: int = 0, split_budget: int = 0, multi_min_states: int = 0,
-              local_states: int = 0, peel: int = 0, peel_items: int = 0, slots: int = 0) -> bisim_opts:
+              local_states: int = 0, peel: int = 0, peel_items: int = 0, small: int = 0,
+              slots: int = 0) -> bisim_opts:
     return bisim_opts(engine, int(rcpp_alg2), int(raw_labels), threads, ctas_per_sm, test_hook,
                       round_cap, timeout_ms, max_ctas, light_edges, preprocess, wide_threads,
                       wide_min_states, splitters, split_budget, multi_min_states, local_states, peel,
-                      peel_items, slots)
+                      peel_items, small, slots)
 
 
 # ----------------------------------------------------------- C-ABI mirrors

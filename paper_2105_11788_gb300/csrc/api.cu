@@ -107,7 +107,7 @@ int bisim_plan(int32_t n, int64_t m, int32_t num_act, const int32_t* src, const 
             break;
         }
         g_launches = 0;
-        rc = plan_build(p, src, act, dst, init_block);
+        rc = small_fits(p) ? small_plan(p, src, act, dst, init_block) : plan_build(p, src, act, dst, init_block);
         p->plan_launches = g_launches;
         if (rc) break;
         float ms = 0;
@@ -143,12 +143,17 @@ int bisim_refine(bisim_plan_t p, int32_t* out_block, bisim_stats* stats) {
         return BISIM_OK;
     }
     BISIM_CUDA_TRY(cudaEventRecord(p->ev0, p->st));
-    int engine = choose_engine(p);
     g_launches = 0;
-    int rc = engine == BISIM_ENGINE_DENSE  ? refine_dense(p, &s)
+    int rc;
+    if (p->small) {
+        rc = small_refine(p, out_block, &s);
+    } else {
+        const int engine = choose_engine(p);
+        rc = engine == BISIM_ENGINE_DENSE  ? refine_dense(p, &s)
              : engine == BISIM_ENGINE_PAIR ? refine_pair(p, &s)
                                            : refine_frontier(p, &s);
-    if (rc == BISIM_OK) rc = write_output(p, out_block, &s.num_blocks);
+        if (rc == BISIM_OK) rc = write_output(p, out_block, &s.num_blocks);
+    }
     s.launches = p->plan_launches + g_launches;
     if (rc == BISIM_OK) {
         float ms = 0;

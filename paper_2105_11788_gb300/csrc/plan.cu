@@ -1008,6 +1008,45 @@ int plan_build(bisim_plan_s* p, const int32_t* src, const int32_t* act, const in
     return BISIM_OK;
 }
 
+// The plan of a small LTS (one CTA in shared memory, see small_refine):
+// validation as in plan_build, and a copy of the inputs, which bisim_refine
+// reduces in one kernel launch.
+int small_plan(bisim_plan_s* p, const int32_t* src, const int32_t* act, const int32_t* dst, const int32_t* init) {
+    const int32_t n = p->n;
+    const int64_t m = p->m;
+    const int32_t A = p->A;
+    cudaStream_t st = p->st;
+    BISIM_TRY(p->ctrl.alloc(sizeof(bisim_ctrl), st));
+    BISIM_CUDA_TRY(cudaMemsetAsync(p->ctrl.p, 0, sizeof(bisim_ctrl), st));
+    DevMem used;
+    BISIM_TRY(used.alloc(sizeof(uint32_t) * (size_t)A, st));
+    BISIM_CUDA_TRY(cudaMemsetAsync(used.p, 0, sizeof(uint32_t) * (size_t)A, st));
+    const int vec = (((uintptr_t)src | (uintptr_t)dst | (uintptr_t)act) & 15u) == 0 ? 1 : 0;
+    k_validate<<<grid_for(std::max<int64_t>(m, n), T), T, 0, st>>>(src, act, dst, init, n, m, A,
+                                                                   &p->ctrl.as<bisim_ctrl>()->status,
+                                                                   used.as<uint32_t>(), vec);
+    BISIM_LAUNCHED();
+    BISIM_CUDA_TRY(cudaGetLastError());
+    BISIM_TRY(p->small_in.alloc(4 * (3 * (size_t)m + (size_t)n), st));
+    BISIM_TRY(p->small_res.alloc(8 * 8, st));
+    int32_t* base = p->small_in.as<int32_t>();
+    if (m) {
+        BISIM_CUDA_TRY(cudaMemcpyAsync(base, src, 4 * (size_t)m, cudaMemcpyDeviceToDevice, st));
+        if (act) BISIM_CUDA_TRY(cudaMemcpyAsync(base + m, act, 4 * (size_t)m, cudaMemcpyDeviceToDevice, st));
+        BISIM_CUDA_TRY(cudaMemcpyAsync(base + 2 * m, dst, 4 * (size_t)m, cudaMemcpyDeviceToDevice, st));
+    }
+    if (init) BISIM_CUDA_TRY(cudaMemcpyAsync(base + 3 * m, init, 4 * (size_t)n, cudaMemcpyDeviceToDevice, st));
+    p->small_has_act = act != nullptr;
+    p->small_has_init = init != nullptr;
+    BISIM_TRY(read_ctrl(p));
+    if (p->ctrl_h->status & ST_INVALID) {
+        set_last_error("an input array entry is out of range");
+        return BISIM_EINVAL;
+    }
+    p->small = true;
+    return BISIM_OK;
+}
+
 int write_output(bisim_plan_s* p, int32_t* out, int64_t* num_blocks) {
     const int32_t n = p->n;
     cudaStream_t st = p->st;

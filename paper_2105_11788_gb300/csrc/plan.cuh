@@ -123,6 +123,13 @@ struct bisim_plan_s {
     cudaStream_t aux_stream = nullptr;  // second stream of the split batch schedule
     cudaEvent_t aux_event = nullptr;
 
+    // small LTSs (one CTA, shared memory): the inputs kept by the plan
+    // (src, act, dst, init back to back), and the kernel's results
+    bool small = false;
+    bool small_has_act = false, small_has_init = false;
+    bisim::DevMem small_in;
+    bisim::DevMem small_res;            // int64 [8]
+
     uint32_t stamp = 0;      // last round stamp used (marks are never cleared)
     int64_t pre_rounds = 0;  // action-set preprocessing rounds run (0 for the pair engine)
     int64_t n_labels = 0;    // labels that occur
@@ -147,6 +154,10 @@ int refine_pair(bisim_plan_s* p, bisim_stats* st);
 // CTA-per-LTS frontier rounds over a batch plan; rounds[i] = iterations of LTS i
 int refine_frontier_batch(bisim_plan_s* p, bisim_stats* st, std::vector<long long>& rounds);
 int write_output(bisim_plan_s* p, int32_t* out_block, int64_t* num_blocks);
+// small LTSs: one CTA holds the whole reduction in shared memory
+bool small_fits(const bisim_plan_s* p);
+int small_plan(bisim_plan_s* p, const int32_t* src, const int32_t* act, const int32_t* dst, const int32_t* init);
+int small_refine(bisim_plan_s* p, int32_t* out_block, bisim_stats* st);
 bool preprocess_fused(const bisim_plan_s* p);
 int group_by_label_set(bisim_plan_s* p, const uint32_t* amask, int mask_words);
 

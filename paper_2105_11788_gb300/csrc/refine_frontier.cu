@@ -184,11 +184,12 @@ struct Worklist {
     size_t stride;
     int32_t base;
     int32_t cap;
+    int nbk = BISIM_BUCKETS;  // rings in use: larger blocks share the last one
 };
 
 // append a label whose block has `size` states to the FIFO ring of its size bucket
 __device__ __forceinline__ void push_sized(const Worklist& wl, int32_t label, int32_t size) {
-    const int bk = size_bucket(size);
+    const int bk = min(size_bucket(size), wl.nbk - 1);
     const unsigned long long pos = atomicAdd(&wl.tail[bk], 1ull);
     wl.queue[(size_t)bk * wl.stride + wl.base + pos % (unsigned long long)wl.cap] = label;
 }
@@ -638,7 +639,7 @@ __device__ __forceinline__ void set_unstable_warp(const FrontierArgs& a, const W
     int bk = 32 + (int)lane;  // a group of its own when nothing is pushed
     if (need) {
         if (size < 0) size = ld(&a.bend[label]) - ld(&a.bbeg[label]);
-        bk = size_bucket(size);
+        bk = min(size_bucket(size), wl.nbk - 1);
     }
     const unsigned peers = __match_any_sync(0xffffffffu, bk);
     const int first = __ffs(peers) - 1;
@@ -1306,6 +1307,7 @@ __device__ __forceinline__ bool multi_round(const FrontierArgs& a, const Worklis
 // size bucket 0, so a round may take tens of thousands of them.
 
 constexpr int PEEL_CHUNKS = 4;  // chunks of 32 transitions a warp loads at once
+constexpr int PEEL_MIN_SINGLES = 256;  // a peel round needs this many labels in size bucket 0
 
 __device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long* p) {
     return *(volatile const unsigned long long*)p;
@@ -1892,7 +1894,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_frontier_hybrid(FrontierArgs a, Hyb
     __shared__ CtaShared sh;
     __shared__ int s_defer[32];
     __shared__ int s_ndefer;
-    __shared__ int s_ns, s_nm, s_heavy, s_cmd, s_K, s_K0;
+    __shared__ int s_ns, s_nm, s_heavy, s_cmd, s_K, s_K0, s_av0;
     __shared__ bool s_peel;
     __shared__ unsigned long long s_h0;
     __shared__ unsigned s_stamp;
@@ -2008,15 +2010,27 @@ __global__ void __launch_bounds__(MAXT, 1) k_frontier_hybrid(FrontierArgs a, Hyb
         int K0 = 0;
         unsigned long long h0 = 0;
         int32_t C;
+        // Peel rounds pay when splitters of one state are many (each warp then
+        // walks several small items); with fewer than PEEL_MIN_SINGLES labels
+        // in size bucket 0 the round is selected and run as in multi_round
+        // (one splitter per touched block). Every CTA reads the same tail
+        // after the barrier, so all decide alike.
+        bool peel_sel = false;
         if (kmax > 1 && h.peel) {
+            if (threadIdx.x == 0)
+                s_av0 = (int)min(*(volatile const unsigned long long*)&wl.tail[0] - sh.head[0],
+                                 (unsigned long long)PEEL_MIN_SINGLES);
+            __syncthreads();
+            peel_sel = s_av0 >= PEEL_MIN_SINGLES;
+            __syncthreads();
+        }
+        if (peel_sel) {
             K1 = select_peel(a, wl, sh.head, sh, s_selC, s_selP, kmax, h.budget, h.cap0);
             K0 = sh.k0;
             h0 = sh.h0;
+            peel_now = true;
             K = K0 + K1;
             C = K0 > 0 ? ld(&wl.queue[wl.base + h0 % (unsigned long long)wl.cap]) : K1 > 0 ? s_selC[0] : -1;
-            // without a splitter of one state nothing can peel: the claim
-            // rule of multi_round (one splitter per touched block) is cheaper
-            peel_now = K0 > 0 || sh.n1 > 0;
         } else if (kmax > 1) {
             K = select_many(a, wl, sh.head, sh, s_selC, s_selP, kmax, h.budget);
             K1 = K;
@@ -2319,6 +2333,378 @@ __global__ void __launch_bounds__(1024) k_frontier_batch(FrontierArgs a, BatchAr
     if (edges) atomicAdd((unsigned long long*)&a.ctrl->edges, (unsigned long long)edges);
     if (states) atomicAdd((unsigned long long*)&a.ctrl->states, (unsigned long long)states);
     if (threadIdx.x == 0 && steps) atomicAdd((unsigned long long*)&a.ctrl->rounds, (unsigned long long)steps);
+}
+
+// ------------------------------------------------------------ small LTSs
+//
+// An LTS small enough to live in one CTA's shared memory is reduced by one
+// kernel launch: validation happened in bisim_plan; this kernel computes the
+// mark-slot layout from label sets (the reading of Algorithm 4 in plan.cu),
+// the incoming-transition CSR, the initial leaders (Algorithm 2, lines 1-6,
+// priority rule), the partition after the action-set preprocessing
+// (Algorithm 5's result: one block per (initial block, label set), led by
+// its smallest state), the refinable partition and worklist, the rounds of
+// the frontier engine (the same round functions, on shared-memory arrays
+// through generic pointers, with CTA barriers), and the canonical ids. Every
+// block's label is its smallest state throughout (a split keeps the label
+// with the part that holds it; the new label is the smallest state of the
+// other part), so the canonical id of a block is the number of labels below
+// it.
+constexpr int SMALL_THREADS = 1024;         // most threads of the CTA
+constexpr int SMALL_THREADS_DEFAULT = 512;
+constexpr int SMALL_RINGS = 4;   // worklist rings: blocks of 1, 2-3, 4-7 and more states
+constexpr int SMALL_KMAX = 32;   // splitters per round at most
+
+struct SmallLayout {
+    size_t tlist, in_edge, claim, mark, mask, off, in_ptr, block, elems, loc, bbeg, bend, mcnt, mscr, yscr, smark,
+        kmark, unstable, bspl, queue, total;
+};
+
+__host__ __device__ inline size_t small_take(size_t& o, size_t bytes, size_t align) {
+    o = (o + align - 1) / align * align;
+    const size_t r = o;
+    o += bytes;
+    return r;
+}
+
+__host__ __device__ inline SmallLayout small_layout(int32_t n, int64_t m) {
+    SmallLayout L;
+    size_t o = 0;
+    const size_t N = (size_t)n, M = (size_t)(m > 0 ? m : 1);
+    L.tlist = small_take(o, 32 * N, 16);  // int4 [2n]; the grouping's hash table while planning
+    L.in_edge = small_take(o, 8 * M, 8);
+    L.claim = small_take(o, 8 * N, 8);
+    L.mark = small_take(o, 4 * M, 4);  // mark_length <= m
+    L.mask = small_take(o, 4 * N, 4);
+    L.off = small_take(o, 4 * (N + 1), 4);
+    L.in_ptr = small_take(o, 4 * (N + 1), 4);
+    L.block = small_take(o, 4 * N, 4);
+    L.elems = small_take(o, 4 * N, 4);
+    L.loc = small_take(o, 4 * N, 4);
+    L.bbeg = small_take(o, 4 * N, 4);
+    L.bend = small_take(o, 4 * N, 4);
+    L.mcnt = small_take(o, 4 * N, 4);
+    L.mscr = small_take(o, 4 * N, 4);
+    L.yscr = small_take(o, 4 * N, 4);
+    L.smark = small_take(o, 4 * N, 4);
+    L.kmark = small_take(o, 4 * N, 4);
+    L.unstable = small_take(o, 4 * N, 4);
+    L.bspl = small_take(o, 4 * N, 4);
+    L.queue = small_take(o, 4 * SMALL_RINGS * N, 4);
+    L.total = o;
+    return L;
+}
+
+struct SmallArgs {
+    int32_t n;
+    int64_t m;
+    const int32_t* src;
+    const int32_t* act;   // null: every label 0
+    const int32_t* dst;
+    const int32_t* init;  // null: one initial block
+    int32_t* out;         // canonical ids
+    long long* res;       // [8]: iterations + 1, rounds, labels present, blocks after preprocessing,
+                          //      blocks, mark_length, transitions walked, states compared
+    bisim_ctrl* ctrl;     // status word
+    int64_t round_cap;
+    int alg2;
+    int kmax;
+    int32_t budget;
+};
+
+// exclusive prefix sum of arr[0 .. cnt) in place; returns the total
+__device__ int32_t cta_scan_array(int32_t* arr, int32_t cnt, CtaShared& sh) {
+    int32_t carry = 0;
+    for (int32_t base = 0; base < cnt; base += blockDim.x) {
+        const int32_t i = base + (int32_t)threadIdx.x;
+        const int32_t v = i < cnt ? arr[i] : 0;
+        int tot;
+        const int ex = cta_scan(v, sh, tot);
+        if (i < cnt) arr[i] = carry + ex;
+        carry += tot;
+    }
+    return carry;
+}
+
+__device__ __forceinline__ uint32_t mix64(unsigned long long x) {
+    x ^= x >> 33;
+    x *= 0xff51afd7ed558ccdull;
+    x ^= x >> 33;
+    x *= 0xc4ceb9fe1a85ec53ull;
+    x ^= x >> 33;
+    return (uint32_t)x;
+}
+
+__global__ void __launch_bounds__(SMALL_THREADS, 1) k_small(SmallArgs g) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ CtaShared sh;
+    __shared__ int s_defer[32];
+    __shared__ int s_ndefer;
+    __shared__ unsigned long long s_tail[BISIM_BUCKETS];
+    __shared__ int s_ns, s_nm;
+    __shared__ int32_t s_selC[SMALL_KMAX];
+    __shared__ int32_t s_selP[SMALL_KMAX + 1];
+    __shared__ uint32_t s_lost[SMALL_KMAX];
+    __shared__ unsigned s_orm;  // labels present (bits)
+    __shared__ int s_lead;
+    const int32_t n = g.n;
+    const int64_t m = g.m;
+    const int tid = threadIdx.x, T = blockDim.x;
+    const SmallLayout Lo = small_layout(n, m);
+    int4* tlist = reinterpret_cast<int4*>(smem + Lo.tlist);
+    unsigned long long* in_edge = reinterpret_cast<unsigned long long*>(smem + Lo.in_edge);
+    unsigned long long* claim = reinterpret_cast<unsigned long long*>(smem + Lo.claim);
+    uint32_t* mark = reinterpret_cast<uint32_t*>(smem + Lo.mark);
+    uint32_t* mask = reinterpret_cast<uint32_t*>(smem + Lo.mask);
+    int32_t* off = reinterpret_cast<int32_t*>(smem + Lo.off);
+    int32_t* in_ptr = reinterpret_cast<int32_t*>(smem + Lo.in_ptr);
+    int32_t* block = reinterpret_cast<int32_t*>(smem + Lo.block);
+    int32_t* elems = reinterpret_cast<int32_t*>(smem + Lo.elems);
+    int32_t* loc = reinterpret_cast<int32_t*>(smem + Lo.loc);
+    int32_t* bbeg = reinterpret_cast<int32_t*>(smem + Lo.bbeg);
+    int32_t* bend = reinterpret_cast<int32_t*>(smem + Lo.bend);
+    int32_t* mcnt = reinterpret_cast<int32_t*>(smem + Lo.mcnt);
+    int32_t* mscr = reinterpret_cast<int32_t*>(smem + Lo.mscr);
+    int32_t* yscr = reinterpret_cast<int32_t*>(smem + Lo.yscr);
+    uint32_t* smark = reinterpret_cast<uint32_t*>(smem + Lo.smark);
+    uint32_t* kmark = reinterpret_cast<uint32_t*>(smem + Lo.kmark);
+    uint32_t* unstable = reinterpret_cast<uint32_t*>(smem + Lo.unstable);
+    int32_t* bspl = reinterpret_cast<int32_t*>(smem + Lo.bspl);
+    int32_t* queue = reinterpret_cast<int32_t*>(smem + Lo.queue);
+
+    // label sets and in-degrees
+    for (int32_t i = tid; i < n; i += T) {
+        mask[i] = 0u;
+        in_ptr[i] = 0;
+    }
+    if (tid == 0) {
+        in_ptr[n] = 0;
+        off[n] = 0;
+        s_orm = 0u;
+        s_lead = 0;
+    }
+    if (tid < BISIM_BUCKETS) {
+        s_tail[tid] = 0ull;
+        sh.head[tid] = 0ull;
+    }
+    if (tid < SMALL_KMAX) s_lost[tid] = 0u;  // older than every round stamp
+    __syncthreads();
+    for (int64_t i = tid; i < m; i += T) {
+        const int32_t s = g.src[i], a = g.act ? g.act[i] : 0, d = g.dst[i];
+        atomicOr(&mask[s], 1u << a);
+        atomicAdd(&in_ptr[d], 1);
+    }
+    __syncthreads();
+    unsigned orm = 0u;
+    for (int32_t i = tid; i < n; i += T) {
+        off[i] = __popc(mask[i]);
+        orm |= mask[i];
+    }
+    orm = __reduce_or_sync(0xffffffffu, orm);
+    if ((tid & 31) == 0 && orm) atomicOr(&s_orm, orm);
+    __syncthreads();
+    // off = exclusive sum of nr_marks (off[n] = L), in_ptr likewise over in-degrees
+    const int32_t L = cta_scan_array(off, n + 1, sh);
+    cta_scan_array(in_ptr, n + 1, sh);
+    // incoming-transition CSR, entries (source << 32) | slot; mcnt counts per target
+    for (int32_t i = tid; i < n; i += T) mcnt[i] = 0;
+    for (int32_t i = tid; i < L; i += T) mark[i] = 0u;
+    __syncthreads();
+    for (int64_t i = tid; i < m; i += T) {
+        const int32_t s = g.src[i], a = g.act ? g.act[i] : 0, d = g.dst[i];
+        const uint32_t slot = (uint32_t)off[s] + __popc(mask[s] & ((1u << a) - 1u));
+        in_edge[in_ptr[d] + atomicAdd(&mcnt[d], 1)] = ((unsigned long long)(uint32_t)s << 32) | slot;
+    }
+    // initial leaders: the smallest member of every initial block
+    for (int32_t i = tid; i < n; i += T) yscr[i] = NONE;
+    __syncthreads();
+    if (g.init)
+        for (int32_t i = tid; i < n; i += T) atomicMin(&yscr[g.init[i]], i);
+    __syncthreads();
+    for (int32_t i = tid; i < n; i += T) block[i] = g.init ? yscr[g.init[i]] : 0;
+    // action-set preprocessing: one block per (initial block, label set), led
+    // by its smallest state, found through a hash table of 2n entries in the
+    // (not yet used) touched-list area
+    const int32_t cap = 2 * n;
+    unsigned long long* hkey = reinterpret_cast<unsigned long long*>(tlist);
+    int32_t* hval = reinterpret_cast<int32_t*>(hkey + cap);
+    for (int32_t h = tid; h < cap; h += T) {
+        hkey[h] = ~0ull;
+        hval[h] = NONE;
+    }
+    __syncthreads();
+    for (int32_t i = tid; i < n; i += T) {
+        const unsigned long long key = ((unsigned long long)(uint32_t)block[i] << 32) | mask[i];
+        int32_t h = (int32_t)(mix64(key) % (uint32_t)cap);
+        for (;;) {
+            const unsigned long long old = atomicCAS(&hkey[h], ~0ull, key);
+            if (old == ~0ull || old == key) {
+                atomicMin(&hval[h], i);
+                break;
+            }
+            h = h + 1 == cap ? 0 : h + 1;
+        }
+    }
+    __syncthreads();
+    for (int32_t i = tid; i < n; i += T) {
+        const unsigned long long key = ((unsigned long long)(uint32_t)block[i] << 32) | mask[i];
+        int32_t h = (int32_t)(mix64(key) % (uint32_t)cap);
+        while (hkey[h] != key) h = h + 1 == cap ? 0 : h + 1;
+        yscr[i] = hval[h];
+    }
+    __syncthreads();
+    // refinable partition: members grouped by label (counting sort), ranges, worklist
+    for (int32_t i = tid; i < n; i += T) {
+        block[i] = yscr[i];
+        mcnt[i] = 0;
+    }
+    __syncthreads();
+    for (int32_t i = tid; i < n; i += T) atomicAdd(&mcnt[block[i]], 1);
+    __syncthreads();
+    for (int32_t i = tid; i < n; i += T) bbeg[i] = mcnt[i];
+    __syncthreads();
+    cta_scan_array(bbeg, n, sh);
+    for (int32_t i = tid; i < n; i += T) {
+        bend[i] = bbeg[i] + mcnt[i];
+        yscr[i] = 0;
+    }
+    __syncthreads();
+    for (int32_t i = tid; i < n; i += T) {
+        const int32_t pos = bbeg[block[i]] + atomicAdd(&yscr[block[i]], 1);
+        elems[pos] = i;
+        loc[i] = pos;
+    }
+    for (int32_t i = tid; i < n; i += T) {
+        smark[i] = 0u;
+        kmark[i] = 0u;
+        bspl[i] = 0;
+        claim[i] = ~0ull;
+        unstable[i] = block[i] == i ? 1u : 0u;
+    }
+    __syncthreads();
+    for (int32_t i = tid; i < n; i += T) mcnt[i] = 0;
+    FrontierArgs a;
+    a.n = n;
+    a.off = off;
+    a.in_ptr = in_ptr;
+    a.in_edge = in_edge;
+    a.block = block;
+    a.mark = mark;
+    a.unstable = unstable;
+    a.elems = elems;
+    a.loc = loc;
+    a.bbeg = bbeg;
+    a.bend = bend;
+    a.mcnt = mcnt;
+    a.mscr = mscr;
+    a.yscr = yscr;
+    a.smark = smark;
+    a.kmark = kmark;
+    a.tlist = tlist;
+    a.queue = queue;
+    a.claim = claim;
+    a.minx = nullptr;
+    a.smark64 = nullptr;
+    a.lostl = nullptr;
+    a.bspl = bspl;
+    a.ctrl = g.ctrl;
+    a.gb.counter = nullptr;
+    a.gb.status = &g.ctrl->status;
+    a.gb.timeout_ns = 0;
+    a.stamp0 = 0;
+    a.round_cap = g.round_cap;
+    a.alg2 = g.alg2;
+    a.test_hook = 0;
+    Worklist wl{s_tail, queue, (size_t)n, 0, n};
+    wl.nbk = SMALL_RINGS;
+    __syncthreads();
+    // Algorithm 3, lines 1-3: every label is unstable
+    int leaders = 0;
+    for (int32_t i = tid; i < n; i += T)
+        if (block[i] == i) {
+            push_sized(wl, i, bend[i] - bbeg[i]);
+            leaders++;
+        }
+    leaders = __reduce_add_sync(0xffffffffu, leaders);
+    if ((tid & 31) == 0 && leaders) atomicAdd(&s_lead, leaders);
+    __syncthreads();
+    // rounds, as the one-CTA rounds of the batch kernel: after a round of
+    // several splitters with at most two winners, single splitters for a
+    // stretch of rounds that doubles (2 ... 64) while such rounds repeat
+    const int64_t gw = tid >> 5, nwarps = T >> 5;
+    long long edges = 0, states = 0, commits = 0;
+    int64_t r = 0;
+    int skip = 0, backoff = 0;
+    for (;;) {
+        r++;
+        const uint32_t stamp = (uint32_t)r;
+        int K;
+        int32_t C;
+        const bool many = g.kmax > 1 && skip == 0;
+        if (skip > 0) skip--;
+        if (many) {
+            K = select_many(a, wl, sh.head, sh, s_selC, s_selP, g.kmax, g.budget);
+            C = K > 0 ? s_selC[0] : -1;
+        } else {
+            C = select_splitter(wl, sh.head, sh);
+            K = C >= 0 ? 1 : 0;
+        }
+        if (K == 0) break;
+        if (r > g.round_cap) {
+            if (tid == 0) atomicOr(&g.ctrl->status, ST_ROUNDS);
+            break;
+        }
+        if (tid == 0) {
+            if (K == 1) {
+                unstable[C] = 0u;
+                commits++;
+            }
+            s_ns = 0;
+            s_nm = 0;
+        }
+        __syncthreads();
+        if (K == 1) {
+            mark_step(a, C, stamp, gw, nwarps, &s_ns, &s_nm, tlist, tlist + n, edges);
+            __syncthreads();
+            split_step(a, wl, sh, s_defer, &s_ndefer, stamp, C, s_ns, tlist, s_nm, tlist + n, 0, 1, states);
+        } else {
+            multi_round(a, wl, sh, s_defer, &s_ndefer, s_selC, s_selP, K, s_lost, stamp, gw, nwarps, &s_ns, &s_nm,
+                        tlist, tlist + n, 0, 1, edges, states, commits, [] {
+                            __syncthreads();
+                            return true;
+                        });
+            int nlost = 0;  // every warp counts the same losers
+            for (int j0 = 0; j0 < K; j0 += 32) {
+                const int j = j0 + (tid & 31);
+                nlost += __popc(__ballot_sync(0xffffffffu, j < K && s_lost[j] == stamp));
+            }
+            if (K - nlost <= 2) {
+                backoff = min(max(2 * backoff, 2), 64);
+                skip = backoff;
+            } else {
+                backoff = 0;
+            }
+        }
+        __syncthreads();
+    }
+    // canonical ids: a block's label is its smallest state, so its id is the
+    // number of labels below it
+    for (int32_t i = tid; i < n; i += T) mcnt[i] = block[i] == i ? 1 : 0;
+    __syncthreads();
+    const int32_t nb = cta_scan_array(mcnt, n, sh);
+    for (int32_t i = tid; i < n; i += T) g.out[i] = mcnt[block[i]];
+    // counts of each thread (commits by the threads that carried splitters out)
+    if (edges) atomicAdd((unsigned long long*)&g.res[6], (unsigned long long)edges);
+    if (states) atomicAdd((unsigned long long*)&g.res[7], (unsigned long long)states);
+    if (commits) atomicAdd((unsigned long long*)&g.res[0], (unsigned long long)commits);
+    if (tid == 0) {
+        atomicAdd((unsigned long long*)&g.res[0], 1ull);  // the final empty iteration
+        g.res[1] = r;
+        g.res[2] = __popc(s_orm);
+        g.res[3] = s_lead;
+        g.res[4] = nb;
+        g.res[5] = L;
+    }
 }
 
 // ---------------------------------------------------------------- set-up
@@ -2700,6 +3086,70 @@ int refine_frontier_batch(bisim_plan_s* p, bisim_stats* stats, std::vector<long 
         stats->grid_ctas = grid;
     }
     return report(p);
+}
+
+// Does this plan's LTS take the one-CTA shared-memory path?
+bool small_fits(const bisim_plan_s* p) {
+    const bisim_opts& o = p->opts;
+    if (o.small < 0 || p->n < 1 || p->A > 32) return false;
+    if (o.engine != BISIM_ENGINE_AUTO && o.engine != BISIM_ENGINE_FRONTIER) return false;
+    if (o.raw_labels || o.local_states != 0 || o.light_edges != 0 || o.preprocess == 1 || o.test_hook) return false;
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return false;
+    return small_layout(p->n, p->m).total + 8192 <= (size_t)optin;  // room for the static shared arrays
+}
+
+int small_refine(bisim_plan_s* p, int32_t* out_block, bisim_stats* stats) {
+    cudaStream_t st = p->st;
+    const SmallLayout Lo = small_layout(p->n, p->m);
+    SmallArgs g;
+    g.n = p->n;
+    g.m = p->m;
+    const int32_t* base = p->small_in.as<int32_t>();
+    g.src = base;
+    g.act = p->small_has_act ? base + p->m : nullptr;
+    g.dst = base + 2 * p->m;
+    g.init = p->small_has_init ? base + 3 * p->m : nullptr;
+    g.out = out_block;
+    g.res = p->small_res.as<long long>();
+    g.ctrl = p->ctrl.as<bisim_ctrl>();
+    g.round_cap = p->opts.round_cap > 0 ? p->opts.round_cap : 3ll * p->n + p->A + 2;
+    g.alg2 = (p->opts.rcpp_alg2 && p->A == 1) ? 1 : 0;
+    g.kmax = p->opts.splitters > 0 ? std::min(p->opts.splitters, SMALL_KMAX) : SMALL_KMAX;
+    const int budget_per_warp = p->opts.split_budget > 0 ? std::min(p->opts.split_budget, 1 << 20) : 4;
+    const int threads = p->opts.threads > 0 ? p->opts.threads : SMALL_THREADS_DEFAULT;
+    g.budget = budget_per_warp * (threads / 32);
+    BISIM_CUDA_TRY(cudaMemsetAsync(p->small_res.p, 0, 8 * 8, st));
+    BISIM_CUDA_TRY(cudaMemsetAsync(&g.ctrl->status, 0, sizeof(int), st));
+    BISIM_CUDA_TRY(cudaFuncSetAttribute(k_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Lo.total));
+    BISIM_CUDA_TRY(cudaEventRecord(p->evk0, st));
+    k_small<<<1, threads, Lo.total, st>>>(g);
+    BISIM_LAUNCHED();
+    BISIM_CUDA_TRY(cudaGetLastError());
+    BISIM_CUDA_TRY(cudaEventRecord(p->evk1, st));
+    long long res[8];
+    BISIM_CUDA_TRY(cudaMemcpyAsync(res, p->small_res.p, sizeof(res), cudaMemcpyDeviceToHost, st));
+    BISIM_TRY(read_ctrl(p));
+    BISIM_TRY(report(p));
+    if (stats) {
+        BISIM_TRY(persistent_ms(p, &stats->t_main_ms));
+        stats->rounds = res[0];
+        stats->steps = res[1];
+        stats->local_steps = res[1];
+        stats->pre_rounds = res[2];
+        stats->initial_blocks = res[3];
+        stats->num_blocks = res[4];
+        stats->mark_length = res[5];
+        stats->edges_visited = res[6];
+        stats->states_visited = res[7];
+        stats->engine = BISIM_ENGINE_SMALL;
+        stats->grid_ctas = 1;
+    }
+    p->L = res[5];
+    p->pre_rounds = res[2];
+    p->initial_blocks = res[3];
+    return BISIM_OK;
 }
 
 }  // namespace bisim

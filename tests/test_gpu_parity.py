@@ -456,7 +456,7 @@ def test_plan_arrays_equal_algorithm4(slots):
               lts_gen.quotient_expansion(seed=6, classes=300, trans=3000, copies_hi=20),
               lts_gen.powerlaw(seed=3, n=20000)]
     for lts in cases:
-        got = _plan_arrays(lts, slots=slots)
+        got = _plan_arrays(lts, slots=slots, small=-1)  # the grid plan (a small LTS keeps no such arrays)
         ref = oracle.plan(lts.n, lts.num_act, lts.src, lts.act, lts.dst)
         off = ref["off"].astype(np.int64)
         L = ref["mark_length"]
@@ -481,3 +481,68 @@ def test_plan_arrays_equal_algorithm4(slots):
         have = np.sort((tgt << 40) | ((ie >> 32) << 20) | (ie & 0xffffffff))
         if want is not None:
             assert have.tolist() == want.tolist(), lts.name
+
+
+def _small_cases():
+    cases = [lts_gen.random_small(1200 + s, int(5 + 7 * s), 1 + s % 4, int(20 + 25 * s), blocks=1 + s % 3)
+             for s in range(40)]
+    cases += [lts_gen.kripke_uniform(), lts_gen.kripke_uniform(seed=7, n=600, m=4000), lts_gen.fan_out(300),
+              lts_gen.chain(n=1500), lts_gen.quotient_expansion(seed=8, classes=40, trans=300, num_act=5, copies_hi=12),
+              _hub_lts(4, 700, 10, 300, deg=3, num_act=2), lts_gen.powerlaw(seed=3, n=600, num_act=32)]
+    e = np.zeros(0, dtype=np.int32)
+    cases += [lts_gen.LTS("no-transitions", 7, 1, e, e, e, np.array([0, 0, 3, 3, 6, 6, 0], np.int32)),
+              lts_gen.from_triples(1, 1, [(0, 0, 0)]), lts_gen.from_triples(2, 3, [(0, 2, 1), (0, 2, 1), (1, 2, 1)]),
+              lts_gen.from_triples(4, 32, [(0, 31, 1), (1, 0, 2), (2, 31, 3), (3, 0, 0)])]
+    return cases
+
+
+def test_small_ltss_on_one_cta_in_shared_memory():
+    """LTSs that fit in one CTA's shared memory are reduced by one launch
+    (stats.engine = BISIM_ENGINE_SMALL): the oracle's partition, the same as
+    with the path off, and Theorem 3's iteration bounds."""
+    for lts in _small_cases():
+        want = oracle.ks_lts(lts)
+        got, st = run(lts, bisim.ENGINE_AUTO)
+        assert st.engine == bisim.ENGINE_SMALL, lts.name
+        assert got.tolist() == want.tolist(), lts.name
+        assert st.num_blocks == defs.num_blocks(want)
+        B = defs.num_blocks(want)
+        assert B + 1 <= st.rounds <= 3 * B - st.initial_blocks + 1, lts.name
+        off, st2 = run(lts, bisim.ENGINE_AUTO, small=-1)
+        assert st2.engine != bisim.ENGINE_SMALL and off.tolist() == want.tolist(), lts.name
+        assert st.pre_rounds == st2.pre_rounds and st.initial_blocks == st2.initial_blocks, lts.name
+        assert st.mark_length == st2.mark_length, lts.name
+
+
+@pytest.mark.parametrize("kw", [dict(splitters=1), dict(splitters=2, split_budget=1), dict(rcpp_alg2=True)],
+                         ids=["one-splitter", "two-splitters", "algorithm-2"])
+def test_small_path_settings(kw):
+    for lts in _small_cases()[:30] + [lts_gen.kripke_uniform(), lts_gen.chain(n=1000)]:
+        got, st = run(lts, bisim.ENGINE_FRONTIER, **kw)
+        assert st.engine == bisim.ENGINE_SMALL
+        assert got.tolist() == oracle.ks_lts(lts).tolist(), lts.name
+        if kw.get("splitters") == 1:
+            assert st.steps == st.rounds
+
+
+def test_small_path_errors_and_replanning():
+    """Out-of-range entries are rejected by bisim_plan; the round cap gives
+    BISIM_EROUNDS; a plan refines twice with the same result."""
+    import torch
+
+    bad = lts_gen.from_triples(3, 2, [(0, 1, 1), (1, 2, 2)])
+    with pytest.raises(bisim.BisimError) as ei:
+        run(bad, bisim.ENGINE_AUTO)
+    assert ei.value.code == bisim.BISIM_EINVAL
+    with pytest.raises(bisim.BisimError) as ei:
+        run(lts_gen.chain(n=500), bisim.ENGINE_AUTO, round_cap=10)
+    assert ei.value.code == bisim.BISIM_EROUNDS
+    lts = lts_gen.kripke_uniform(seed=2)
+    d = lambda a: torch.from_numpy(a).cuda()  # noqa: E731
+    with bisim.Plan(lts.n, lts.num_act, d(lts.src), d(lts.act), d(lts.dst), d(lts.init)) as p:
+        a, st1 = p.refine()
+        a = a.cpu().numpy().copy()
+        b, st2 = p.refine()
+        b = b.cpu().numpy()
+    assert st1.engine == bisim.ENGINE_SMALL
+    assert np.array_equal(a, b) and a.tolist() == oracle.ks_lts(lts).tolist()
