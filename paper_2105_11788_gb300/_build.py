@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libbisim.so")
-# diagnostic build with the hybrid kernel's phase timers (see diag.py phases)
+# diagnostic build with the hybrid kernel's phase timers (bisim_phase_times, bisim_phase_trace)
 PHASE_OUT = os.path.join(OUT, "phase")
 PHASE_LIB = os.path.join(PHASE_OUT, "libbisim_phase.so")
 ROOT = os.path.dirname(HERE)
