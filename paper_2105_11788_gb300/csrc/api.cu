@@ -84,23 +84,11 @@ int bisim_plan(int32_t n, int64_t m, int32_t num_act, const int32_t* src, const 
     p->A = num_act;
     p->st = (cudaStream_t)stream;
     if (opts) p->opts = *opts;
-    int dev = 0;
     int rc = BISIM_OK;
     do {
-        cudaError_t e = cudaGetDevice(&dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, dev);
-        if (e == cudaSuccess && retain_pool_memory() != BISIM_OK) e = cudaErrorUnknown;
-        if (e == cudaSuccess) e = cudaMallocHost(&p->ctrl_h, sizeof(bisim_ctrl));
-        if (e == cudaSuccess) e = cudaEventCreate(&p->ev0);
-        if (e == cudaSuccess) e = cudaEventCreate(&p->ev1);
-        if (e == cudaSuccess) e = cudaEventCreate(&p->evk0);
-        if (e == cudaSuccess) e = cudaEventCreate(&p->evk1);
-        if (e != cudaSuccess) {
-            set_last_error(std::string("device setup: ") + cudaGetErrorString(e));
-            rc = BISIM_ECUDA;
-            break;
-        }
-        e = cudaEventRecord(p->ev0, p->st);
+        rc = device_setup(p);
+        if (rc) break;
+        cudaError_t e = cudaEventRecord(p->ev0, p->st);
         if (e != cudaSuccess) {
             set_last_error(std::string("cudaEventRecord: ") + cudaGetErrorString(e));
             rc = BISIM_ECUDA;
@@ -179,6 +167,7 @@ int bisim_plan_arrays(bisim_plan_t p, int32_t* off_h, int32_t* slot_src_h, int32
         set_last_error("bad argument");
         return BISIM_EINVAL;
     }
+    if (slot_src_h || slot_act_h) BISIM_TRY(ensure_slot_arrays(p));
     const size_t n1 = (size_t)p->n + 1, L = (size_t)p->L, m = (size_t)p->m;
     if (mark_length) *mark_length = p->L;
     if (off_h && p->off.p) BISIM_CUDA_TRY(cudaMemcpyAsync(off_h, p->off.p, 4 * n1, cudaMemcpyDeviceToHost, p->st));

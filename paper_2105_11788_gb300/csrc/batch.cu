@@ -155,19 +155,6 @@ __global__ void k_batch_local(int k, const int64_t* __restrict__ state_off, cons
     }
 }
 
-int device_setup(bisim_plan_s* p) {
-    int dev = 0;
-    BISIM_CUDA_TRY(cudaGetDevice(&dev));
-    BISIM_CUDA_TRY(cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, dev));
-    BISIM_TRY(retain_pool_memory());
-    BISIM_CUDA_TRY(cudaMallocHost(&p->ctrl_h, sizeof(bisim_ctrl)));
-    BISIM_CUDA_TRY(cudaEventCreate(&p->ev0));
-    BISIM_CUDA_TRY(cudaEventCreate(&p->ev1));
-    BISIM_CUDA_TRY(cudaEventCreate(&p->evk0));
-    BISIM_CUDA_TRY(cudaEventCreate(&p->evk1));
-    return BISIM_OK;
-}
-
 int batch_plan_build(bisim_plan_s* p, int32_t k, const int64_t* state_off_h, const int64_t* trans_off_h,
                      const int32_t* num_act_h, const int32_t* src, const int32_t* act, const int32_t* dst,
                      const int32_t* init) {

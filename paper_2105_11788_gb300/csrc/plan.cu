@@ -15,6 +15,8 @@
 //    leader getting its smallest member as new leader.
 // Plus the canonical output step shared by both engines.
 #include <algorithm>
+#include <mutex>
+#include <vector>
 
 #include "plan.cuh"
 
@@ -595,12 +597,72 @@ int group_by_label_set(bisim_plan_s* p, const uint32_t* amask, int mask_words) {
 
 }  // namespace bisim
 
+namespace {
+
+// Pinned control mirrors and timing events outlive their plans: creating
+// them (a page-locked host allocation and four events) costs more than a
+// whole small reduction, so released sets wait here, per device, for the
+// next plan.
+struct HostRes {
+    int dev;
+    bisim_ctrl* ctrl_h;
+    cudaEvent_t ev[4];
+};
+constexpr size_t HOST_RES_KEEP = 64;
+std::mutex g_res_mu;
+std::vector<HostRes> g_res;
+
+}  // namespace
+
+namespace bisim {
+
+int device_setup(bisim_plan_s* p) {
+    int dev = 0;
+    BISIM_CUDA_TRY(cudaGetDevice(&dev));
+    BISIM_CUDA_TRY(cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, dev));
+    BISIM_TRY(retain_pool_memory());
+    p->dev = dev;
+    {
+        std::lock_guard<std::mutex> lk(g_res_mu);
+        for (size_t i = g_res.size(); i-- > 0;) {
+            if (g_res[i].dev != dev) continue;
+            const HostRes r = g_res[i];
+            g_res.erase(g_res.begin() + (std::ptrdiff_t)i);
+            p->ctrl_h = r.ctrl_h;
+            p->ev0 = r.ev[0];
+            p->ev1 = r.ev[1];
+            p->evk0 = r.ev[2];
+            p->evk1 = r.ev[3];
+            return BISIM_OK;
+        }
+    }
+    BISIM_CUDA_TRY(cudaMallocHost(&p->ctrl_h, sizeof(bisim_ctrl)));
+    BISIM_CUDA_TRY(cudaEventCreate(&p->ev0));
+    BISIM_CUDA_TRY(cudaEventCreate(&p->ev1));
+    BISIM_CUDA_TRY(cudaEventCreate(&p->evk0));
+    BISIM_CUDA_TRY(cudaEventCreate(&p->evk1));
+    return BISIM_OK;
+}
+
+}  // namespace bisim
+
 bisim_plan_s::~bisim_plan_s() {
-    if (ctrl_h) cudaFreeHost(ctrl_h);
-    if (ev0) cudaEventDestroy(ev0);
-    if (ev1) cudaEventDestroy(ev1);
-    if (evk0) cudaEventDestroy(evk0);
-    if (evk1) cudaEventDestroy(evk1);
+    // the destroy call synchronised the stream: nothing in flight uses these
+    bool kept = false;
+    if (ctrl_h && ev0 && ev1 && evk0 && evk1) {
+        std::lock_guard<std::mutex> lk(g_res_mu);
+        if (g_res.size() < HOST_RES_KEEP) {
+            g_res.push_back(HostRes{dev, ctrl_h, {ev0, ev1, evk0, evk1}});
+            kept = true;
+        }
+    }
+    if (!kept) {
+        if (ctrl_h) cudaFreeHost(ctrl_h);
+        if (ev0) cudaEventDestroy(ev0);
+        if (ev1) cudaEventDestroy(ev1);
+        if (evk0) cudaEventDestroy(evk0);
+        if (evk1) cudaEventDestroy(evk1);
+    }
     if (aux_event) cudaEventDestroy(aux_event);
     if (aux_stream) {
         cudaStreamSynchronize(aux_stream);
@@ -791,14 +853,6 @@ static int slots_from_masks(bisim_plan_s* p, const int32_t* src, const int32_t* 
     BISIM_CUDA_TRY(cudaMemcpyAsync(&L_h, off + n, 4, cudaMemcpyDeviceToHost, st));
     BISIM_CUDA_TRY(cudaStreamSynchronize(st));
     p->L = (int64_t)L_h;
-    BISIM_TRY(p->slot_src.alloc(4 * (size_t)p->L, st));
-    BISIM_TRY(p->slot_act.alloc(4 * (size_t)p->L, st));
-    if (n) {
-        k_mask_slots<<<gn, T, 0, st>>>(amask, off, n, mask_words, p->slot_src.as<int32_t>(),
-                                       p->slot_act.as<int32_t>());
-        BISIM_LAUNCHED();
-        BISIM_CUDA_TRY(cudaGetLastError());
-    }
     BISIM_TRY(p->in_edge.alloc(8 * (size_t)m, st));
     if (!m) return BISIM_OK;
     // a3: bins of 2^bin_bits targets, at most CSR_MAX_BINS of them, whose
@@ -840,6 +894,19 @@ static int slots_from_masks(bisim_plan_s* p, const int32_t* src, const int32_t* 
     return BISIM_OK;
 }
 
+int ensure_slot_arrays(bisim_plan_s* p) {
+    if (p->slot_src.p || !p->amask.p || p->L == 0) return BISIM_OK;
+    cudaStream_t st = p->st;
+    BISIM_TRY(p->slot_src.alloc(4 * (size_t)p->L, st));
+    BISIM_TRY(p->slot_act.alloc(4 * (size_t)p->L, st));
+    k_mask_slots<<<grid_for(p->n, T), T, 0, st>>>(p->amask.as<uint32_t>(), p->off.as<uint32_t>(), p->n,
+                                                  p->mask_words, p->slot_src.as<int32_t>(),
+                                                  p->slot_act.as<int32_t>());
+    BISIM_LAUNCHED();
+    BISIM_CUDA_TRY(cudaGetLastError());
+    return BISIM_OK;
+}
+
 int plan_build(bisim_plan_s* p, const int32_t* src, const int32_t* act, const int32_t* dst,
                const int32_t* init) {
     const int32_t n = p->n;
@@ -860,8 +927,10 @@ int plan_build(bisim_plan_s* p, const int32_t* src, const int32_t* act, const in
     const int vec = (((uintptr_t)src | (uintptr_t)dst | (uintptr_t)act) & 15u) == 0 ? 1 : 0;
     const int mask_words = (A + 31) / 32;
     const bool by_masks = mask_words <= MASK_WORDS_MAX && p->opts.slots == 0;
-    DevMem amask;
+    DevMem amask_local;
+    DevMem& amask = by_masks ? p->amask : amask_local;
     if (by_masks) {
+        p->mask_words = mask_words;
         BISIM_TRY(amask.alloc(4 * (size_t)mask_words * n, st));
         BISIM_TRY(p->off.alloc(4 * ((size_t)n + 1), st));
         BISIM_TRY(p->in_ptr.alloc(4 * ((size_t)n + 1), st));
@@ -947,8 +1016,6 @@ int plan_build(bisim_plan_s* p, const int32_t* src, const int32_t* act, const in
         a.L = L;
         a.n_labels = (int32_t)p->pre_rounds;
         a.labels = p->labels.as<int32_t>();
-        a.slot_src = p->slot_src.as<int32_t>();
-        a.slot_act = p->slot_act.as<int32_t>();
         a.block = p->block.as<int32_t>();
         a.lmark = p->lmark.as<uint32_t>();
         a.nl64 = p->nl64.as<unsigned long long>();
@@ -961,13 +1028,16 @@ int plan_build(bisim_plan_s* p, const int32_t* src, const int32_t* act, const in
         } else if (a.mask_words <= MASK_WORDS_MAX) {  // up to 128 labels: 16 B or less per state
             BISIM_TRY(amask.alloc(4 * (size_t)a.mask_words * n, st));
             BISIM_CUDA_TRY(cudaMemsetAsync(amask.p, 0, 4 * (size_t)a.mask_words * n, st));
-            k_label_masks<<<grid_for(L, T), T, 0, st>>>(a.slot_src, a.slot_act, L, a.mask_words,
-                                                        amask.as<uint32_t>());
+            k_label_masks<<<grid_for(L, T), T, 0, st>>>(p->slot_src.as<int32_t>(), p->slot_act.as<int32_t>(), L,
+                                                        a.mask_words, amask.as<uint32_t>());
             BISIM_LAUNCHED();
             BISIM_CUDA_TRY(cudaGetLastError());
             a.amask = amask.as<uint32_t>();
         }
         const bool fused = a.amask && preprocess_fused(p);
+        if (!fused) BISIM_TRY(ensure_slot_arrays(p));  // the literal label rounds walk the slots
+        a.slot_src = p->slot_src.as<int32_t>();
+        a.slot_act = p->slot_act.as<int32_t>();
         if (fused) {
             // the partition after every label round: one block per (initial
             // block, label set), led by its smallest state

@@ -70,6 +70,7 @@ struct bisim_plan_s {
     cudaStream_t st = nullptr;
     bisim_opts opts{};
     int sm_count = 0;
+    int dev = 0;
 
     // read-only after planning
     bisim::DevMem off;       // int32 [n+1]: first mark slot of each state; off[n] = L
@@ -77,6 +78,10 @@ struct bisim_plan_s {
     bisim::DevMem in_edge;   // uint64 [m]: (source << 32) | mark slot of the transition
     bisim::DevMem slot_src;  // int32 [L]: state owning each mark slot
     bisim::DevMem slot_act;  // int32 [L]: label of each mark slot
+    // label set of every state (mask_words 32-bit words) when the slots came
+    // from label sets; slot_src / slot_act are then filled on first use
+    bisim::DevMem amask;
+    int mask_words = 0;
     bisim::DevMem labels;    // int32 [n_labels]: labels that occur, increasing
     bisim::DevMem block0;    // int32 [n]: leader labels after preprocessing
 
@@ -171,5 +176,10 @@ int launch_persistent(const void* fn, void** args, int threads, bisim_plan_s* p,
 // Device time between evk0 and evk1 of the last persistent launch.
 int persistent_ms(bisim_plan_s* p, double* ms);
 int read_ctrl(bisim_plan_s* p);
+// Device, SM count, pool settings, the pinned control mirror and the timing
+// events of a new plan (the last three reused from destroyed plans).
+int device_setup(bisim_plan_s* p);
+// Fill slot_src / slot_act from the label sets if the plan has not yet.
+int ensure_slot_arrays(bisim_plan_s* p);
 
 }  // namespace bisim

@@ -32,6 +32,7 @@
 // below). Rounds run on the whole grid, on CTA 0 alone (light rounds of the
 // hybrid schedule) or on the CTA that owns an LTS of a batch.
 #include <algorithm>
+#include <mutex>
 
 #include "plan.cuh"
 
@@ -3088,16 +3089,41 @@ int refine_frontier_batch(bisim_plan_s* p, bisim_stats* stats, std::vector<long 
     return report(p);
 }
 
+// Dynamic shared memory k_small may take on `dev`: the opt-in maximum per
+// CTA less the kernel's static shared arrays. The kernel's limit is raised
+// to that once per device; 0 if either query fails.
+static size_t small_smem_room(int dev) {
+    constexpr int MAXDEV = 64;
+    static std::mutex mu;
+    static size_t room[MAXDEV];
+    static bool known[MAXDEV];
+    if (dev < 0 || dev >= MAXDEV) return 0;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!known[dev]) {
+        int optin = 0;
+        cudaFuncAttributes fa{};
+        size_t r = 0;
+        if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess &&
+            cudaFuncGetAttributes(&fa, k_small) == cudaSuccess && (size_t)optin > fa.sharedSizeBytes) {
+            r = (size_t)optin - fa.sharedSizeBytes;
+            if (cudaFuncSetAttribute(k_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)r) != cudaSuccess)
+                r = 0;
+        }
+        (void)cudaGetLastError();
+        room[dev] = r;
+        known[dev] = true;
+    }
+    return room[dev];
+}
+
 // Does this plan's LTS take the one-CTA shared-memory path?
 bool small_fits(const bisim_plan_s* p) {
     const bisim_opts& o = p->opts;
     if (o.small < 0 || p->n < 1 || p->A > 32) return false;
     if (o.engine != BISIM_ENGINE_AUTO && o.engine != BISIM_ENGINE_FRONTIER) return false;
     if (o.raw_labels || o.local_states != 0 || o.light_edges != 0 || o.preprocess == 1 || o.test_hook) return false;
-    int dev = 0, optin = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return false;
-    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return false;
-    return small_layout(p->n, p->m).total + 8192 <= (size_t)optin;  // room for the static shared arrays
+    const size_t room = small_smem_room(p->dev);
+    return small_layout(p->n, p->m).total <= room;
 }
 
 int small_refine(bisim_plan_s* p, int32_t* out_block, bisim_stats* stats) {
@@ -3122,7 +3148,6 @@ int small_refine(bisim_plan_s* p, int32_t* out_block, bisim_stats* stats) {
     g.budget = budget_per_warp * (threads / 32);
     BISIM_CUDA_TRY(cudaMemsetAsync(p->small_res.p, 0, 8 * 8, st));
     BISIM_CUDA_TRY(cudaMemsetAsync(&g.ctrl->status, 0, sizeof(int), st));
-    BISIM_CUDA_TRY(cudaFuncSetAttribute(k_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Lo.total));
     BISIM_CUDA_TRY(cudaEventRecord(p->evk0, st));
     k_small<<<1, threads, Lo.total, st>>>(g);
     BISIM_LAUNCHED();

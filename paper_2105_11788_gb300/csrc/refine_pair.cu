@@ -162,6 +162,7 @@ int refine_pair(bisim_plan_s* p, bisim_stats* stats) {
     a.labels = p->labels.as<int32_t>();
     a.in_ptr = p->in_ptr.as<int32_t>();
     a.in_edge = p->in_edge.as<unsigned long long>();
+    BISIM_TRY(ensure_slot_arrays(p));
     a.slot_act = p->slot_act.as<int32_t>();
     a.block = p->block.as<int32_t>();
     a.pmark = p->lmark.as<uint32_t>();
