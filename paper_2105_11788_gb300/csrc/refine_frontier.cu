@@ -1643,20 +1643,30 @@ __device__ void peel_items(const FrontierArgs& a, const Worklist& wl, unsigned l
     }
 }
 
-// What a warp's claim pass keeps in registers for its mark pass when its
-// share of the round is one group of at most 32 items in at most
-// PEEL_CHUNKS chunks with no item of more than 32 transitions: per lane its
-// item, and per chunk the lane's transition, its source's block and flags
-// (the lane of the transition's item, whether the block has several states,
-// whether the touch is exclusive).
+// What a warp's claim pass keeps for its mark pass when its share of the
+// round is one group of at most 32 items in at most PEEL_CARRY_CHUNKS chunks
+// of 32 transitions with no item of more than 32 transitions: per lane its
+// item (registers), and per chunk the lane's transition, its source's block
+// and flags (the lane of the transition's item, whether the block has several
+// states, whether the touch is exclusive) in the warp's slice of shared
+// memory, each lane reading back only what it wrote.
+constexpr int PEEL_CARRY_CHUNKS = 8;
+constexpr int PEEL_CARRY_BYTES = PEEL_CARRY_CHUNKS * 32 * 16;  // per warp
+
 struct PeelCarry {
     int32_t C, deg;
     bool first, pending;  // pending: the item is decided in the mark pass
-    int my_chunk, my_start;
-    unsigned long long e[PEEL_CHUNKS];
-    int32_t b[PEEL_CHUNKS];
-    int fl[PEEL_CHUNKS];  // item lane | 32 (block of several states) | 64 (exclusive touch)
+    int my_chunk, my_start, nchunks;
+    unsigned long long* e;  // [chunk * 32 + lane]
+    int32_t* b;
+    int* fl;                // item lane | 32 (block of several states) | 64 (exclusive touch)
 };
+
+__device__ __forceinline__ void peel_carry_at(PeelCarry& cy, unsigned char* warp_slice) {
+    cy.e = reinterpret_cast<unsigned long long*>(warp_slice);
+    cy.b = reinterpret_cast<int32_t*>(warp_slice + PEEL_CARRY_CHUNKS * 32 * 8);
+    cy.fl = reinterpret_cast<int*>(warp_slice + PEEL_CARRY_CHUNKS * 32 * 12);
+}
 
 // Claim pass of a warp's items [g0, g1) (g1 - g0 <= 32). Returns true (to
 // every lane) when everything the mark pass needs is in `cy`; then the items
@@ -1698,8 +1708,9 @@ __device__ bool peel_claim(const FrontierArgs& a, const Worklist& wl, unsigned l
             cur += d;
         }
     }
-    const int nchunks = cur > 0 ? chunk + 1 : chunk;
-    const bool fits = nchunks <= PEEL_CHUNKS && __ballot_sync(FULL, (int)lane < ng && it.deg > 32) == 0u;
+    const int nchunks = cur > 0 ? chunk + 1 : chunk;  // the same on every lane
+    const bool fits =
+        nchunks <= PEEL_CARRY_CHUNKS && __ballot_sync(FULL, (int)lane < ng && it.deg > 32) == 0u;
     if (!fits) {
         peel_items<0>(a, wl, h0, K0, selC, selP, K1, g0, g1, stamp, nullptr, nullptr, nullptr, nullptr, edges,
                       commits);
@@ -1708,49 +1719,59 @@ __device__ bool peel_claim(const FrontierArgs& a, const Worklist& wl, unsigned l
     cy.C = it.C;
     cy.deg = it.deg;
     cy.first = it.first;
-    bool val[PEEL_CHUNKS];
-    int bb[PEEL_CHUNKS], be[PEEL_CHUNKS];
-#pragma unroll
-    for (int u = 0; u < PEEL_CHUNKS; u++) {
-        const unsigned mc = __ballot_sync(FULL, cy.my_chunk == u);
-        const unsigned starts = __reduce_or_sync(FULL, cy.my_chunk == u ? (1u << cy.my_start) : 0u);
-        const int r = __popc(starts & (0xffffffffu >> (31 - lane))) - 1;
-        const int il = (mc != 0u && r >= 0) ? (int)__fns(mc, 0, r + 1) : 0;
-        const int st = __shfl_sync(FULL, cy.my_start, il);
-        const int dg = __shfl_sync(FULL, it.deg, il);
-        const int d0 = __shfl_sync(FULL, it.d0, il);
-        val[u] = u < nchunks && mc != 0u && r >= 0 && (int)lane < st + dg;
-        cy.fl[u] = il;
-        cy.e[u] = val[u] ? a.in_edge[d0 + (int)lane - st] : 0ull;
-    }
-#pragma unroll
-    for (int u = 0; u < PEEL_CHUNKS; u++) cy.b[u] = val[u] ? ld(&a.block[(int32_t)(cy.e[u] >> 32)]) : 0;
-#pragma unroll
-    for (int u = 0; u < PEEL_CHUNKS; u++) {
-        bb[u] = val[u] ? ld(&a.bbeg[cy.b[u]]) : 0;
-        be[u] = val[u] ? ld(&a.bend[cy.b[u]]) : 0;
-    }
+    cy.nchunks = nchunks;
     bool touched = false;  // item lane: one of its transitions comes from a block of several states
+    for (int u0 = 0; u0 < nchunks; u0 += PEEL_CHUNKS) {
+        bool val[PEEL_CHUNKS];
+        int ils[PEEL_CHUNKS], bb[PEEL_CHUNKS], be[PEEL_CHUNKS];
+        unsigned long long e[PEEL_CHUNKS];
+        int32_t b[PEEL_CHUNKS];
 #pragma unroll
-    for (int u = 0; u < PEEL_CHUNKS; u++) {
-        const int il = cy.fl[u];
-        const int32_t s = (int32_t)(cy.e[u] >> 32);
-        const int32_t b = cy.b[u];
-        const bool ns = val[u] && be[u] - bb[u] > 1;
-        const int32_t C = __shfl_sync(FULL, it.C, il);
-        const bool single = __shfl_sync(FULL, it.single, il);
-        const unsigned long long vb = ns ? ((unsigned long long)il << 32) | (uint32_t)b : ~0ull - lane;
-        const unsigned mb = __match_any_sync(FULL, vb);
-        const unsigned long long vbs = ns ? ((unsigned long long)(uint32_t)b << 32) | (uint32_t)s : ~0ull - lane;
-        const unsigned mbs = __match_any_sync(FULL, vbs) & mb;
-        const bool lead = (__ballot_sync(FULL, ns && s == b) & mb) != 0u;
-        const bool x = !single || mbs != mb || lead;
-        cy.fl[u] = il | (ns ? 32 : 0) | (x ? 64 : 0);
-        if (ns && (mb & lanemask_lt()) == 0u) claim_peel(a, b, peel_key(stamp, C, x), x, stamp);
-        const unsigned nsm = __ballot_sync(FULL, ns);
-        if (cy.my_chunk == u) {
-            const unsigned mine = (it.deg >= 32 ? 0xffffffffu : ((1u << it.deg) - 1u)) << cy.my_start;
-            touched = (nsm & mine) != 0u;
+        for (int k = 0; k < PEEL_CHUNKS; k++) {
+            const int u = u0 + k;
+            const unsigned mc = __ballot_sync(FULL, cy.my_chunk == u);
+            const unsigned starts = __reduce_or_sync(FULL, cy.my_chunk == u ? (1u << cy.my_start) : 0u);
+            const int r = __popc(starts & (0xffffffffu >> (31 - lane))) - 1;
+            const int il = (mc != 0u && r >= 0) ? (int)__fns(mc, 0, r + 1) : 0;
+            const int st = __shfl_sync(FULL, cy.my_start, il);
+            const int dg = __shfl_sync(FULL, it.deg, il);
+            const int d0 = __shfl_sync(FULL, it.d0, il);
+            val[k] = u < nchunks && mc != 0u && r >= 0 && (int)lane < st + dg;
+            ils[k] = il;
+            e[k] = val[k] ? a.in_edge[d0 + (int)lane - st] : 0ull;
+        }
+#pragma unroll
+        for (int k = 0; k < PEEL_CHUNKS; k++) b[k] = val[k] ? ld(&a.block[(int32_t)(e[k] >> 32)]) : 0;
+#pragma unroll
+        for (int k = 0; k < PEEL_CHUNKS; k++) {
+            bb[k] = val[k] ? ld(&a.bbeg[b[k]]) : 0;
+            be[k] = val[k] ? ld(&a.bend[b[k]]) : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < PEEL_CHUNKS; k++) {
+            const int u = u0 + k;
+            const int il = ils[k];
+            const int32_t s = (int32_t)(e[k] >> 32);
+            const bool ns = val[k] && be[k] - bb[k] > 1;
+            const int32_t C = __shfl_sync(FULL, it.C, il);
+            const bool single = __shfl_sync(FULL, it.single, il);
+            const unsigned long long vb = ns ? ((unsigned long long)il << 32) | (uint32_t)b[k] : ~0ull - lane;
+            const unsigned mb = __match_any_sync(FULL, vb);
+            const unsigned long long vbs = ns ? ((unsigned long long)(uint32_t)b[k] << 32) | (uint32_t)s : ~0ull - lane;
+            const unsigned mbs = __match_any_sync(FULL, vbs) & mb;
+            const bool lead = (__ballot_sync(FULL, ns && s == b[k]) & mb) != 0u;
+            const bool x = !single || mbs != mb || lead;
+            if (u < nchunks) {
+                cy.e[u * 32 + lane] = e[k];
+                cy.b[u * 32 + lane] = b[k];
+                cy.fl[u * 32 + lane] = il | (ns ? 32 : 0) | (x ? 64 : 0);
+            }
+            if (ns && (mb & lanemask_lt()) == 0u) claim_peel(a, b[k], peel_key(stamp, C, x), x, stamp);
+            const unsigned nsm = __ballot_sync(FULL, ns);
+            if (cy.my_chunk == u) {
+                const unsigned mine = (it.deg >= 32 ? 0xffffffffu : ((1u << it.deg) - 1u)) << cy.my_start;
+                touched = (nsm & mine) != 0u;
+            }
         }
     }
     cy.pending = false;
@@ -1769,44 +1790,61 @@ __device__ bool peel_claim(const FrontierArgs& a, const Worklist& wl, unsigned l
     return true;
 }
 
-// Mark pass from the claim pass's registers (the block ranges are read again
+// Mark pass from what the claim pass kept (the block ranges are read again
 // for the few transitions from blocks of several states).
 __device__ void peel_mark_carried(const FrontierArgs& a, const Worklist& wl, uint32_t stamp, const PeelCarry& cy,
                                   int* n_small, int* n_mid, int4* small_list, int4* mid_list, long long& edges,
                                   long long& commits) {
     const unsigned FULL = 0xffffffffu;
+    const unsigned lane = threadIdx.x & 31u;
     if (__ballot_sync(FULL, cy.pending) == 0u) return;
     const bool lost_x = cy.pending && ld_volatile_u32(&a.lostl[cy.C]) == stamp;
     bool lost_p = false;
+    for (int u0 = 0; u0 < cy.nchunks; u0 += PEEL_CHUNKS) {
+        int fl[PEEL_CHUNKS];
+        int32_t b[PEEL_CHUNKS];
+        bool ns[PEEL_CHUNKS], lp[PEEL_CHUNKS];
 #pragma unroll
-    for (int u = 0; u < PEEL_CHUNKS; u++) {
-        const int il = cy.fl[u] & 31;
-        const bool pend = __shfl_sync(FULL, cy.pending, il);
-        const bool ns = pend && (cy.fl[u] & 32);
-        const bool x = cy.fl[u] & 64;
-        const int32_t b = cy.b[u];
-        const bool lp = ns && !x && ld_volatile_u64(&a.minx[b]) == ld_volatile_u64(&a.claim[b]);
-        const unsigned lpm = __ballot_sync(FULL, lp);
-        const int st = __shfl_sync(FULL, cy.my_start, il);
-        const int dg = __shfl_sync(FULL, cy.deg, il);
-        const int32_t C = __shfl_sync(FULL, cy.C, il);
-        const unsigned range = (dg >= 32 ? 0xffffffffu : ((1u << dg) - 1u)) << st;
-        const bool lose = __shfl_sync(FULL, lost_x, il) || (lpm & range) != 0u;
-        if (cy.my_chunk == u) {
-            const unsigned mine = (cy.deg >= 32 ? 0xffffffffu : ((1u << cy.deg) - 1u)) << cy.my_start;
-            lost_p = (lpm & mine) != 0u;
+        for (int k = 0; k < PEEL_CHUNKS; k++) {
+            const int u = u0 + k;
+            fl[k] = u < cy.nchunks ? cy.fl[u * 32 + lane] : 0;
+            b[k] = u < cy.nchunks ? cy.b[u * 32 + lane] : 0;
         }
-        if (ns && !lose) {
-            const int32_t s = (int32_t)(cy.e[u] >> 32);
-            const int32_t bb = ld(&a.bbeg[b]), be = ld(&a.bend[b]);
-            if (x) {
-                a.mark[(uint32_t)cy.e[u]] = stamp;
-                if (atomicExch(&a.smark[s], stamp) != stamp)
-                    rank_marked(a, s, b, bb, be, C, n_small, n_mid, small_list, mid_list, 0);
-            } else {
-                const unsigned long long pk = ((unsigned long long)(~stamp) << 32) | (uint32_t)C;
-                const unsigned long long old = atomicMin(&a.smark64[s], pk);
-                if ((old >> 32) != (pk >> 32)) rank_marked(a, s, b, bb, be, C, n_small, n_mid, small_list, mid_list, 1);
+#pragma unroll
+        for (int k = 0; k < PEEL_CHUNKS; k++) {
+            const bool pend = __shfl_sync(FULL, cy.pending, fl[k] & 31);
+            ns[k] = u0 + k < cy.nchunks && pend && (fl[k] & 32);
+            lp[k] = ns[k] && !(fl[k] & 64) && ld_volatile_u64(&a.minx[b[k]]) == ld_volatile_u64(&a.claim[b[k]]);
+        }
+#pragma unroll
+        for (int k = 0; k < PEEL_CHUNKS; k++) {
+            const int u = u0 + k;
+            const int il = fl[k] & 31;
+            const bool x = fl[k] & 64;
+            const unsigned lpm = __ballot_sync(FULL, lp[k]);
+            const int st = __shfl_sync(FULL, cy.my_start, il);
+            const int dg = __shfl_sync(FULL, cy.deg, il);
+            const int32_t C = __shfl_sync(FULL, cy.C, il);
+            const unsigned range = (dg >= 32 ? 0xffffffffu : ((1u << dg) - 1u)) << st;
+            const bool lose = __shfl_sync(FULL, lost_x, il) || (lpm & range) != 0u;
+            if (cy.my_chunk == u) {
+                const unsigned mine = (cy.deg >= 32 ? 0xffffffffu : ((1u << cy.deg) - 1u)) << cy.my_start;
+                lost_p = (lpm & mine) != 0u;
+            }
+            if (ns[k] && !lose) {
+                const unsigned long long e = cy.e[u * 32 + lane];
+                const int32_t s = (int32_t)(e >> 32);
+                const int32_t bb = ld(&a.bbeg[b[k]]), be = ld(&a.bend[b[k]]);
+                if (x) {
+                    a.mark[(uint32_t)e] = stamp;
+                    if (atomicExch(&a.smark[s], stamp) != stamp)
+                        rank_marked(a, s, b[k], bb, be, C, n_small, n_mid, small_list, mid_list, 0);
+                } else {
+                    const unsigned long long pk = ((unsigned long long)(~stamp) << 32) | (uint32_t)C;
+                    const unsigned long long old = atomicMin(&a.smark64[s], pk);
+                    if ((old >> 32) != (pk >> 32))
+                        rank_marked(a, s, b[k], bb, be, C, n_small, n_mid, small_list, mid_list, 1);
+                }
             }
         }
     }
@@ -1835,13 +1873,14 @@ __device__ __forceinline__ bool peel_round(const FrontierArgs& a, const Worklist
                                            unsigned long long h0, uint32_t stamp, int64_t gw, int64_t nwarps,
                                            int* n_small, int* n_mid, int4* small_list, int4* mid_list, int cta,
                                            int ncta, long long& edges, long long& states, long long& commits,
-                                           Sync sync) {
+                                           unsigned char* carry, Sync sync) {
     const int64_t I = (int64_t)K0 + selP[K1];
     const int64_t per = (I + nwarps - 1) / nwarps;
     const int64_t i0 = gw * per, i1 = min(I, i0 + per);
     if (per <= 32) {
-        // one group per warp: the claim pass's loads stay in registers
+        // one group per warp: what the claim pass loaded is kept for the mark pass
         PeelCarry cy;
+        peel_carry_at(cy, carry);
         const bool carried =
             i0 < i1 && peel_claim(a, wl, h0, K0, selC, selP, K1, i0, i1, stamp, cy, edges, commits);
         PHASE(2);
@@ -1890,6 +1929,13 @@ __device__ __forceinline__ bool peel_round(const FrontierArgs& a, const Worklist
 // CTA's wait is bounded by timeout_ns without progress, where progress is a
 // new command or a new heartbeat from CTA 0. The touched-block counters of
 // grid rounds alternate by round parity; CTA 0 clears the next round's pair.
+// Dynamic shared memory of the hybrid kernel: the selection (kmax + 32
+// labels and kmax + 33 offsets), then, with peel rounds, PEEL_CARRY_BYTES per
+// warp.
+__host__ __device__ inline size_t peel_carry_offset(int kmax) {
+    return (sizeof(int32_t) * (2 * ((size_t)kmax + 32) + 1) + 7) / 8 * 8;
+}
+
 template <int MAXT>  // most threads per CTA (sets the register budget)
 __global__ void __launch_bounds__(MAXT, 1) k_frontier_hybrid(FrontierArgs a, HybridArgs h) {
     __shared__ CtaShared sh;
@@ -1905,6 +1951,8 @@ __global__ void __launch_bounds__(MAXT, 1) k_frontier_hybrid(FrontierArgs a, Hyb
     // kmax labels plus 32 for the singletons a CTA-0 round of a peel selection appends
     int32_t* s_selC = s_dyn;
     int32_t* s_selP = s_dyn + kmax + 32;
+    // peel rounds: each warp's claim-pass carry, after the selection (8-byte aligned)
+    unsigned char* s_carry = reinterpret_cast<unsigned char*>(s_dyn) + peel_carry_offset(kmax);
     const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
     const int32_t n = a.n;
@@ -1929,7 +1977,8 @@ __global__ void __launch_bounds__(MAXT, 1) k_frontier_hybrid(FrontierArgs a, Hyb
         int* nm = &c->n_mid[par];
         if (peel_now && K + K0 > 1)
             return peel_round(a, wl, sh, s_defer, &s_ndefer, s_selC, s_selP, K, K0, h0, stamp, gw, nwarps, ns, nm,
-                              a.tlist, a.tlist + n, (int)blockIdx.x, (int)gridDim.x, edges, states, commits, gsync);
+                              a.tlist, a.tlist + n, (int)blockIdx.x, (int)gridDim.x, edges, states, commits,
+                              s_carry + wid * PEEL_CARRY_BYTES, gsync);
         if (K > 1)
             return multi_round(a, wl, sh, s_defer, &s_ndefer, s_selC, s_selP, K, h.g_lost, stamp, gw, nwarps, ns, nm,
                                a.tlist, a.tlist + n, (int)blockIdx.x, (int)gridDim.x, edges, states, commits, gsync);
@@ -2974,12 +3023,13 @@ int refine_frontier(bisim_plan_s* p, bisim_stats* stats) {
         const int per_warp = p->opts.split_budget > 0 ? p->opts.split_budget : 1;
         h.budget = (int)std::min<int64_t>((int64_t)per_warp * g * (threads / 32), 1 << 30);
         h.peel = p->opts.peel >= 0 && h.kmax > 1 ? 1 : 0;
-        const int peel_items = p->opts.peel_items > 0 ? std::min(p->opts.peel_items, 1 << 12) : 8;
+        const int peel_items = p->opts.peel_items > 0 ? std::min(p->opts.peel_items, 1 << 12) : 16;
         int64_t cap0 = (int64_t)peel_items * g * (threads / 32);
         if (p->opts.splitters > 0) cap0 = std::min<int64_t>(cap0, p->opts.splitters);
         h.cap0 = (int)std::min<int64_t>(cap0, 1 << 30);
-        BISIM_TRY(launch_persistent(fn, args, threads, p, &grid, 1,
-                                    sizeof(int32_t) * (2 * ((size_t)h.kmax + 32) + 1)));
+        const size_t dyn = h.peel ? peel_carry_offset(h.kmax) + (size_t)(threads / 32) * PEEL_CARRY_BYTES
+                                  : sizeof(int32_t) * (2 * ((size_t)h.kmax + 32) + 1);
+        BISIM_TRY(launch_persistent(fn, args, threads, p, &grid, 1, dyn));
     }
     BISIM_TRY(read_ctrl(p));
     p->stamp = base + (uint32_t)std::min<long long>(done + p->ctrl_h->rounds + 1, cap + 1);

@@ -373,8 +373,9 @@ def _hub_lts(seed, n, hubs, hub_deg, deg=6, num_act=2):
                        dst[perm].astype(np.int32), init)
 
 
-@pytest.mark.parametrize("peel,items", [(0, 0), (0, 1), (0, 64), (-1, 0)],
-                         ids=["default", "one-per-warp", "64-per-warp", "exclusive-only"])
+@pytest.mark.parametrize("peel,items", [(0, 0), (0, 1), (0, 8), (0, 24), (0, 64), (-1, 0)],
+                         ids=["default", "one-per-warp", "8-per-warp", "24-per-warp", "64-per-warp",
+                              "exclusive-only"])
 def test_peel_rounds(peel, items):
     """Grid rounds where several splitters of one state may split the same
     block (each marking one member of it, not its leader): the oracle's
