@@ -42,6 +42,7 @@ struct bisim_ctrl {
     int cmd_K0;                          // how many
     int cmd_peel;                        // 1: the published round is a peel round
     unsigned long long cmd_h0;           // ring-0 head before them
+    int n_defer[2];                      // hybrid sweep rounds: labels pushed back untouched, by round parity
 };
 
 // Most splitters one multi-splitter round takes: grid rounds of the hybrid

@@ -31,10 +31,14 @@
 // barrier, split, barrier (see the section on rounds with several splitters
 // below). Rounds run on the whole grid, on CTA 0 alone (light rounds of the
 // hybrid schedule) or on the CTA that owns an LTS of a batch.
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <mutex>
 
 #include "plan.cuh"
+
+namespace cg = cooperative_groups;
 
 using namespace bisim;
 
@@ -179,6 +183,18 @@ __device__ __forceinline__ int size_bucket(int32_t sz) { return 31 - __clz(max(s
 // entries, bucket k at queue[k * stride + base ...]. `tail` holds the pushes
 // per bucket; it lives in global memory for the grid engine (every CTA pops)
 // and in shared memory for the CTA-per-instance engine.
+// Pushes of one CTA collected in shared memory during a split step and
+// appended to the rings at its end with one global atomic per ring
+// (flush_pushes); a push that finds the buffer full goes to its ring at once.
+constexpr int PUSH_BUF = 4096;
+struct PushBuf {
+    int n;  // pushes so far (may pass PUSH_BUF; the rest went to the rings)
+    unsigned cnt[BISIM_BUCKETS];
+    unsigned long long base[BISIM_BUCKETS];
+    int32_t lab[PUSH_BUF];
+    uint8_t bk[PUSH_BUF];
+};
+
 struct Worklist {
     unsigned long long* tail;
     int32_t* queue;
@@ -186,13 +202,50 @@ struct Worklist {
     int32_t base;
     int32_t cap;
     int nbk = BISIM_BUCKETS;  // rings in use: larger blocks share the last one
+    PushBuf* buf = nullptr;   // this CTA's push buffer, if any
 };
+
+__device__ __forceinline__ void push_ring(const Worklist& wl, int32_t label, int bk) {
+    if (wl.buf) {
+        const int i = atomicAdd(&wl.buf->n, 1);
+        if (i < PUSH_BUF) {
+            wl.buf->lab[i] = label;
+            wl.buf->bk[i] = (uint8_t)bk;
+            return;
+        }
+    }
+    const unsigned long long pos = atomicAdd(&wl.tail[bk], 1ull);
+    wl.queue[(size_t)bk * wl.stride + wl.base + pos % (unsigned long long)wl.cap] = label;
+}
 
 // append a label whose block has `size` states to the FIFO ring of its size bucket
 __device__ __forceinline__ void push_sized(const Worklist& wl, int32_t label, int32_t size) {
-    const int bk = min(size_bucket(size), wl.nbk - 1);
-    const unsigned long long pos = atomicAdd(&wl.tail[bk], 1ull);
-    wl.queue[(size_t)bk * wl.stride + wl.base + pos % (unsigned long long)wl.cap] = label;
+    push_ring(wl, label, min(size_bucket(size), wl.nbk - 1));
+}
+
+// Append a CTA's buffered pushes to the rings (the whole CTA calls, after a
+// __syncthreads that follows the last push); the buffer is empty afterwards.
+__device__ void flush_pushes(const Worklist& wl) {
+    PushBuf* pb = wl.buf;
+    const int n = min(pb->n, PUSH_BUF);
+    if (threadIdx.x < BISIM_BUCKETS) pb->cnt[threadIdx.x] = 0u;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&pb->cnt[pb->bk[i]], 1u);
+    __syncthreads();
+    if (threadIdx.x < BISIM_BUCKETS) {
+        const unsigned c = pb->cnt[threadIdx.x];
+        pb->base[threadIdx.x] = c ? atomicAdd(&wl.tail[threadIdx.x], (unsigned long long)c) : 0ull;
+        pb->cnt[threadIdx.x] = 0u;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int bk = pb->bk[i];
+        const unsigned long long pos = pb->base[bk] + atomicAdd(&pb->cnt[bk], 1u);
+        wl.queue[(size_t)bk * wl.stride + wl.base + pos % (unsigned long long)wl.cap] = pb->lab[i];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) pb->n = 0;
+    __syncthreads();
 }
 
 __device__ __forceinline__ void push(const FrontierArgs& a, const Worklist& wl, int32_t label) {
@@ -642,6 +695,10 @@ __device__ __forceinline__ void set_unstable_warp(const FrontierArgs& a, const W
         if (size < 0) size = ld(&a.bend[label]) - ld(&a.bbeg[label]);
         bk = min(size_bucket(size), wl.nbk - 1);
     }
+    if (wl.buf) {
+        if (need) push_ring(wl, label, bk);
+        return;
+    }
     const unsigned peers = __match_any_sync(0xffffffffu, bk);
     const int first = __ffs(peers) - 1;
     unsigned long long pos = 0;
@@ -837,10 +894,16 @@ __device__ __forceinline__ void rank_marked(const FrontierArgs& a, int32_t s, in
     a.mscr[be - 1 - rk] = s;
     if (rk == 0) {
         if (Cw >= 0) a.bspl[b] = Cw;
-        if (be - bb <= WARP_MAX)
-            small_list[atomicAdd(n_small, 1)] = make_int4(b, bb, be, mode);
-        else
-            mid_list[atomicAdd(n_mid, 1)] = make_int4(b, bb, be, mode);
+        // the lanes here that list a block into the same list take their
+        // entries with one atomic (the list lengths are one word each for the
+        // whole grid)
+        const bool small = be - bb <= WARP_MAX;
+        const cg::coalesced_group g = cg::coalesced_threads();
+        const cg::coalesced_group part = cg::labeled_partition(g, small ? 1 : 0);
+        int base = 0;
+        if (part.thread_rank() == 0) base = atomicAdd(small ? n_small : n_mid, (int)part.size());
+        base = part.shfl(base, 0) + (int)part.thread_rank();
+        (small ? small_list : mid_list)[base] = make_int4(b, bb, be, mode);
     }
 }
 
@@ -1307,8 +1370,14 @@ __device__ __forceinline__ bool multi_round(const FrontierArgs& a, const Worklis
 // iterations. The splitters of one state come by position from the ring of
 // size bucket 0, so a round may take tens of thousands of them.
 
-constexpr int PEEL_CHUNKS = 4;  // chunks of 32 transitions a warp loads at once
-constexpr int PEEL_MIN_SINGLES = 256;  // a peel round needs this many labels in size bucket 0
+#ifndef BISIM_PEEL_CHUNKS
+#define BISIM_PEEL_CHUNKS 4
+#endif
+constexpr int PEEL_CHUNKS = BISIM_PEEL_CHUNKS;  // chunks of 32 transitions a warp loads at once
+constexpr int PEEL_MIN_SINGLES = 256;
+constexpr int PEEL_QUIET = 32;             // a peel round is quiet below one touched block per 32 splitters
+constexpr int PEEL_SWEEP_GROWTH = 4;
+constexpr int PEEL_SWEEP_MAX = 1 << 24;  // a peel round needs this many labels in size bucket 0
 
 __device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long* p) {
     return *(volatile const unsigned long long*)p;
@@ -1341,8 +1410,35 @@ __device__ __forceinline__ void claim_peel(const FrontierArgs& a, int32_t b, uns
 constexpr int PEEL_SEL_E = 16;  // listed labels per thread of a peel selection at most
 
 __device__ int select_peel(const FrontierArgs& a, const Worklist& wl, unsigned long long* head, CtaShared& sh,
-                           int32_t* selC, int32_t* selP, int kmax1, int32_t budget1, int cap0) {
+                           int32_t* selC, int32_t* selP, int kmax1, int32_t budget1, int cap0, bool sweep) {
     const unsigned lane = threadIdx.x & 31u;
+    if (sweep) {
+        // sweep round: up to cap0 labels by position from the rings, lowest
+        // bucket first, nothing listed; ring b's run starts at ring position
+        // hp[b], holds bn[b] labels and is items [bx[b], bx[b] + bn[b])
+        if (threadIdx.x < 32) {
+            const unsigned long long h = head[lane];
+            const unsigned long long t = *(volatile const unsigned long long*)&wl.tail[lane];
+            const long long av = (long long)(t - h);
+            long long x = av;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const long long y = __shfl_up_sync(0xffffffffu, x, o);
+                if ((int)lane >= o) x += y;
+            }
+            const long long ex = x - av;
+            const int take = (int)max(0ll, min(av, (long long)cap0 - ex));
+            sh.bx[lane] = (int)min(ex, (long long)cap0);
+            sh.bn[lane] = take;
+            sh.hp[lane] = (int)(h % (unsigned long long)wl.cap);
+            head[lane] = h + (unsigned long long)take;
+            if (lane == 31) sh.k0 = (int)min(x, (long long)cap0);
+            if (lane == 0) sh.h0 = h;
+        }
+        if (threadIdx.x == 0) selP[0] = 0;
+        __syncthreads();
+        return 0;
+    }
     kmax1 = min(kmax1, PEEL_SEL_E * (int)blockDim.x);
     if (threadIdx.x < 32) {
         const unsigned long long h = head[lane];
@@ -1446,17 +1542,36 @@ struct PeelItem {
     int32_t C, t, d0, deg;
     bool first;   // the first member of its splitter
     bool single;  // the splitter has one state
+    bool defer;   // sweep rounds: a label whose block has several states, pushed back untouched
 };
 
 __device__ __forceinline__ PeelItem peel_item(const FrontierArgs& a, const Worklist& wl, unsigned long long h0,
-                                              int K0, const int32_t* selC, const int32_t* selP, int K1,
-                                              int64_t item) {
+                                              const CtaShared* sw, int K0, const int32_t* selC,
+                                              const int32_t* selP, int K1, int64_t item) {
     PeelItem it;
+    it.defer = false;
     if (item < K0) {
-        it.C = ld(&wl.queue[wl.base + (h0 + (unsigned long long)item) % (unsigned long long)wl.cap]);
-        it.t = it.C;
+        int bk = 0;
+        unsigned long long pos;
+        if (sw) {
+            // sweep round: entry (item - bx[bk]) of ring bk's taken run
+            const int i = (int)item;
+            while (i >= sw->bx[bk] + sw->bn[bk]) bk++;
+            pos = (unsigned long long)sw->hp[bk] + (unsigned long long)(i - sw->bx[bk]);
+            if (pos >= (unsigned long long)wl.cap) pos -= (unsigned long long)wl.cap;
+        } else {
+            pos = (h0 + (unsigned long long)item) % (unsigned long long)wl.cap;
+        }
+        it.C = ld(&wl.queue[(size_t)bk * wl.stride + wl.base + pos]);
+        it.t = it.C;  // the label of a block of one state is that state
         it.first = true;
         it.single = true;
+        if (bk > 0 && ld(&a.bend[it.C]) - ld(&a.bbeg[it.C]) != 1) {
+            it.defer = true;
+            it.d0 = 0;
+            it.deg = 0;
+            return it;
+        }
     } else {
         const int32_t i = (int32_t)(item - K0);
         const int j = find_sel(selP, K1, i);
@@ -1483,10 +1598,10 @@ struct PeelEdge {
 // (so one ballot sees all of an item's transitions); larger ones are walked
 // by the whole warp afterwards and touch exclusively.
 template <int PASS>
-__device__ void peel_items(const FrontierArgs& a, const Worklist& wl, unsigned long long h0, int K0,
-                           const int32_t* selC, const int32_t* selP, int K1, int64_t g0, int64_t g1,
+__device__ void peel_items(const FrontierArgs& a, const Worklist& wl, unsigned long long h0, const CtaShared* sw,
+                           int K0, const int32_t* selC, const int32_t* selP, int K1, int64_t g0, int64_t g1,
                            uint32_t stamp, int* n_small, int* n_mid, int4* small_list, int4* mid_list,
-                           long long& edges, long long& commits) {
+                           int* n_defer, long long& edges, long long& commits) {
     const unsigned lane = threadIdx.x & 31u;
     const unsigned FULL = 0xffffffffu;
     const int ng = (int)(g1 - g0);
@@ -1495,9 +1610,17 @@ __device__ void peel_items(const FrontierArgs& a, const Worklist& wl, unsigned l
     it.deg = 0;
     it.single = true;
     it.first = false;
+    it.defer = false;
     it.t = 0;
     it.d0 = 0;
-    if ((int)lane < ng) it = peel_item(a, wl, h0, K0, selC, selP, K1, g0 + lane);
+    if ((int)lane < ng) it = peel_item(a, wl, h0, sw, K0, selC, selP, K1, g0 + lane);
+    // pass 1: an item of one state that pass 0 carried out already (it touched
+    // no block of several states) is done
+    bool done = false;
+    if (PASS == 1 && (int)lane < ng && it.single && !it.defer && ld(&a.unstable[it.C]) == 0u) {
+        done = true;
+        it.deg = 0;
+    }
     // pass 1: exclusive losses recorded by the claims
     bool lost_x = false;
     if (PASS == 1 && (int)lane < ng) lost_x = ld_volatile_u32(&a.lostl[it.C]) == stamp;
@@ -1522,8 +1645,9 @@ __device__ void peel_items(const FrontierArgs& a, const Worklist& wl, unsigned l
         }
         nchunks = cur > 0 ? chunk + 1 : chunk;
     }
-    // pass 1: the item's loss as seen from its peel touches (filled per chunk)
-    bool lost_p = false;
+    // pass 1: the item's loss as seen from its peel touches (filled per chunk);
+    // pass 0: whether one of its transitions comes from a block of several states
+    bool lost_p = false, touched = false;
     for (int c0 = 0; c0 < nchunks; c0 += PEEL_CHUNKS) {
         PeelEdge ed[PEEL_CHUNKS];
         int src_lane[PEEL_CHUNKS];
@@ -1568,6 +1692,11 @@ __device__ void peel_items(const FrontierArgs& a, const Worklist& wl, unsigned l
             const bool x = !single || mbs != mb || lead;
             if (PASS == 0) {
                 if (ns && (mb & lanemask_lt()) == 0u) claim_peel(a, b, peel_key(stamp, C, x), x, stamp);
+                const unsigned nsm = __ballot_sync(FULL, ns);
+                if (my_chunk == c0 + u) {
+                    const unsigned mine = (it.deg >= 32 ? 0xffffffffu : ((1u << it.deg) - 1u)) << my_start;
+                    touched = (nsm & mine) != 0u;
+                }
             } else {
                 // a peel touch of a block whose least touch is exclusive: this splitter loses
                 const bool lp = ns && !x && ld_volatile_u64(&a.minx[b]) == ld_volatile_u64(&a.claim[b]);
@@ -1605,6 +1734,7 @@ __device__ void peel_items(const FrontierArgs& a, const Worklist& wl, unsigned l
         const int32_t d0 = __shfl_sync(FULL, it.d0, il);
         const int32_t dg = __shfl_sync(FULL, it.deg, il);
         const bool lose = PASS == 1 && __shfl_sync(FULL, lost_x, il);
+        bool tb = false;
         for (int32_t q0 = 0; q0 < dg; q0 += 32) {
             const bool v = q0 + (int32_t)lane < dg;
             const unsigned long long e = v ? a.in_edge[d0 + q0 + (int32_t)lane] : 0ull;
@@ -1612,6 +1742,7 @@ __device__ void peel_items(const FrontierArgs& a, const Worklist& wl, unsigned l
             const int32_t b = v ? ld(&a.block[s]) : 0;
             const int32_t bb = v ? ld(&a.bbeg[b]) : 0, be = v ? ld(&a.bend[b]) : 0;
             const bool ns = v && be - bb > 1;
+            tb |= __any_sync(FULL, ns);
             if (PASS == 0) {
                 const unsigned mb = __match_any_sync(FULL, ns ? b : -1 - (int)lane);
                 if (ns && (mb & lanemask_lt()) == 0u) claim_peel(a, b, peel_key(stamp, C, true), true, stamp);
@@ -1621,14 +1752,28 @@ __device__ void peel_items(const FrontierArgs& a, const Worklist& wl, unsigned l
                     rank_marked(a, s, b, bb, be, C, n_small, n_mid, small_list, mid_list, 0);
             }
         }
-        if ((int)lane == il) lost_p = lost_x;
+        if ((int)lane == il) {
+            lost_p = lost_x;
+            touched = tb;
+        }
     }
-    if ((int)lane < ng) {
+    if (PASS == 0 && n_defer) {
+        const unsigned dm = __ballot_sync(FULL, (int)lane < ng && it.defer);
+        if (dm != 0u && lane == 0) atomicAdd(n_defer, __popc(dm));
+    }
+    if ((int)lane < ng && !done) {
         if (PASS == 0) {
             // a splitter of several states claims its own block
             if (it.first && !it.single) claim_peel(a, it.C, peel_key(stamp, it.C, true), true, stamp);
+            if (it.single && !touched && !it.defer) {
+                // nothing to claim, nothing to mark: this iteration is carried out now
+                a.unstable[it.C] = 0u;
+                commits++;
+                edges += it.deg;
+                TRACE_WIN();
+            }
         } else {
-            const bool lose = lost_x || lost_p;
+            const bool lose = lost_x || lost_p || it.defer;
             if (it.first) {
                 if (lose) {
                     push(a, wl, it.C);
@@ -1656,6 +1801,7 @@ constexpr int PEEL_CARRY_BYTES = PEEL_CARRY_CHUNKS * 32 * 16;  // per warp
 struct PeelCarry {
     int32_t C, deg;
     bool first, pending;  // pending: the item is decided in the mark pass
+    bool defer;           // pushed back untouched (sweep rounds)
     int my_chunk, my_start, nchunks;
     unsigned long long* e;  // [chunk * 32 + lane]
     int32_t* b;
@@ -1674,9 +1820,9 @@ __device__ __forceinline__ void peel_carry_at(PeelCarry& cy, unsigned char* warp
 // already (they claim nothing, so they cannot lose, and they mark nothing).
 // Otherwise the claims are made by peel_items<0> and the mark pass must
 // recompute.
-__device__ bool peel_claim(const FrontierArgs& a, const Worklist& wl, unsigned long long h0, int K0,
-                           const int32_t* selC, const int32_t* selP, int K1, int64_t g0, int64_t g1, uint32_t stamp,
-                           PeelCarry& cy, long long& edges, long long& commits) {
+__device__ bool peel_claim(const FrontierArgs& a, const Worklist& wl, unsigned long long h0, const CtaShared* sw,
+                           int K0, const int32_t* selC, const int32_t* selP, int K1, int64_t g0, int64_t g1,
+                           uint32_t stamp, PeelCarry& cy, int* n_defer, long long& edges, long long& commits) {
     const unsigned lane = threadIdx.x & 31u;
     const unsigned FULL = 0xffffffffu;
     const int ng = (int)(g1 - g0);
@@ -1685,9 +1831,10 @@ __device__ bool peel_claim(const FrontierArgs& a, const Worklist& wl, unsigned l
     it.deg = 0;
     it.single = true;
     it.first = false;
+    it.defer = false;
     it.t = 0;
     it.d0 = 0;
-    if ((int)lane < ng) it = peel_item(a, wl, h0, K0, selC, selP, K1, g0 + lane);
+    if ((int)lane < ng) it = peel_item(a, wl, h0, sw, K0, selC, selP, K1, g0 + lane);
     const bool packable = (int)lane < ng && it.deg > 0 && it.deg <= 32;
     int cur = 0, chunk = 0;
     cy.my_chunk = -1;
@@ -1712,13 +1859,18 @@ __device__ bool peel_claim(const FrontierArgs& a, const Worklist& wl, unsigned l
     const bool fits =
         nchunks <= PEEL_CARRY_CHUNKS && __ballot_sync(FULL, (int)lane < ng && it.deg > 32) == 0u;
     if (!fits) {
-        peel_items<0>(a, wl, h0, K0, selC, selP, K1, g0, g1, stamp, nullptr, nullptr, nullptr, nullptr, edges,
-                      commits);
+        peel_items<0>(a, wl, h0, sw, K0, selC, selP, K1, g0, g1, stamp, nullptr, nullptr, nullptr, nullptr, n_defer,
+                      edges, commits);
         return false;
+    }
+    if (n_defer) {
+        const unsigned dm = __ballot_sync(FULL, (int)lane < ng && it.defer);
+        if (dm != 0u && lane == 0) atomicAdd(n_defer, __popc(dm));
     }
     cy.C = it.C;
     cy.deg = it.deg;
     cy.first = it.first;
+    cy.defer = it.defer;
     cy.nchunks = nchunks;
     bool touched = false;  // item lane: one of its transitions comes from a block of several states
     for (int u0 = 0; u0 < nchunks; u0 += PEEL_CHUNKS) {
@@ -1777,7 +1929,7 @@ __device__ bool peel_claim(const FrontierArgs& a, const Worklist& wl, unsigned l
     cy.pending = false;
     if ((int)lane < ng) {
         if (it.first && !it.single) claim_peel(a, it.C, peel_key(stamp, it.C, true), true, stamp);
-        if (it.single && !touched) {
+        if (it.single && !touched && !it.defer) {
             // nothing to claim, nothing to mark: this iteration is carried out now
             a.unstable[it.C] = 0u;
             commits++;
@@ -1849,7 +2001,7 @@ __device__ void peel_mark_carried(const FrontierArgs& a, const Worklist& wl, uin
         }
     }
     if (cy.pending) {
-        const bool lose = lost_x || lost_p;
+        const bool lose = lost_x || lost_p || cy.defer;
         if (cy.first) {
             if (lose) {
                 push(a, wl, cy.C);
@@ -1865,15 +2017,19 @@ __device__ void peel_mark_carried(const FrontierArgs& a, const Worklist& wl, uin
 
 // A peel round on the whole grid: claim pass, barrier, mark pass, barrier,
 // split step, barrier. The items (members of the round's splitters: K0 of
-// one state from the ring of bucket 0, then the members of the K1 listed
-// ones) are cut into one contiguous share per warp.
+// one state from the ring of bucket 0 - in a sweep round, `sweep`, the runs
+// select_peel took from every ring, whose labels of blocks of several states
+// are pushed back untouched and counted in n_defer - then the members of the
+// K1 listed ones) are cut into one contiguous share per warp.
 template <typename Sync>
 __device__ __forceinline__ bool peel_round(const FrontierArgs& a, const Worklist& wl, CtaShared& sh, int* defer,
                                            int* ndefer, const int32_t* selC, const int32_t* selP, int K1, int K0,
                                            unsigned long long h0, uint32_t stamp, int64_t gw, int64_t nwarps,
                                            int* n_small, int* n_mid, int4* small_list, int4* mid_list, int cta,
                                            int ncta, long long& edges, long long& states, long long& commits,
-                                           unsigned char* carry, Sync sync) {
+                                           unsigned char* carry, PushBuf* pbuf, bool sweep, int* n_defer,
+                                           int& touched, Sync sync) {
+    const CtaShared* sw = sweep ? &sh : nullptr;
     const int64_t I = (int64_t)K0 + selP[K1];
     const int64_t per = (I + nwarps - 1) / nwarps;
     const int64_t i0 = gw * per, i1 = min(I, i0 + per);
@@ -1882,33 +2038,40 @@ __device__ __forceinline__ bool peel_round(const FrontierArgs& a, const Worklist
         PeelCarry cy;
         peel_carry_at(cy, carry);
         const bool carried =
-            i0 < i1 && peel_claim(a, wl, h0, K0, selC, selP, K1, i0, i1, stamp, cy, edges, commits);
+            i0 < i1 && peel_claim(a, wl, h0, sw, K0, selC, selP, K1, i0, i1, stamp, cy, n_defer, edges, commits);
         PHASE(2);
         if (!sync()) return false;
         PHASE(3);
         if (carried)
             peel_mark_carried(a, wl, stamp, cy, n_small, n_mid, small_list, mid_list, edges, commits);
         else if (i0 < i1)
-            peel_items<1>(a, wl, h0, K0, selC, selP, K1, i0, i1, stamp, n_small, n_mid, small_list, mid_list,
-                          edges, commits);
+            peel_items<1>(a, wl, h0, sw, K0, selC, selP, K1, i0, i1, stamp, n_small, n_mid, small_list, mid_list,
+                          nullptr, edges, commits);
     } else {
         for (int64_t g = i0; g < i1; g += 32)
-            peel_items<0>(a, wl, h0, K0, selC, selP, K1, g, min(i1, g + 32), stamp, n_small, n_mid, small_list,
-                          mid_list, edges, commits);
+            peel_items<0>(a, wl, h0, sw, K0, selC, selP, K1, g, min(i1, g + 32), stamp, n_small, n_mid,
+                          small_list, mid_list, n_defer, edges, commits);
         PHASE(2);
         if (!sync()) return false;
         PHASE(3);
         for (int64_t g = i0; g < i1; g += 32)
-            peel_items<1>(a, wl, h0, K0, selC, selP, K1, g, min(i1, g + 32), stamp, n_small, n_mid, small_list,
-                          mid_list, edges, commits);
+            peel_items<1>(a, wl, h0, sw, K0, selC, selP, K1, g, min(i1, g + 32), stamp, n_small, n_mid,
+                          small_list, mid_list, nullptr, edges, commits);
     }
     PHASE(4);
     if (!sync()) return false;
     PHASE(5);
     const int ns = ld_volatile_i32(n_small), nm = ld_volatile_i32(n_mid);
+    // final after the barrier: the same on every thread of the grid
+    touched = ns + nm + (n_defer ? ld_volatile_i32(n_defer) : 0);
     PHASE_ADD(14, (unsigned long long)(ns + nm));
     TRACE_TOUCHED((unsigned long long)(ns + nm));
-    split_step(a, wl, sh, defer, ndefer, stamp, MULTI, ns, small_list, nm, mid_list, cta, ncta, states);
+    // the split step's pushes (peeled members, their splitters, the blocks)
+    // gather in shared memory and reach the rings once per CTA
+    Worklist wlb = wl;
+    wlb.buf = pbuf;
+    split_step(a, wlb, sh, defer, ndefer, stamp, MULTI, ns, small_list, nm, mid_list, cta, ncta, states);
+    if (pbuf) flush_pushes(wlb);
     PHASE(6);
     const bool ok = sync();
     PHASE(7);
@@ -1931,7 +2094,7 @@ __device__ __forceinline__ bool peel_round(const FrontierArgs& a, const Worklist
 // grid rounds alternate by round parity; CTA 0 clears the next round's pair.
 // Dynamic shared memory of the hybrid kernel: the selection (kmax + 32
 // labels and kmax + 33 offsets), then, with peel rounds, PEEL_CARRY_BYTES per
-// warp.
+// warp and the CTA's push buffer.
 __host__ __device__ inline size_t peel_carry_offset(int kmax) {
     return (sizeof(int32_t) * (2 * ((size_t)kmax + 32) + 1) + 7) / 8 * 8;
 }
@@ -1941,7 +2104,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_frontier_hybrid(FrontierArgs a, Hyb
     __shared__ CtaShared sh;
     __shared__ int s_defer[32];
     __shared__ int s_ndefer;
-    __shared__ int s_ns, s_nm, s_heavy, s_cmd, s_K, s_K0, s_av0;
+    __shared__ int s_ns, s_nm, s_heavy, s_cmd, s_K, s_K0, s_av0, s_avall;
     __shared__ bool s_peel;
     __shared__ unsigned long long s_h0;
     __shared__ unsigned s_stamp;
@@ -1953,6 +2116,8 @@ __global__ void __launch_bounds__(MAXT, 1) k_frontier_hybrid(FrontierArgs a, Hyb
     int32_t* s_selP = s_dyn + kmax + 32;
     // peel rounds: each warp's claim-pass carry, after the selection (8-byte aligned)
     unsigned char* s_carry = reinterpret_cast<unsigned char*>(s_dyn) + peel_carry_offset(kmax);
+    PushBuf* s_pbuf = h.peel ? reinterpret_cast<PushBuf*>(s_carry + (size_t)(blockDim.x >> 5) * PEEL_CARRY_BYTES)
+                             : nullptr;
     const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
     const int32_t n = a.n;
@@ -1965,6 +2130,19 @@ __global__ void __launch_bounds__(MAXT, 1) k_frontier_hybrid(FrontierArgs a, Hyb
     if (a.test_hook == 1 && lead) return;  // testing: never publish, never arrive
     const Worklist wl{c->bq_tail, a.queue, (size_t)n, 0, n};
     auto gsync = [&]() { return grid_sync(a.gb, tgt); };
+    // one-state splitters a peel round takes from ring 0: cap0, or, after a
+    // quiet round (fewer than one touched block per PEEL_QUIET splitters),
+    // PEEL_SWEEP_GROWTH times the last cap (at most PEEL_SWEEP_MAX): most of
+    // them then touch no block of several states and are carried out in the
+    // claim pass, so a round sweeps many of them. Every CTA updates it from
+    // the same counts, so all select alike.
+    int peel_cap = h.cap0;
+    int peel_touched = 0;
+    auto next_peel_cap = [&](int K) {
+        peel_cap = (long long)peel_touched * PEEL_QUIET < (long long)K
+                       ? (int)min((long long)peel_cap * PEEL_SWEEP_GROWTH, (long long)PEEL_SWEEP_MAX)
+                       : h.cap0;
+    };
     auto csync = [&]() {
         __syncthreads();
         return true;
@@ -1972,13 +2150,14 @@ __global__ void __launch_bounds__(MAXT, 1) k_frontier_hybrid(FrontierArgs a, Hyb
     // a grid round: K > 1 splitters in selC / selP (peel rounds: K listed ones
     // and K0 of one state from ring 0 after h0), or the single splitter C
     auto grid_round = [&](int K, int K0, unsigned long long h0, int32_t C, uint32_t stamp, int par,
-                          bool peel_now) -> bool {
+                          bool peel_now, bool sweep) -> bool {
         int* ns = &c->n_touched[par];
         int* nm = &c->n_mid[par];
         if (peel_now && K + K0 > 1)
             return peel_round(a, wl, sh, s_defer, &s_ndefer, s_selC, s_selP, K, K0, h0, stamp, gw, nwarps, ns, nm,
                               a.tlist, a.tlist + n, (int)blockIdx.x, (int)gridDim.x, edges, states, commits,
-                              s_carry + wid * PEEL_CARRY_BYTES, gsync);
+                              s_carry + wid * PEEL_CARRY_BYTES, s_pbuf, sweep, &c->n_defer[par], peel_touched,
+                              gsync);
         if (K > 1)
             return multi_round(a, wl, sh, s_defer, &s_ndefer, s_selC, s_selP, K, h.g_lost, stamp, gw, nwarps, ns, nm,
                                a.tlist, a.tlist + n, (int)blockIdx.x, (int)gridDim.x, edges, states, commits, gsync);
@@ -1992,6 +2171,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_frontier_hybrid(FrontierArgs a, Hyb
     // CTA 0's commands never overwrite, so a late-starting CTA reads it too)
     if (threadIdx.x < BISIM_BUCKETS) sh.head[threadIdx.x] = ldcg(&c->start_heads[threadIdx.x]);
     if (threadIdx.x < 32) s_lost[threadIdx.x] = 0u;
+    if (s_pbuf && threadIdx.x == 0) s_pbuf->n = 0;
     PHASE_RESET();
     __syncthreads();
     bool in_step = true;  // the other CTAs follow the selection (CTA 0: they are not parked)
@@ -2046,7 +2226,9 @@ __global__ void __launch_bounds__(MAXT, 1) k_frontier_hybrid(FrontierArgs a, Hyb
                 }
             __syncthreads();
             r = (int64_t)(stamp - a.stamp0);
-            if (!grid_round(C == MULTI ? K : 1, C == MULTI ? K0c : 0, h0c, C, stamp, (int)(r & 1), s_peel)) return;
+            if (!grid_round(C == MULTI ? K : 1, C == MULTI ? K0c : 0, h0c, C, stamp, (int)(r & 1), s_peel, false))
+                return;
+            if (s_peel && C == MULTI) next_peel_cap(K + K0c);  // as CTA 0 does after this round
             in_step = true;
             continue;
         }
@@ -2066,16 +2248,26 @@ __global__ void __launch_bounds__(MAXT, 1) k_frontier_hybrid(FrontierArgs a, Hyb
         // (one splitter per touched block). Every CTA reads the same tail
         // after the barrier, so all decide alike.
         bool peel_sel = false;
+        // a sweep round needs every CTA to select it (none parked)
+        const bool sweep_ok = peel_cap > h.cap0 && (!lead || in_step);
+        bool sweep_now = false;
         if (kmax > 1 && h.peel) {
-            if (threadIdx.x == 0)
+            if (threadIdx.x == 0) {
                 s_av0 = (int)min(*(volatile const unsigned long long*)&wl.tail[0] - sh.head[0],
                                  (unsigned long long)PEEL_MIN_SINGLES);
+                unsigned long long av = 0;
+                if (sweep_ok)
+                    for (int b = 0; b < BISIM_BUCKETS; b++)
+                        av += *(volatile const unsigned long long*)&wl.tail[b] - sh.head[b];
+                s_avall = (int)min(av, (unsigned long long)PEEL_MIN_SINGLES);
+            }
             __syncthreads();
-            peel_sel = s_av0 >= PEEL_MIN_SINGLES;
+            sweep_now = sweep_ok && s_avall >= PEEL_MIN_SINGLES;
+            peel_sel = sweep_now || s_av0 >= PEEL_MIN_SINGLES;
             __syncthreads();
         }
         if (peel_sel) {
-            K1 = select_peel(a, wl, sh.head, sh, s_selC, s_selP, kmax, h.budget, h.cap0);
+            K1 = select_peel(a, wl, sh.head, sh, s_selC, s_selP, kmax, h.budget, peel_cap, sweep_now);
             K0 = sh.k0;
             h0 = sh.h0;
             peel_now = true;
@@ -2110,7 +2302,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_frontier_hybrid(FrontierArgs a, Hyb
         // CTA 0 alone, or the grid?
         bool local;
         if (K > 1) {
-            local = K0 + s_selP[K1] <= h.local_budget;
+            local = !sweep_now && K0 + s_selP[K1] <= h.local_budget;
             if (local && K0 > 0) {
                 // the splitters of one state join the list (at most local_budget <= 32 of them)
                 for (int i = threadIdx.x; i < K0; i += blockDim.x) {
@@ -2141,6 +2333,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_frontier_hybrid(FrontierArgs a, Hyb
         if (lead && threadIdx.x == 0) {
             c->n_touched[par ^ 1] = 0;  // the next grid round's counters
             c->n_mid[par ^ 1] = 0;
+            c->n_defer[par ^ 1] = 0;
             if (K == 1) {
                 a.unstable[C] = 0u;
                 commits++;
@@ -2200,7 +2393,8 @@ __global__ void __launch_bounds__(MAXT, 1) k_frontier_hybrid(FrontierArgs a, Hyb
             PHASE_ADD(12, (unsigned long long)K);
             PHASE_ADD(13, (unsigned long long)(K0 + s_selP[K1]));
         }
-        if (!grid_round(K > 1 ? K1 : 1, K > 1 ? K0 : 0, h0, C, stamp, par, peel_now)) return;
+        if (!grid_round(K > 1 ? K1 : 1, K > 1 ? K0 : 0, h0, C, stamp, par, peel_now, sweep_now)) return;
+        if (peel_now && K > 1) next_peel_cap(K);
         if (K == 1) PHASE(8);
         TRACE_END(r, 0u);
     }
@@ -3023,11 +3217,12 @@ int refine_frontier(bisim_plan_s* p, bisim_stats* stats) {
         const int per_warp = p->opts.split_budget > 0 ? p->opts.split_budget : 1;
         h.budget = (int)std::min<int64_t>((int64_t)per_warp * g * (threads / 32), 1 << 30);
         h.peel = p->opts.peel >= 0 && h.kmax > 1 ? 1 : 0;
-        const int peel_items = p->opts.peel_items > 0 ? std::min(p->opts.peel_items, 1 << 12) : 16;
+        const int peel_items = p->opts.peel_items > 0 ? std::min(p->opts.peel_items, 1 << 12) : 64;
         int64_t cap0 = (int64_t)peel_items * g * (threads / 32);
         if (p->opts.splitters > 0) cap0 = std::min<int64_t>(cap0, p->opts.splitters);
         h.cap0 = (int)std::min<int64_t>(cap0, 1 << 30);
-        const size_t dyn = h.peel ? peel_carry_offset(h.kmax) + (size_t)(threads / 32) * PEEL_CARRY_BYTES
+        const size_t dyn = h.peel ? peel_carry_offset(h.kmax) + (size_t)(threads / 32) * PEEL_CARRY_BYTES +
+                                        sizeof(PushBuf)
                                   : sizeof(int32_t) * (2 * ((size_t)h.kmax + 32) + 1);
         BISIM_TRY(launch_persistent(fn, args, threads, p, &grid, 1, dyn));
     }
