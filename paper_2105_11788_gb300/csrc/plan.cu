@@ -151,11 +151,32 @@ __global__ void k_validate_count(const int32_t* __restrict__ src, const int32_t*
         const int4 a = act ? ld4(act, q) : make_int4(0, 0, 0, 0);
         const int b0 = check_transition(s.x, a.x, d.x, n, A, used), b1 = check_transition(s.y, a.y, d.y, n, A, used);
         const int b2 = check_transition(s.z, a.z, d.z, n, A, used), b3 = check_transition(s.w, a.w, d.w, n, A, used);
-        if (!b0) count_transition(s.x, a.x, d.x, mask_words, amask, indeg);
-        if (!b1) count_transition(s.y, a.y, d.y, mask_words, amask, indeg);
-        if (!b2) count_transition(s.z, a.z, d.z, mask_words, amask, indeg);
-        if (!b3) count_transition(s.w, a.w, d.w, mask_words, amask, indeg);
         bad |= b0 | b1 | b2 | b3;
+        if (!(b0 | b1 | b2 | b3)) {
+            // consecutive transitions with the same label-set word (one source,
+            // when the input is grouped by source) set their bits with one atomic
+            const int sv[4] = {s.x, s.y, s.z, s.w}, av[4] = {a.x, a.y, a.z, a.w}, dv[4] = {d.x, d.y, d.z, d.w};
+            size_t wprev = (size_t)sv[0] * mask_words + (av[0] >> 5);
+            uint32_t bits = 1u << (av[0] & 31);
+#pragma unroll
+            for (int k = 1; k < 4; k++) {
+                const size_t w = (size_t)sv[k] * mask_words + (av[k] >> 5);
+                if (w != wprev) {
+                    atomicOr(&amask[wprev], bits);
+                    wprev = w;
+                    bits = 0u;
+                }
+                bits |= 1u << (av[k] & 31);
+            }
+            atomicOr(&amask[wprev], bits);
+#pragma unroll
+            for (int k = 0; k < 4; k++) atomicAdd(&indeg[dv[k]], 1u);
+        } else {
+            if (!b0) count_transition(s.x, a.x, d.x, mask_words, amask, indeg);
+            if (!b1) count_transition(s.y, a.y, d.y, mask_words, amask, indeg);
+            if (!b2) count_transition(s.z, a.z, d.z, mask_words, amask, indeg);
+            if (!b3) count_transition(s.w, a.w, d.w, mask_words, amask, indeg);
+        }
     }
     for (int64_t i = 4 * m4 + gtid; i < m; i += gsz) {
         const int32_t s = src[i], a = act ? act[i] : 0, d = dst[i];
@@ -239,8 +260,15 @@ __global__ void k_mask_csr(const int32_t* __restrict__ src, const int32_t* __res
 //     records into the bin's range of two scratch arrays;
 //   pass B: one CTA per bin places the bin's records by target with
 //     shared-memory counters: entry in_ptr[t] + (rank among t's records).
-constexpr int CSR_A_THREADS = 1024;
-constexpr int CSR_A_ITEMS = 16;   // transitions per thread of pass A
+#ifndef BISIM_CSR_A_THREADS
+#define BISIM_CSR_A_THREADS 1024
+#endif
+#ifndef BISIM_CSR_A_ITEMS
+#define BISIM_CSR_A_ITEMS 8
+#endif
+constexpr int CSR_A_THREADS = BISIM_CSR_A_THREADS;
+constexpr int CSR_A_ITEMS = BISIM_CSR_A_ITEMS;   // transitions per thread of pass A
+constexpr int CSR_A_TILE = CSR_A_THREADS * CSR_A_ITEMS;
 constexpr int CSR_MAX_BINS = 4096;
 constexpr int CSR_B_THREADS = 1024;
 
@@ -253,43 +281,119 @@ __device__ __forceinline__ uint32_t slot_of(int32_t s, int32_t a, const uint32_t
     return off[s] + order;
 }
 
-__global__ void __launch_bounds__(CSR_A_THREADS) k_csr_bin(const int32_t* __restrict__ src,
+// With at most 32 labels a state's first slot and label set fit one word
+// (off << 32 | label set): one gather per transition instead of two.
+__global__ void k_pack_sinfo(const uint32_t* __restrict__ off, const uint32_t* __restrict__ amask, int32_t n,
+                             unsigned long long* sinfo) {
+    const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gsz)
+        sinfo[s] = ((unsigned long long)off[s] << 32) | amask[s];
+}
+
+__global__ void __launch_bounds__(CSR_A_THREADS, 1) k_csr_bin(const int32_t* __restrict__ src,
                                                            const int32_t* __restrict__ act,
                                                            const int32_t* __restrict__ dst, int64_t m,
                                                            const uint32_t* __restrict__ amask,
                                                            const uint32_t* __restrict__ off, int mask_words,
+                                                           const unsigned long long* __restrict__ sinfo,
                                                            int bin_bits, int nbins, uint32_t* bin_cursor,
                                                            uint32_t* rec_t, unsigned long long* rec_v) {
-    __shared__ uint32_t cnt[CSR_MAX_BINS];
-    __shared__ uint32_t base[CSR_MAX_BINS];
-    const int64_t tile0 = (int64_t)blockIdx.x * (CSR_A_THREADS * CSR_A_ITEMS);
+    // dynamic shared memory: per bin the tile's count, then its first
+    // position in the tile (exclusive scan) and its reserved global position;
+    // the tile's records sorted by bin
+    extern __shared__ __align__(16) unsigned char csr_smem[];
+    unsigned long long* vs = reinterpret_cast<unsigned long long*>(csr_smem);  // [CSR_A_TILE]
+    uint32_t* ts = reinterpret_cast<uint32_t*>(vs + CSR_A_TILE);              // [CSR_A_TILE]
+    uint32_t* cnt = ts + CSR_A_TILE;                                           // [nbins]
+    uint32_t* toff = cnt + CSR_MAX_BINS;                                       // [nbins]
+    uint32_t* base = toff + CSR_MAX_BINS;                                      // [nbins]
+    __shared__ uint32_t wsum[CSR_A_THREADS / 32];
+    const int64_t tile0 = (int64_t)blockIdx.x * CSR_A_TILE;
+    const int tn = (int)min((int64_t)CSR_A_TILE, m - tile0);
     for (int b = threadIdx.x; b < nbins; b += CSR_A_THREADS) cnt[b] = 0;
     __syncthreads();
     int32_t t[CSR_A_ITEMS];
     uint32_t rk[CSR_A_ITEMS];
 #pragma unroll
     for (int j = 0; j < CSR_A_ITEMS; j++) {
-        const int64_t i = tile0 + (int64_t)j * CSR_A_THREADS + threadIdx.x;
-        t[j] = i < m ? dst[i] : -1;
+        const int k = j * CSR_A_THREADS + (int)threadIdx.x;
+        t[j] = k < tn ? dst[tile0 + k] : -1;
     }
 #pragma unroll
     for (int j = 0; j < CSR_A_ITEMS; j++)
         if (t[j] >= 0) rk[j] = atomicAdd(&cnt[t[j] >> bin_bits], 1u);
     __syncthreads();
-    for (int b = threadIdx.x; b < nbins; b += CSR_A_THREADS)
-        if (cnt[b]) base[b] = atomicAdd(&bin_cursor[b], cnt[b]);
+    // exclusive scan of the counts over the bins (CSR_MAX_BINS / CSR_A_THREADS per thread)
+    {
+        constexpr int E = CSR_MAX_BINS / CSR_A_THREADS;
+        const int b0 = (int)threadIdx.x * E;
+        uint32_t c[E], sum = 0;
+#pragma unroll
+        for (int e = 0; e < E; e++) {
+            c[e] = b0 + e < nbins ? cnt[b0 + e] : 0u;
+            sum += c[e];
+        }
+        const unsigned lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+        uint32_t x = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= (unsigned)o) x += y;
+        }
+        if (lane == 31) wsum[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            uint32_t v = lane < CSR_A_THREADS / 32 ? wsum[lane] : 0u;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= (unsigned)o) v += y;
+            }
+            if (lane < CSR_A_THREADS / 32) wsum[lane] = v;
+        }
+        __syncthreads();
+        uint32_t ex = x - sum + (w > 0 ? wsum[w - 1] : 0u);
+#pragma unroll
+        for (int e = 0; e < E; e++) {
+            if (b0 + e < nbins) {
+                toff[b0 + e] = ex;
+                base[b0 + e] = c[e] ? atomicAdd(&bin_cursor[b0 + e], c[e]) : 0u;
+            }
+            ex += c[e];
+        }
+    }
     __syncthreads();
-    // the tile's sources and labels again (just read, so close), its slots, and the records
+    // the tile's sources and labels again (just read, so close) and its
+    // records, placed by bin in shared memory
 #pragma unroll
     for (int j = 0; j < CSR_A_ITEMS; j++)
         if (t[j] >= 0) {
             const int64_t i = tile0 + (int64_t)j * CSR_A_THREADS + threadIdx.x;
             const int32_t s = src[i], a = act ? act[i] : 0;
-            const uint32_t q = base[t[j] >> bin_bits] + rk[j];
-            rec_t[q] = (uint32_t)t[j];
-            rec_v[q] = ((unsigned long long)(uint32_t)s << 32) | slot_of(s, a, amask, off, mask_words);
+            uint32_t slot;
+            if (sinfo) {
+                const unsigned long long si = sinfo[s];
+                slot = (uint32_t)(si >> 32) + __popc((uint32_t)si & ((1u << (a & 31)) - 1u));
+            } else {
+                slot = slot_of(s, a, amask, off, mask_words);
+            }
+            const uint32_t q = toff[t[j] >> bin_bits] + rk[j];
+            ts[q] = (uint32_t)t[j];
+            vs[q] = ((unsigned long long)(uint32_t)s << 32) | slot;
         }
+    __syncthreads();
+    // consecutive records of a bin go to consecutive global positions
+    for (int q = threadIdx.x; q < tn; q += CSR_A_THREADS) {
+        const uint32_t tt = ts[q];
+        const int b = (int)(tt >> bin_bits);
+        const uint32_t g = base[b] + (uint32_t)q - toff[b];
+        rec_t[g] = tt;
+        rec_v[g] = vs[q];
+    }
 }
+
+// dynamic shared memory of k_csr_bin
+constexpr size_t CSR_A_SMEM = (size_t)CSR_A_TILE * 12 + (size_t)CSR_MAX_BINS * 12;
 
 __global__ void __launch_bounds__(CSR_B_THREADS) k_csr_place(const uint32_t* __restrict__ in_ptr, int32_t n,
                                                              int bin_bits, const uint32_t* __restrict__ rec_t,
@@ -861,16 +965,23 @@ static int slots_from_masks(bisim_plan_s* p, const int32_t* src, const int32_t* 
     while (((int64_t)n + ((int64_t)1 << bin_bits) - 1) >> bin_bits > CSR_MAX_BINS) bin_bits++;
     if (bin_bits <= 15) {
         const int nbins = (int)(((int64_t)n + ((int64_t)1 << bin_bits) - 1) >> bin_bits);
-        DevMem bin_cursor, rec_t, rec_v;
+        DevMem bin_cursor, rec_t, rec_v, sinfo;
+        if (mask_words == 1) {
+            BISIM_TRY(sinfo.alloc(8 * (size_t)n, st));
+            k_pack_sinfo<<<gn, T, 0, st>>>(off, amask, n, sinfo.as<unsigned long long>());
+            BISIM_LAUNCHED();
+        }
         BISIM_TRY(bin_cursor.alloc(4 * (size_t)nbins, st));
         BISIM_TRY(rec_t.alloc(4 * (size_t)m, st));
         BISIM_TRY(rec_v.alloc(8 * (size_t)m, st));
         k_bin_starts<<<grid_for(nbins, T), T, 0, st>>>(p->in_ptr.as<uint32_t>(), n, bin_bits, nbins,
                                                        bin_cursor.as<uint32_t>());
         BISIM_LAUNCHED();
-        const int64_t tile = (int64_t)CSR_A_THREADS * CSR_A_ITEMS;
-        k_csr_bin<<<(unsigned)((m + tile - 1) / tile), CSR_A_THREADS, 0, st>>>(
-            src, act, dst, m, amask, off, mask_words, bin_bits, nbins, bin_cursor.as<uint32_t>(),
+        const int64_t tile = CSR_A_TILE;
+        BISIM_CUDA_TRY(cudaFuncSetAttribute(k_csr_bin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CSR_A_SMEM));
+        k_csr_bin<<<(unsigned)((m + tile - 1) / tile), CSR_A_THREADS, CSR_A_SMEM, st>>>(
+            src, act, dst, m, amask, off, mask_words, sinfo.p ? sinfo.as<unsigned long long>() : nullptr, bin_bits,
+            nbins, bin_cursor.as<uint32_t>(),
             rec_t.as<uint32_t>(), rec_v.as<unsigned long long>());
         BISIM_LAUNCHED();
         BISIM_CUDA_TRY(cudaGetLastError());
