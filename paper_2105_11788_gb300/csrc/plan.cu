@@ -131,19 +131,44 @@ __global__ void k_csr_scatter(const uint32_t* __restrict__ tkey, const uint64_t*
 // (source, label) pairs in (source, label) order, which is exactly what
 // Algorithm 4's sort, action_switch and segmented scans compute.
 constexpr int MASK_WORDS_MAX = 4;
+// The incoming-transition CSR is built by bins of 2^bin_bits targets, at most
+// CSR_MAX_BINS of them (see k_csr_bin).
+constexpr int CSR_MAX_BINS = 4096;
+
+// In-degrees, counted either per target (a global atomic per transition,
+// indeg != null) or per bin of 2^bin_bits targets in the CTA's shared
+// histogram, added to bin_cnt at the end (the CSR passes then derive the
+// per-target offsets bin by bin).
+struct InCount {
+    uint32_t* indeg;
+    uint32_t* hist;  // shared, or null
+    int bin_bits;
+    __device__ __forceinline__ void add(int32_t d) const {
+        if (hist)
+            atomicAdd(&hist[(uint32_t)d >> bin_bits], 1u);
+        else
+            atomicAdd(&indeg[d], 1u);
+    }
+};
 
 __device__ __forceinline__ void count_transition(int32_t s, int32_t a, int32_t d, int mask_words, uint32_t* amask,
-                                                 uint32_t* indeg) {
+                                                 const InCount& ic) {
     atomicOr(&amask[(size_t)s * mask_words + (a >> 5)], 1u << (a & 31));
-    atomicAdd(&indeg[d], 1u);
+    ic.add(d);
 }
 
 __global__ void k_validate_count(const int32_t* __restrict__ src, const int32_t* __restrict__ act,
                                  const int32_t* __restrict__ dst, const int32_t* __restrict__ init, int32_t n,
                                  int64_t m, int32_t A, int* status, uint32_t* used, int vec, int mask_words,
-                                 uint32_t* amask, uint32_t* indeg) {
+                                 uint32_t* amask, uint32_t* indeg, int bin_bits, int nbins, uint32_t* bin_cnt) {
+    __shared__ uint32_t hist[CSR_MAX_BINS];
     const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
     const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const InCount ic{indeg, bin_cnt ? hist : nullptr, bin_bits};
+    if (bin_cnt) {
+        for (int b = threadIdx.x; b < nbins; b += blockDim.x) hist[b] = 0u;
+        __syncthreads();
+    }
     int bad = 0;
     const int64_t m4 = vec ? m / 4 : 0;
     for (int64_t q = gtid; q < m4; q += gsz) {
@@ -170,24 +195,29 @@ __global__ void k_validate_count(const int32_t* __restrict__ src, const int32_t*
             }
             atomicOr(&amask[wprev], bits);
 #pragma unroll
-            for (int k = 0; k < 4; k++) atomicAdd(&indeg[dv[k]], 1u);
+            for (int k = 0; k < 4; k++) ic.add(dv[k]);
         } else {
-            if (!b0) count_transition(s.x, a.x, d.x, mask_words, amask, indeg);
-            if (!b1) count_transition(s.y, a.y, d.y, mask_words, amask, indeg);
-            if (!b2) count_transition(s.z, a.z, d.z, mask_words, amask, indeg);
-            if (!b3) count_transition(s.w, a.w, d.w, mask_words, amask, indeg);
+            if (!b0) count_transition(s.x, a.x, d.x, mask_words, amask, ic);
+            if (!b1) count_transition(s.y, a.y, d.y, mask_words, amask, ic);
+            if (!b2) count_transition(s.z, a.z, d.z, mask_words, amask, ic);
+            if (!b3) count_transition(s.w, a.w, d.w, mask_words, amask, ic);
         }
     }
     for (int64_t i = 4 * m4 + gtid; i < m; i += gsz) {
         const int32_t s = src[i], a = act ? act[i] : 0, d = dst[i];
         const int b = check_transition(s, a, d, n, A, used);
-        if (!b) count_transition(s, a, d, mask_words, amask, indeg);
+        if (!b) count_transition(s, a, d, mask_words, amask, ic);
         bad |= b;
     }
     if (init)
         for (int64_t i = gtid; i < n; i += gsz)
             if ((unsigned)init[i] >= (unsigned)n) bad = 1;
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, ST_INVALID);
+    if (bin_cnt) {
+        __syncthreads();
+        for (int b = threadIdx.x; b < nbins; b += blockDim.x)
+            if (hist[b]) atomicAdd(&bin_cnt[b], hist[b]);
+    }
 }
 
 // nr_marks of every state (into off, scanned afterwards)
@@ -269,7 +299,6 @@ __global__ void k_mask_csr(const int32_t* __restrict__ src, const int32_t* __res
 constexpr int CSR_A_THREADS = BISIM_CSR_A_THREADS;
 constexpr int CSR_A_ITEMS = BISIM_CSR_A_ITEMS;   // transitions per thread of pass A
 constexpr int CSR_A_TILE = CSR_A_THREADS * CSR_A_ITEMS;
-constexpr int CSR_MAX_BINS = 4096;
 constexpr int CSR_B_THREADS = 1024;
 
 __device__ __forceinline__ uint32_t slot_of(int32_t s, int32_t a, const uint32_t* __restrict__ amask,
@@ -395,28 +424,64 @@ __global__ void __launch_bounds__(CSR_A_THREADS, 1) k_csr_bin(const int32_t* __r
 // dynamic shared memory of k_csr_bin
 constexpr size_t CSR_A_SMEM = (size_t)CSR_A_TILE * 12 + (size_t)CSR_MAX_BINS * 12;
 
-__global__ void __launch_bounds__(CSR_B_THREADS) k_csr_place(const uint32_t* __restrict__ in_ptr, int32_t n,
-                                                             int bin_bits, const uint32_t* __restrict__ rec_t,
+// Pass B: bin b's records are rec_t / rec_v[bin_end[b - 1], bin_end[b])
+// (bin_end: the bin cursors after pass A). The CTA counts them per target,
+// writes in_ptr for the bin's targets (and in_ptr[n] = m in the last bin)
+// from the exclusive scan of the counts, and places every record by target
+// with shared-memory cursors.
+__global__ void __launch_bounds__(CSR_B_THREADS) k_csr_place(const uint32_t* __restrict__ bin_end, int32_t n,
+                                                             int64_t m, int bin_bits,
+                                                             const uint32_t* __restrict__ rec_t,
                                                              const unsigned long long* __restrict__ rec_v,
-                                                             unsigned long long* in_edge) {
+                                                             uint32_t* in_ptr, unsigned long long* in_edge) {
     extern __shared__ uint32_t tcnt[];  // 2^bin_bits counters
-    const int64_t lo = (int64_t)blockIdx.x << bin_bits;
-    const int64_t hi = min((int64_t)n, lo + ((int64_t)1 << bin_bits));
-    for (int64_t i = threadIdx.x; i < hi - lo; i += CSR_B_THREADS) tcnt[i] = 0;
+    __shared__ uint32_t wsum[CSR_B_THREADS / 32];
+    const int b = (int)blockIdx.x;
+    const int64_t lo = (int64_t)b << bin_bits;
+    const int nt = (int)(min((int64_t)n, lo + ((int64_t)1 << bin_bits)) - lo);
+    for (int i = threadIdx.x; i < nt; i += CSR_B_THREADS) tcnt[i] = 0;
     __syncthreads();
-    const uint32_t r0 = in_ptr[lo], r1 = in_ptr[hi];
+    const uint32_t r0 = b ? bin_end[b - 1] : 0u, r1 = bin_end[b];
+    for (uint32_t i = r0 + threadIdx.x; i < r1; i += CSR_B_THREADS) atomicAdd(&tcnt[rec_t[i] - (uint32_t)lo], 1u);
+    __syncthreads();
+    // exclusive scan of tcnt[0, nt): each thread a run of E counters
+    const int E = (nt + CSR_B_THREADS - 1) / CSR_B_THREADS;
+    const int i0 = (int)threadIdx.x * E, i1 = min(nt, i0 + E);
+    uint32_t sum = 0;
+    for (int i = i0; i < i1; i++) sum += tcnt[i];
+    const unsigned lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+    uint32_t x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= (unsigned)o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t v = lane < CSR_B_THREADS / 32 ? wsum[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= (unsigned)o) v += y;
+        }
+        if (lane < CSR_B_THREADS / 32) wsum[lane] = v;
+    }
+    __syncthreads();
+    uint32_t ex = x - sum + (w > 0 ? wsum[w - 1] : 0u);
+    for (int i = i0; i < i1; i++) {
+        const uint32_t c = tcnt[i];
+        tcnt[i] = ex;
+        in_ptr[lo + i] = r0 + ex;
+        ex += c;
+    }
+    if (lo + nt == (int64_t)n && threadIdx.x == 0) in_ptr[n] = (uint32_t)m;
+    __syncthreads();
     for (uint32_t i = r0 + threadIdx.x; i < r1; i += CSR_B_THREADS) {
         const uint32_t tt = rec_t[i];
         const uint32_t r = atomicAdd(&tcnt[tt - (uint32_t)lo], 1u);
-        in_edge[in_ptr[tt] + r] = rec_v[i];
+        in_edge[r0 + r] = rec_v[i];
     }
-}
-
-// the bins' first entries: bin_cursor[b] = in_ptr[b << bin_bits]
-__global__ void k_bin_starts(const uint32_t* __restrict__ in_ptr, int32_t n, int bin_bits, int nbins,
-                             uint32_t* bin_cursor) {
-    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nbins; b += gridDim.x * blockDim.x)
-        bin_cursor[b] = in_ptr[min((int64_t)n, (int64_t)b << bin_bits)];
 }
 
 // label set of every state as a bitmask of mask_words 32-bit words
@@ -938,8 +1003,21 @@ static int slots_by_sort(bisim_plan_s* p, const int32_t* src, const int32_t* act
 }
 
 // a2 + a3 from the label sets recorded by k_validate_count (see there).
+// Bins of the incoming-transition CSR: 2^bin_bits targets each, at most
+// CSR_MAX_BINS of them, whose counters fit in shared memory (2^15 targets:
+// 128 KB); 0 when n needs more (the CSR then takes one atomic per transition).
+static int csr_bin_bits(int32_t n) {
+    int bin_bits = 11;
+    while (((int64_t)n + ((int64_t)1 << bin_bits) - 1) >> bin_bits > CSR_MAX_BINS) bin_bits++;
+    return bin_bits <= 15 ? bin_bits : 0;
+}
+
+// a2 + a3 from the label sets recorded by k_validate_count (see there). With
+// bin_cnt the validation counted transitions per target bin (bin_bits) and
+// the CSR passes write in_ptr; otherwise it counted in-degrees into in_ptr.
 static int slots_from_masks(bisim_plan_s* p, const int32_t* src, const int32_t* act, const int32_t* dst,
-                            const uint32_t* amask, int mask_words, int vec) {
+                            const uint32_t* amask, int mask_words, int vec, const uint32_t* bin_cnt,
+                            int bin_bits) {
     const int32_t n = p->n;
     const int64_t m = p->m;
     cudaStream_t st = p->st;
@@ -952,18 +1030,16 @@ static int slots_from_masks(bisim_plan_s* p, const int32_t* src, const int32_t* 
     }
     // off = exclusive sum of nr_marks (off[n] = L); in_ptr likewise over in-degrees
     BISIM_TRY(scan_exclusive_u32(off, off, (int64_t)n + 1, nullptr, st));
-    BISIM_TRY(scan_exclusive_u32(p->in_ptr.as<uint32_t>(), p->in_ptr.as<uint32_t>(), (int64_t)n + 1, nullptr, st));
+    if (!bin_cnt)
+        BISIM_TRY(scan_exclusive_u32(p->in_ptr.as<uint32_t>(), p->in_ptr.as<uint32_t>(), (int64_t)n + 1, nullptr,
+                                     st));
     uint32_t L_h = 0;
     BISIM_CUDA_TRY(cudaMemcpyAsync(&L_h, off + n, 4, cudaMemcpyDeviceToHost, st));
     BISIM_CUDA_TRY(cudaStreamSynchronize(st));
     p->L = (int64_t)L_h;
     BISIM_TRY(p->in_edge.alloc(8 * (size_t)m, st));
     if (!m) return BISIM_OK;
-    // a3: bins of 2^bin_bits targets, at most CSR_MAX_BINS of them, whose
-    // counters fit in shared memory (2^15 targets: 128 KB)
-    int bin_bits = 11;
-    while (((int64_t)n + ((int64_t)1 << bin_bits) - 1) >> bin_bits > CSR_MAX_BINS) bin_bits++;
-    if (bin_bits <= 15) {
+    if (bin_cnt) {
         const int nbins = (int)(((int64_t)n + ((int64_t)1 << bin_bits) - 1) >> bin_bits);
         DevMem bin_cursor, rec_t, rec_v, sinfo;
         if (mask_words == 1) {
@@ -974,22 +1050,21 @@ static int slots_from_masks(bisim_plan_s* p, const int32_t* src, const int32_t* 
         BISIM_TRY(bin_cursor.alloc(4 * (size_t)nbins, st));
         BISIM_TRY(rec_t.alloc(4 * (size_t)m, st));
         BISIM_TRY(rec_v.alloc(8 * (size_t)m, st));
-        k_bin_starts<<<grid_for(nbins, T), T, 0, st>>>(p->in_ptr.as<uint32_t>(), n, bin_bits, nbins,
-                                                       bin_cursor.as<uint32_t>());
-        BISIM_LAUNCHED();
+        // the bins' first records: exclusive scan of the per-bin counts
+        BISIM_TRY(scan_exclusive_u32(bin_cnt, bin_cursor.as<uint32_t>(), nbins, nullptr, st));
         const int64_t tile = CSR_A_TILE;
         BISIM_CUDA_TRY(cudaFuncSetAttribute(k_csr_bin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CSR_A_SMEM));
         k_csr_bin<<<(unsigned)((m + tile - 1) / tile), CSR_A_THREADS, CSR_A_SMEM, st>>>(
             src, act, dst, m, amask, off, mask_words, sinfo.p ? sinfo.as<unsigned long long>() : nullptr, bin_bits,
-            nbins, bin_cursor.as<uint32_t>(),
-            rec_t.as<uint32_t>(), rec_v.as<unsigned long long>());
+            nbins, bin_cursor.as<uint32_t>(), rec_t.as<uint32_t>(), rec_v.as<unsigned long long>());
         BISIM_LAUNCHED();
         BISIM_CUDA_TRY(cudaGetLastError());
+        // bin_cursor now holds each bin's end
         const size_t smem = sizeof(uint32_t) << bin_bits;
         BISIM_CUDA_TRY(cudaFuncSetAttribute(k_csr_place, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_csr_place<<<nbins, CSR_B_THREADS, smem, st>>>(p->in_ptr.as<uint32_t>(), n, bin_bits,
+        k_csr_place<<<nbins, CSR_B_THREADS, smem, st>>>(bin_cursor.as<uint32_t>(), n, m, bin_bits,
                                                         rec_t.as<uint32_t>(), rec_v.as<unsigned long long>(),
-                                                        p->in_edge.as<unsigned long long>());
+                                                        p->in_ptr.as<uint32_t>(), p->in_edge.as<unsigned long long>());
         BISIM_LAUNCHED();
         BISIM_CUDA_TRY(cudaGetLastError());
         return BISIM_OK;
@@ -1038,10 +1113,16 @@ int plan_build(bisim_plan_s* p, const int32_t* src, const int32_t* act, const in
     const int vec = (((uintptr_t)src | (uintptr_t)dst | (uintptr_t)act) & 15u) == 0 ? 1 : 0;
     const int mask_words = (A + 31) / 32;
     const bool by_masks = mask_words <= MASK_WORDS_MAX && p->opts.slots == 0;
-    DevMem amask_local;
+    DevMem amask_local, bin_cnt;
     DevMem& amask = by_masks ? p->amask : amask_local;
+    const int bin_bits = by_masks && m > 0 ? csr_bin_bits(n) : 0;
+    const int nbins = bin_bits ? (int)(((int64_t)n + ((int64_t)1 << bin_bits) - 1) >> bin_bits) : 0;
     if (by_masks) {
         p->mask_words = mask_words;
+        if (bin_bits) {
+            BISIM_TRY(bin_cnt.alloc(4 * (size_t)nbins, st));
+            BISIM_CUDA_TRY(cudaMemsetAsync(bin_cnt.p, 0, 4 * (size_t)nbins, st));
+        }
         BISIM_TRY(amask.alloc(4 * (size_t)mask_words * n, st));
         BISIM_TRY(p->off.alloc(4 * ((size_t)n + 1), st));
         BISIM_TRY(p->in_ptr.alloc(4 * ((size_t)n + 1), st));
@@ -1050,7 +1131,7 @@ int plan_build(bisim_plan_s* p, const int32_t* src, const int32_t* act, const in
         BISIM_CUDA_TRY(cudaMemsetAsync(p->in_ptr.p, 0, 4 * ((size_t)n + 1), st));
         k_validate_count<<<grid_for(std::max<int64_t>(m, n), T), T, 0, st>>>(
             src, act, dst, init, n, m, A, status, used.as<uint32_t>(), vec, mask_words, amask.as<uint32_t>(),
-            p->in_ptr.as<uint32_t>());
+            p->in_ptr.as<uint32_t>(), bin_bits, nbins, bin_bits ? bin_cnt.as<uint32_t>() : nullptr);
     } else {
         k_validate<<<grid_for(std::max<int64_t>(m, n), T), T, 0, st>>>(src, act, dst, init, n, m, A,
                                                                        status, used.as<uint32_t>(), vec);
@@ -1073,7 +1154,8 @@ int plan_build(bisim_plan_s* p, const int32_t* src, const int32_t* act, const in
     p->pre_rounds = p->opts.engine == BISIM_ENGINE_PAIR ? 0 : p->n_labels;
 
     if (by_masks) {
-        BISIM_TRY(slots_from_masks(p, src, act, dst, amask.as<uint32_t>(), mask_words, vec));
+        BISIM_TRY(slots_from_masks(p, src, act, dst, amask.as<uint32_t>(), mask_words, vec,
+                                   bin_bits ? bin_cnt.as<uint32_t>() : nullptr, bin_bits));
     } else {
         BISIM_TRY(slots_by_sort(p, src, act, dst, vec));
     }
