@@ -1,8 +1,12 @@
 // C ABI entry points (include/bisim.h): argument checks, plan lifetime,
 // engine selection, device timing and error reporting.
+#include <array>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "plan.cuh"
 
@@ -33,6 +37,45 @@ static void fill_static_stats(const bisim_plan_s* p, bisim_stats* s) {
     s->t_plan_ms = p->t_plan_ms;
     s->t_pre_ms = p->t_pre_ms;
 }
+
+namespace {
+
+// Streams for the input copies of bisim_reduce_host, three per device,
+// created on first use and kept for the process.
+std::mutex g_copy_mu;
+std::vector<std::pair<int, std::array<cudaStream_t, 3>>> g_copy_streams;
+
+int copy_streams(cudaStream_t* cs) {
+    int dev = 0;
+    BISIM_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_copy_mu);
+    for (auto& e : g_copy_streams)
+        if (e.first == dev) {
+            for (int k = 0; k < 3; k++) cs[k] = e.second[k];
+            return BISIM_OK;
+        }
+    std::array<cudaStream_t, 3> a{};
+    for (int k = 0; k < 3; k++) BISIM_CUDA_TRY(cudaStreamCreateWithFlags(&a[k], cudaStreamNonBlocking));
+    g_copy_streams.emplace_back(dev, a);
+    for (int k = 0; k < 3; k++) cs[k] = a[k];
+    return BISIM_OK;
+}
+
+// Events of one call (destroyed with it; a destroyed event that a stream
+// still waits on is released once the wait completes).
+struct EventSet {
+    cudaEvent_t e[4] = {};
+    int n = 0;
+    int create(int k) {
+        for (; n < k; n++) BISIM_CUDA_TRY(cudaEventCreateWithFlags(&e[n], cudaEventDisableTiming));
+        return BISIM_OK;
+    }
+    ~EventSet() {
+        for (int i = 0; i < n; i++) cudaEventDestroy(e[i]);
+    }
+};
+
+}  // namespace
 
 extern "C" {
 
@@ -197,17 +240,33 @@ int bisim_reduce_host(int32_t n, int64_t m, int32_t num_act, const int32_t* src_
     BISIM_TRY(dsrc.alloc(4 * (size_t)m, st));
     BISIM_TRY(ddst.alloc(4 * (size_t)m, st));
     BISIM_TRY(dout.alloc(4 * (size_t)n, st));
-    if (m) {
-        BISIM_CUDA_TRY(cudaMemcpyAsync(dsrc.p, src_h, 4 * (size_t)m, cudaMemcpyHostToDevice, st));
-        BISIM_CUDA_TRY(cudaMemcpyAsync(ddst.p, dst_h, 4 * (size_t)m, cudaMemcpyHostToDevice, st));
-    }
-    if (act_h) {
-        BISIM_TRY(dact.alloc(4 * (size_t)m, st));
-        if (m) BISIM_CUDA_TRY(cudaMemcpyAsync(dact.p, act_h, 4 * (size_t)m, cudaMemcpyHostToDevice, st));
-    }
-    if (init_h) {
-        BISIM_TRY(dinit.alloc(4 * (size_t)n, st));
-        if (n) BISIM_CUDA_TRY(cudaMemcpyAsync(dinit.p, init_h, 4 * (size_t)n, cudaMemcpyHostToDevice, st));
+    if (act_h) BISIM_TRY(dact.alloc(4 * (size_t)m, st));
+    if (init_h) BISIM_TRY(dinit.alloc(4 * (size_t)n, st));
+    // the input arrays travel on separate streams at once (one copy each),
+    // after the allocations and before the plan
+    {
+        cudaStream_t cs[3];
+        BISIM_TRY(copy_streams(cs));
+        struct Copy {
+            void* d;
+            const void* h;
+            size_t bytes;
+        } copies[4] = {{dsrc.p, src_h, 4 * (size_t)m},
+                       {ddst.p, dst_h, 4 * (size_t)m},
+                       {act_h ? dact.p : nullptr, act_h, act_h ? 4 * (size_t)m : 0},
+                       {init_h ? dinit.p : nullptr, init_h, init_h ? 4 * (size_t)n : 0}};
+        EventSet ev;
+        BISIM_TRY(ev.create(4));
+        BISIM_CUDA_TRY(cudaEventRecord(ev.e[0], st));
+        for (int k = 0; k < 3; k++) BISIM_CUDA_TRY(cudaStreamWaitEvent(cs[k], ev.e[0], 0));
+        for (int k = 0; k < 4; k++)
+            if (copies[k].bytes)
+                BISIM_CUDA_TRY(cudaMemcpyAsync(copies[k].d, copies[k].h, copies[k].bytes, cudaMemcpyHostToDevice,
+                                               cs[k % 3]));
+        for (int k = 0; k < 3; k++) {
+            BISIM_CUDA_TRY(cudaEventRecord(ev.e[1 + k], cs[k]));
+            BISIM_CUDA_TRY(cudaStreamWaitEvent(st, ev.e[1 + k], 0));
+        }
     }
     bisim_plan_t plan = nullptr;
     int rc = bisim_plan(n, m, num_act, dsrc.as<int32_t>(), act_h ? dact.as<int32_t>() : nullptr,

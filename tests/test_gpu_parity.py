@@ -229,6 +229,27 @@ def test_host_buffer_entry_point():
     assert st.num_blocks == defs.num_blocks(out)
 
 
+def test_host_buffer_entry_point_with_initial_partition():
+    """All four input arrays from host memory (copied on separate streams
+    before the plan), pageable and pinned, with and without the labels."""
+    import torch
+
+    lts = lts_gen.kripke_uniform(seed=5, n=20000, m=80000)
+    want = oracle.ks_lts(lts).tolist()
+    for pinned in (False, True):
+        conv = (lambda a: torch.from_numpy(a).pin_memory()) if pinned else torch.from_numpy
+        src, act, dst, init = conv(lts.src), conv(lts.act), conv(lts.dst), conv(lts.init)
+        out = torch.empty(lts.n, dtype=torch.int32)
+        if pinned:
+            out = out.pin_memory()
+        for with_act in (True, False):
+            bisim.bisim_reduce_host(lts.n, lts.m, lts.num_act, src.data_ptr(),
+                                    act.data_ptr() if with_act else None, dst.data_ptr(), init.data_ptr(),
+                                    out.data_ptr())
+            if with_act or lts.num_act == 1:
+                assert out.tolist() == want
+
+
 @pytest.mark.parametrize("engine", ENGINES, ids=ENGINE_IDS)
 def test_launch_shapes(engine):
     lts = lts_gen.quotient_expansion(seed=4, classes=400, trans=4000, copies_hi=30)
