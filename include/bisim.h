@@ -128,7 +128,7 @@ typedef struct bisim_opts {
                                  splitter per round */
     int32_t peel_items;       /* frontier engine, grid rounds with several splitters:
                                  at most this many splitters of one state per warp of
-                                 the grid (0 = 64) */
+                                 the grid (0 = 96) */
     int32_t small;            /* engine auto or frontier with the default schedule: an
                                  LTS with |Act| <= 32 whose arrays fit in one CTA's
                                  shared memory (about 12 B per transition and 116 B

@@ -3217,7 +3217,7 @@ int refine_frontier(bisim_plan_s* p, bisim_stats* stats) {
         const int per_warp = p->opts.split_budget > 0 ? p->opts.split_budget : 1;
         h.budget = (int)std::min<int64_t>((int64_t)per_warp * g * (threads / 32), 1 << 30);
         h.peel = p->opts.peel >= 0 && h.kmax > 1 ? 1 : 0;
-        const int peel_items = p->opts.peel_items > 0 ? std::min(p->opts.peel_items, 1 << 12) : 64;
+        const int peel_items = p->opts.peel_items > 0 ? std::min(p->opts.peel_items, 1 << 12) : 96;
         int64_t cap0 = (int64_t)peel_items * g * (threads / 32);
         if (p->opts.splitters > 0) cap0 = std::min<int64_t>(cap0, p->opts.splitters);
         h.cap0 = (int)std::min<int64_t>(cap0, 1 << 30);
