@@ -223,7 +223,8 @@ void bisim_plan_destroy(bisim_plan_t plan);
  * off read as start offsets), and the slot of a transition s -a-> t is
  * off(s) + order, order = the number of labels of s smaller than a.
  * off_h       int32 [n + 1] or NULL
- * slot_src_h  int32 [mark_length] or NULL: the state owning each slot
+ * slot_src_h  int32 [mark_length] or NULL: the state owning each slot (plans
+ *             that took the slots from label sets fill these on this call)
  * slot_act_h  int32 [mark_length] or NULL: its label
  * in_ptr_h    int32 [n + 1] or NULL: incoming transitions of t are entries
  *             in_ptr[t] .. in_ptr[t+1]-1 of in_edge
@@ -237,10 +238,12 @@ int bisim_plan_arrays(bisim_plan_t plan, int32_t* off_h, int32_t* slot_src_h, in
 
 /*
  * bisim_reduce_host - one whole reduction from HOST buffers: copies the
- * arrays to the device, plans, refines, copies the canonical block ids back
- * into out_block_h and releases everything. Same arguments and errors as
- * bisim_plan + bisim_refine; all pointers ending in _h are host memory
- * (pinned memory gives faster copies), act_h and init_h may be NULL.
+ * arrays to the device (on three streams of the library at once, ordered
+ * before the plan on `stream`), plans, refines, copies the canonical block
+ * ids back into out_block_h, synchronises `stream` and releases everything.
+ * Same arguments and errors as bisim_plan + bisim_refine; all pointers
+ * ending in _h are host memory (pinned memory gives faster copies) and must
+ * stay valid until the call returns; act_h and init_h may be NULL.
  */
 int bisim_reduce_host(int32_t n, int64_t m, int32_t num_act, const int32_t* src_h,
                       const int32_t* act_h, const int32_t* dst_h, const int32_t* init_h,
