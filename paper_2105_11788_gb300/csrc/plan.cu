@@ -6,7 +6,8 @@
 //    starts gives slot = off(source) + order for every transition, nr_marks
 //    is the number of pairs of a state and off their exclusive prefix sum;
 //  - the incoming-transition CSR by target, every entry carrying (source,
-//    slot), built with a counting sort;
+//    slot), built by target bins (or, for very many states and on the sort
+//    route, with a counting sort);
 //  - initial leaders (Algorithm 2, lines 1-6, priority rule: the smallest
 //    member of each initial block);
 //  - action-set preprocessing (Algorithm 5): for every label that occurs, in
@@ -281,15 +282,17 @@ __global__ void k_mask_csr(const int32_t* __restrict__ src, const int32_t* __res
 }
 
 // The incoming-transition CSR in two passes, without a returning global
-// atomic per transition. Targets are cut into bins of 2^bin_bits states;
-// since in_ptr is already known, a bin's entries occupy the known range
-// [in_ptr[first target], in_ptr[last target + 1]) of in_edge.
+// atomic per transition. Targets are cut into bins of 2^bin_bits states; the
+// validation pass counted the transitions of every bin, so a bin's entries
+// occupy a known range of in_edge (the exclusive scan of those counts).
 //   pass A: a CTA takes a tile of transitions, ranks them per bin with
 //     shared-memory atomics, reserves each bin's share of the tile with one
-//     global atomic per (CTA, bin), and writes (target, source << 32 | slot)
-//     records into the bin's range of two scratch arrays;
-//   pass B: one CTA per bin places the bin's records by target with
-//     shared-memory counters: entry in_ptr[t] + (rank among t's records).
+//     global atomic per (CTA, bin), sorts the tile's (target, source << 32 |
+//     slot) records by bin in shared memory and writes each bin's records as
+//     one run into the bin's range of two scratch arrays;
+//   pass B: one CTA per bin counts the bin's records per target, writes
+//     in_ptr for its targets from the scan of the counts, and places every
+//     record at in_ptr[t] + (rank among t's records).
 #ifndef BISIM_CSR_A_THREADS
 #define BISIM_CSR_A_THREADS 1024
 #endif

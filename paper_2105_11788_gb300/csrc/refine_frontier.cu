@@ -1374,10 +1374,10 @@ __device__ __forceinline__ bool multi_round(const FrontierArgs& a, const Worklis
 #define BISIM_PEEL_CHUNKS 4
 #endif
 constexpr int PEEL_CHUNKS = BISIM_PEEL_CHUNKS;  // chunks of 32 transitions a warp loads at once
-constexpr int PEEL_MIN_SINGLES = 256;
-constexpr int PEEL_QUIET = 32;             // a peel round is quiet below one touched block per 32 splitters
-constexpr int PEEL_SWEEP_GROWTH = 4;
-constexpr int PEEL_SWEEP_MAX = 1 << 24;  // a peel round needs this many labels in size bucket 0
+constexpr int PEEL_MIN_SINGLES = 256;    // a peel round needs this many labels in size bucket 0
+constexpr int PEEL_QUIET = 32;           // a peel round is quiet below one touched block per 32 splitters
+constexpr int PEEL_SWEEP_GROWTH = 4;     // after a quiet round the next takes this many times the labels
+constexpr int PEEL_SWEEP_MAX = 1 << 24;  // labels one sweep round takes at most
 
 __device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long* p) {
     return *(volatile const unsigned long long*)p;
