@@ -1,9 +1,9 @@
 """Benchmark: strong-bisimulation reduction of one synthetic LTS per step.
 
 A step is one whole reduction through the C ABI: bisim_plan (validation,
-sort by (source, label), mark slots, incoming-transition CSR, initial
-leaders, action-set preprocessing) and bisim_refine (the main loop and the
-canonical output) on inputs already resident in device memory. The default
+the mark-slot layout of the (source, label) pairs, incoming-transition CSR,
+initial leaders, action-set preprocessing) and bisim_refine (the main loop
+and the canonical output) on inputs already resident in device memory. The default
 workload is the large power-law LTS (seed 3: 10,000,000 states, 99,917,783
 transitions, out-degree Pareto alpha = 2.1 with mean 10, 32 uniform labels,
 4 initial blocks from two atomic propositions). Single-LTS throughput is
